@@ -1,0 +1,184 @@
+/*
+ * rt.h -- C ABI of the GB300 long-characteristics radiative-transfer library.
+ *
+ * The library solves the scattering problem of Hauschildt & Baron, "A 3D
+ * radiative transfer framework IV: spherical & cylindrical coordinate
+ * systems": a formal solution along full (long) characteristics through a
+ * spherical (r, theta_c, phi_c) or cylindrical (R, phi_c, z) voxel grid
+ * (Sect. 2 "Method"), driven by an operator-splitting (ALI) iteration with a
+ * diagonal approximate Lambda operator and Ng acceleration (Sect. 3.2.1), for
+ * a grey continuum with coherent isotropic scattering
+ * S = (1 - eps) J + eps B (Sect. 3.1, item 6).
+ *
+ * Conventions
+ *  - Every call returns an int status (RT_OK = 0 on success).  On failure the
+ *    grid is left unchanged unless stated otherwise, and rt_last_error()
+ *    returns a message for the calling thread.
+ *  - Voxel index v = (i*n2 + j)*n3 + k with (i, j, k) = (r, theta_c, phi_c) on
+ *    the spherical grid and (R, phi_c, z) on the cylindrical grid.  Per-voxel
+ *    arrays are contiguous doubles of length n_vox = n1*n2*n3.
+ *  - `where` says whether a data pointer is host memory (RT_HOST, any pageable
+ *    or pinned buffer) or device memory of the grid's GPU (RT_DEVICE, e.g. the
+ *    data pointer of a CUDA tensor); device copies are ordered on the grid's
+ *    stream.  Host pointers are only read or written during the call.
+ *  - The library owns all device memory it allocates; the caller owns every
+ *    buffer it passes.  A grid is not thread-safe: serialise calls on one grid.
+ */
+#ifndef RT_H
+#define RT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RT_OK 0
+#define RT_EINVAL 1         /* invalid argument; nothing changed */
+#define RT_ENOMEM 2         /* device or host allocation failed */
+#define RT_ECUDA 3          /* a CUDA runtime call failed */
+#define RT_ENOTCONVERGED 4  /* rt_solve reached max_iter */
+#define RT_ETIMEOUT 5       /* reserved: a bounded device wait gave up */
+#define RT_EDEVICE 6        /* a kernel raised its error flag (e.g. a lost characteristic) */
+
+/* coordinate systems (Sect. 3 and 4) */
+#define RT_SPHERICAL 0
+#define RT_CYLINDRICAL 1
+/* inner boundary: I = B of the innermost voxel on characteristics leaving the
+ * core (Sect. 3.1, spherical tests), or a transparent hole crossed without
+ * opacity */
+#define RT_CORE_B 0
+#define RT_TRANSPARENT 1
+/* precision of the formal solution: all FP64, or FP32 ray march with FP64
+ * accumulation, ALI/Ng and FP64 iterative refinement */
+#define RT_FP64 0
+#define RT_MIXED 1
+/* source-function interpolation along a characteristic */
+#define RT_PARABOLIC 0
+#define RT_LINEAR 1
+/* memory spaces */
+#define RT_HOST 0
+#define RT_DEVICE 1
+
+typedef struct rt_grid rt_grid;
+
+/* Problem description for rt_grid_create.  All arrays are copied. */
+typedef struct rt_grid_desc {
+    int coord;              /* RT_SPHERICAL or RT_CYLINDRICAL */
+    int n[3];               /* voxels per axis, each >= 1 */
+    const double *edges[3]; /* n[a]+1 strictly increasing edges per axis.
+                             * spherical: r (r_0 > 0), theta_c in [0, pi] (first 0,
+                             * last pi), phi_c with last - first = 2 pi.
+                             * cylindrical: R (R_0 >= 0), phi_c (2 pi span), z. */
+    int n_angles;           /* solid angles, >= 1 (Sect. 2: prescribed set) */
+    const double *dirs;     /* n_angles x 3 unit direction vectors (p_x, p_y, p_z) */
+    const double *weights;  /* n_angles quadrature weights, positive, sum 1 */
+    int inner_bc;           /* RT_CORE_B or RT_TRANSPARENT */
+    int interp;             /* RT_PARABOLIC (default) or RT_LINEAR */
+    double I_outer;         /* incident intensity at the outer boundary (paper: 0) */
+    int precision;          /* RT_FP64 or RT_MIXED */
+    int use_lstar;          /* 1: diagonal Lambda* ALI; 0: plain Lambda iteration */
+    int ng;                 /* 1: order-2 Ng acceleration every 4 ALI iterates */
+    int refine_every;       /* RT_MIXED: maximum FP32 correction sweeps per FP64
+                             * refinement (0 = default 16) */
+    int angle_block;        /* solid angles per formal-solution block (0 = auto) */
+    int device;             /* CUDA device ordinal */
+    void *stream;           /* cudaStream_t for all work (NULL = legacy default) */
+} rt_grid_desc;
+
+/* Sizes and diagnostics of a grid (rt_get_info). */
+typedef struct rt_info {
+    int64_t n_vox;
+    int64_t n_angles;
+    int64_t n_rays;         /* characteristics over all solid angles */
+    int64_t n_segments;     /* voxel crossings over all solid angles */
+    int64_t device_bytes;   /* device memory held by the grid */
+    int32_t n_blocks;       /* formal-solution angle blocks */
+    int32_t angle_block;
+    int32_t lost_rays;      /* characteristics that could not be tracked (0 expected) */
+    int32_t precision;
+    double geometry_ms;     /* wall time of the characteristic geometry at create */
+} rt_info;
+
+/* Thread-local message for the last failed call (never NULL). */
+const char *rt_last_error(void);
+
+/* Build a grid: copies the description, computes on the GPU, for every solid
+ * angle, the characteristics (one through each boundary voxel the direction
+ * enters, one leaving each core voxel, then one through every voxel not yet
+ * hit, Sect. 2) and their voxel crossing lists (exact shell / cone /
+ * half-plane / cylinder / z-plane crossings), and the per-voxel ownership
+ * lists used to gather J and Lambda* without atomics.  Fields start as
+ * chi = 1, eps = 1, B = 0, S = 0.  *out is set only on RT_OK. */
+int rt_grid_create(rt_grid **out, const rt_grid_desc *d);
+
+/* Release every resource of the grid (NULL is accepted). */
+int rt_grid_destroy(rt_grid *g);
+
+int rt_get_info(const rt_grid *g, rt_info *info);
+
+/* Set extinction chi (> 0, finite), thermalisation eps (in (0, 1]) and Planck
+ * function B (>= 0, finite) per voxel (Sect. 3.1 items 5-6).  S is set to B.
+ * Host input is validated (RT_EINVAL, nothing changed); device input is
+ * taken as given. */
+int rt_set_opacity(rt_grid *g, const double *chi, const double *eps, const double *B, int where);
+
+/* Replace the source function S (warm restart). */
+int rt_set_S(rt_grid *g, const double *S, int where);
+
+/* Formal solution from the current S with the grid's precision: J, the
+ * diagonal Lambda* and the flux vector per voxel (Sect. 2, 3.2). */
+int rt_formal_solution(rt_grid *g);
+
+/* Formal solution with an explicit precision (RT_FP64 or RT_MIXED, i.e. the
+ * FP32 march) and optionally homogeneous boundaries (homog = 1: every incoming
+ * intensity zero, so J = Lambda S). */
+int rt_formal_solution_ex(rt_grid *g, int precision, int homog);
+
+/* One ALI iteration: formal solution, S <- S + [(1-eps) J + eps B - S] /
+ * (1 - (1-eps) Lambda*), and Ng extrapolation when four iterates have
+ * accumulated (if enabled).  *max_rel_dS (may be NULL) receives
+ * max_v |dS| / |S_new| of the update. */
+int rt_ali_step(rt_grid *g, double *max_rel_dS);
+
+/* Iterate to max rel dS < tol.  RT_FP64: plain ALI(+Ng) with the FP64 formal
+ * solution.  RT_MIXED: FP64 formal solutions give the exact residual
+ * r = (1-eps) J + eps B - S, FP32 correction sweeps (ALI + Ng on the
+ * homogeneous problem) solve for the update, repeated until the residual
+ * meets tol.  *iters (may be NULL) receives the number of formal solutions
+ * of the precision that drives convergence (FP64 ones for RT_FP64 and the
+ * total for RT_MIXED).  Returns RT_ENOTCONVERGED at max_iter. */
+int rt_solve(rt_grid *g, double tol, int max_iter, int *iters);
+
+/* Per-voxel results (n_vox doubles; flux: n_vox x 3 in the local basis
+ * (r, theta, phi) or (R, phi, z) at the voxel centre). */
+int rt_get_J(const rt_grid *g, double *out, int where);
+int rt_get_S(const rt_grid *g, double *out, int where);
+int rt_get_Lstar(const rt_grid *g, double *out, int where);
+int rt_get_flux(const rt_grid *g, double *out3, int where);
+
+/* Convergence history of the last rt_solve / rt_ali_step sequence: up to max
+ * values of max rel dS, *n receives the count stored. */
+int rt_get_history(const rt_grid *g, double *hist, int max, int *n);
+
+/* Crossing lists of solid angle omega (host buffers).  Call with NULL arrays
+ * to get *n_rays and *n_seg, then with buffers of those sizes:
+ * ray_off[n_rays+1] (segment offsets), ray_origin[n_rays] (voxel whose centre
+ * the characteristic passes), ray_core[n_rays] (1: starts on the core),
+ * vox[n_seg], len[n_seg] (FP64 path lengths), restart[n_seg] (1: first
+ * segment after a transparent hole).  Rays are listed boundary voxels first,
+ * then core voxels, then coverage completions, each in voxel order. */
+int rt_get_crossings(const rt_grid *g, int omega, int64_t *n_rays, int64_t *n_seg, int32_t *ray_off,
+                     int32_t *ray_origin, int32_t *ray_core, int32_t *vox, double *len, uint8_t *restart);
+
+/* Path-length averaged intensity Ibar and Lambda* element of each voxel for
+ * the n listed solid angles (out arrays n x n_vox), from the current S, with
+ * the given precision.  Used to compare single solid angles. */
+int rt_fs_angles(rt_grid *g, const int32_t *omegas, int n, int precision, double *Ibar, double *Lbar,
+                 int where);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_H */

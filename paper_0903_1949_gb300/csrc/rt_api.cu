@@ -1,0 +1,812 @@
+// rt_api.cu -- C ABI (include/rt.h): grid construction, formal solution,
+// ALI / Ng iteration and mixed-precision refinement, all on one GPU.
+//
+// Host code here only validates, allocates, orders launches on the grid's
+// stream and moves the few scalars the iteration control needs; every step
+// of the method runs in the kernels of geom.cu, march.cu, gather.cu, ali.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rt_internal.h"
+
+using namespace rtk;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(...)                                                                                             \
+    do {                                                                                                    \
+        cudaError_t e_ = (__VA_ARGS__);                                                                     \
+        if (e_ != cudaSuccess) return fail(RT_ECUDA, "%s failed: %s", #__VA_ARGS__, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define RCK(call)             \
+    do {                      \
+        int r_ = (call);      \
+        if (r_ != RT_OK) return r_; \
+    } while (0)
+
+constexpr int MARCH_CHUNK = 512;
+constexpr int64_t BLOCK_SEG_TARGET = 6000000;  // segments per angle block (FP32 pair buffer ~48 MB, L2-resident)
+constexpr int MAX_BLOCK_ANGLES = 256;
+
+}  // namespace
+
+struct rt_grid {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    int coord = 0, n1 = 0, n2 = 0, n3 = 0, nvox = 0, n_ang = 0, nphi = 0;
+    int inner_bc = 0, interp = 0, precision = 0, use_lstar = 1, ng = 1, refine_every = 16;
+    double I_outer = 0.0;
+    std::vector<double> h_e[3], h_dirs, h_wt;
+    std::vector<void *> allocs;
+    int64_t bytes = 0;
+    GeomDev G{};
+    double *d_dirs = nullptr, *d_wt = nullptr;
+    int64_t n_rays = 0, n_seg = 0;
+    std::vector<int64_t> h_ang_ray_off, h_ang_seg_off;
+    int64_t *d_ang_seg_off = nullptr, *d_ray_off = nullptr;
+    int32_t *d_ray_origin = nullptr, *d_ray_angle = nullptr;
+    uint32_t *d_vox = nullptr;
+    double *d_len64 = nullptr;
+    float *d_len32 = nullptr;
+    int ablk = 1, nblk = 0;
+    std::vector<int> blk_w0, blk_nw;
+    int64_t max_blk_seg = 0;
+    int32_t *d_csr_off = nullptr, *d_perm = nullptr;
+    double *d_invL = nullptr;
+    void *d_segbuf = nullptr;
+    double *d_chi = nullptr, *d_eps = nullptr, *d_B = nullptr, *d_S = nullptr;
+    double *d_J = nullptr, *d_L = nullptr, *d_Fc = nullptr, *d_F = nullptr;
+    double2 *d_cs64 = nullptr;
+    float2 *d_cs32 = nullptr;
+    float *d_B32 = nullptr;
+    double *d_H = nullptr, *d_ng_part = nullptr, *d_ng_coef = nullptr;
+    unsigned long long *d_maxrel = nullptr;
+    double *d_r = nullptr, *d_delta = nullptr, *d_Jd = nullptr, *d_Ld = nullptr, *d_Fcd = nullptr, *d_Lkeep = nullptr;
+    double *h_pin = nullptr;  // pinned scalars read back by the iteration control
+    int *d_lost = nullptr;
+    int lost = 0;
+    double geom_ms = 0.0;
+    int hs[4] = {0, 1, 2, 3};
+    int nh = 0;
+    std::vector<double> history;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(rt_grid *g, T **p, size_t count)
+{
+    void *q = nullptr;
+    size_t nbytes = sizeof(T) * (count > 0 ? count : 1);
+    cudaError_t e = cudaMalloc(&q, nbytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RT_ENOMEM, "cudaMalloc of %zu bytes failed: %s", nbytes, cudaGetErrorString(e));
+    }
+    g->allocs.push_back(q);
+    g->bytes += (int64_t)nbytes;
+    *p = (T *)q;
+    return RT_OK;
+}
+
+void dfree(rt_grid *g, void *p)
+{
+    if (!p) return;
+    auto it = std::find(g->allocs.begin(), g->allocs.end(), p);
+    if (it != g->allocs.end()) {
+        g->allocs.erase(it);
+        cudaFree(p);
+    }
+}
+
+void release(rt_grid *g)
+{
+    for (void *p : g->allocs) cudaFree(p);
+    g->allocs.clear();
+    if (g->h_pin) cudaFreeHost(g->h_pin);
+    g->h_pin = nullptr;
+}
+
+int sync(rt_grid *g)
+{
+    CK(cudaStreamSynchronize(g->st));
+    return RT_OK;
+}
+
+int check_desc(const rt_grid_desc *d)
+{
+    if (!d) return fail(RT_EINVAL, "descriptor is NULL");
+    if (d->coord != RT_SPHERICAL && d->coord != RT_CYLINDRICAL) return fail(RT_EINVAL, "coord must be RT_SPHERICAL or RT_CYLINDRICAL");
+    for (int a = 0; a < 3; ++a) {
+        if (d->n[a] < 1) return fail(RT_EINVAL, "n[%d] = %d must be >= 1", a, d->n[a]);
+        if (!d->edges[a]) return fail(RT_EINVAL, "edges[%d] is NULL", a);
+        for (int q = 0; q < d->n[a]; ++q)
+            if (!(d->edges[a][q + 1] > d->edges[a][q]) || !std::isfinite(d->edges[a][q + 1]) ||
+                !std::isfinite(d->edges[a][q]))
+                return fail(RT_EINVAL, "edges[%d] must be finite and strictly increasing (index %d)", a, q);
+    }
+    int64_t nvox = (int64_t)d->n[0] * d->n[1] * d->n[2];
+    if (nvox >= (int64_t)RTK_VOXMASK) return fail(RT_EINVAL, "too many voxels (%lld)", (long long)nvox);
+    const double TWO_PI = 6.283185307179586476925286766559;
+    if (d->coord == RT_SPHERICAL) {
+        if (!(d->edges[0][0] > 0.0)) return fail(RT_EINVAL, "spherical grids need r_0 > 0 (core or hole)");
+        if (d->edges[1][0] != 0.0 || std::fabs(d->edges[1][d->n[1]] - 3.141592653589793238462643383279) > 1e-12)
+            return fail(RT_EINVAL, "theta edges must run from 0 to pi");
+        if (std::fabs(d->edges[2][d->n[2]] - d->edges[2][0] - TWO_PI) > 1e-12)
+            return fail(RT_EINVAL, "phi edges must span 2 pi");
+    } else {
+        if (!(d->edges[0][0] >= 0.0)) return fail(RT_EINVAL, "cylindrical grids need R_0 >= 0");
+        if (std::fabs(d->edges[1][d->n[1]] - d->edges[1][0] - TWO_PI) > 1e-12)
+            return fail(RT_EINVAL, "phi edges must span 2 pi");
+    }
+    if (d->n_angles < 1 || !d->dirs || !d->weights) return fail(RT_EINVAL, "need n_angles >= 1, dirs and weights");
+    double wsum = 0.0;
+    for (int w = 0; w < d->n_angles; ++w) {
+        const double *n = d->dirs + 3 * w;
+        double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+        if (!(std::fabs(nn - 1.0) < 1e-12)) return fail(RT_EINVAL, "direction %d is not a unit vector", w);
+        if (!(d->weights[w] > 0.0) || !std::isfinite(d->weights[w])) return fail(RT_EINVAL, "weight %d must be > 0", w);
+        wsum += d->weights[w];
+    }
+    if (!(std::fabs(wsum - 1.0) < 1e-10)) return fail(RT_EINVAL, "weights must sum to 1 (got %.17g)", wsum);
+    if (d->inner_bc != RT_CORE_B && d->inner_bc != RT_TRANSPARENT) return fail(RT_EINVAL, "bad inner_bc");
+    if (d->interp != RT_PARABOLIC && d->interp != RT_LINEAR) return fail(RT_EINVAL, "bad interp");
+    if (d->precision != RT_FP64 && d->precision != RT_MIXED) return fail(RT_EINVAL, "bad precision");
+    if (!std::isfinite(d->I_outer) || d->I_outer < 0.0) return fail(RT_EINVAL, "I_outer must be finite and >= 0");
+    if (d->angle_block < 0 || d->angle_block > MAX_BLOCK_ANGLES) return fail(RT_EINVAL, "angle_block must be in [0, 256]");
+    if (d->refine_every < 0) return fail(RT_EINVAL, "refine_every must be >= 0");
+    return RT_OK;
+}
+
+// Trigonometric tables of the angular edges and mid-points (G0), uploaded.
+int upload_tables(rt_grid *g)
+{
+    const bool sph = g->coord == RT_SPHERICAL;
+    const std::vector<double> &pe = sph ? g->h_e[2] : g->h_e[1];
+    int nphi = g->nphi;
+    std::vector<double> cp(nphi), sp(nphi), cpm(nphi), spm(nphi);
+    for (int k = 0; k < nphi; ++k) {
+        double pm = 0.5 * (pe[k] + pe[k + 1]);
+        cp[k] = std::cos(pe[k]);
+        sp[k] = std::sin(pe[k]);
+        cpm[k] = std::cos(pm);
+        spm[k] = std::sin(pm);
+    }
+    std::vector<double> ct, ctm, stm;
+    if (sph) {
+        ct.resize(g->n2 + 1);
+        ctm.resize(g->n2);
+        stm.resize(g->n2);
+        for (int j = 0; j <= g->n2; ++j) ct[j] = std::cos(g->h_e[1][j]);
+        for (int j = 0; j < g->n2; ++j) {
+            double tm = 0.5 * (g->h_e[1][j] + g->h_e[1][j + 1]);
+            ctm[j] = std::cos(tm);
+            stm[j] = std::sin(tm);
+        }
+    } else {
+        ct.assign(1, 0.0);
+        ctm.assign(1, 0.0);
+        stm.assign(1, 0.0);
+    }
+    auto up = [&](const std::vector<double> &h, const double **out) -> int {
+        double *p = nullptr;
+        RCK(dalloc(g, &p, h.size()));
+        CK(cudaMemcpyAsync(p, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, g->st));
+        *out = p;
+        return RT_OK;
+    };
+    RCK(up(g->h_e[0], &g->G.e1));
+    RCK(up(g->h_e[1], &g->G.e2));
+    RCK(up(g->h_e[2], &g->G.e3));
+    RCK(up(ct, &g->G.ct));
+    RCK(up(ctm, &g->G.ctm));
+    RCK(up(stm, &g->G.stm));
+    RCK(up(cp, &g->G.cp));
+    RCK(up(sp, &g->G.sp));
+    RCK(up(cpm, &g->G.cpm));
+    RCK(up(spm, &g->G.spm));
+    const double *pd = nullptr, *pw = nullptr;
+    RCK(up(g->h_dirs, &pd));
+    RCK(up(g->h_wt, &pw));
+    g->d_dirs = (double *)pd;
+    g->d_wt = (double *)pw;
+    g->G.coord = g->coord;
+    g->G.n1 = g->n1;
+    g->G.n2 = g->n2;
+    g->G.n3 = g->n3;
+    g->G.nphi = g->nphi;
+    g->G.inner_bc = g->inner_bc;
+    g->G.nvox = g->nvox;
+    return RT_OK;
+}
+
+// Launch set, crossing lists and ownership lists of every solid angle.
+int build_geometry(rt_grid *g)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const int nvox = g->nvox, n_ang = g->n_ang;
+    const int words = (nvox + 31) / 32;
+    RCK(dalloc(g, &g->d_lost, 1));
+    CK(cudaMemsetAsync(g->d_lost, 0, sizeof(int), g->st));
+    uint32_t *comp = nullptr;
+    RCK(dalloc(g, &comp, (size_t)n_ang * words));
+    CK(cudaMemsetAsync(comp, 0, sizeof(uint32_t) * (size_t)n_ang * words, g->st));
+    // launch set: boundary marks, then serial-order coverage completion, in angle chunks
+    const int cap = geom_scratch_cap(g->G);
+    const int64_t per_angle = (int64_t)words * 4 + (int64_t)32 * cap * 4;
+    int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(n_ang, ((int64_t)1 << 31) / per_angle));
+    uint32_t *hit = nullptr;
+    int32_t *scratch = nullptr;
+    RCK(dalloc(g, &hit, (size_t)chunk * words));
+    RCK(dalloc(g, &scratch, (size_t)chunk * 32 * cap));
+    for (int w0 = 0; w0 < n_ang; w0 += chunk) {
+        int nw = std::min(chunk, n_ang - w0);
+        CK(cudaMemsetAsync(hit, 0, sizeof(uint32_t) * (size_t)nw * words, g->st));
+        CK(geom_mark_boundary(g->G, g->d_dirs, w0, nw, hit, words, g->d_lost, g->st));
+        CK(geom_complete(g->G, g->d_dirs, w0, nw, hit, comp + (size_t)w0 * words, words, scratch, cap, g->d_lost,
+                         g->st));
+    }
+    dfree(g, hit);
+    dfree(g, scratch);
+    // ordered ray lists
+    int32_t *counts = nullptr;
+    RCK(dalloc(g, &counts, n_ang));
+    CK(geom_count_rays(g->G, g->d_dirs, n_ang, comp, words, counts, g->st));
+    std::vector<int32_t> hc(n_ang);
+    CK(cudaMemcpyAsync(hc.data(), counts, sizeof(int32_t) * n_ang, cudaMemcpyDeviceToHost, g->st));
+    RCK(sync(g));
+    g->h_ang_ray_off.assign(n_ang + 1, 0);
+    for (int w = 0; w < n_ang; ++w) g->h_ang_ray_off[w + 1] = g->h_ang_ray_off[w] + hc[w];
+    g->n_rays = g->h_ang_ray_off[n_ang];
+    int64_t *d_aro = nullptr;
+    RCK(dalloc(g, &d_aro, n_ang + 1));
+    CK(cudaMemcpyAsync(d_aro, g->h_ang_ray_off.data(), sizeof(int64_t) * (n_ang + 1), cudaMemcpyHostToDevice, g->st));
+    RCK(dalloc(g, &g->d_ray_origin, g->n_rays));
+    RCK(dalloc(g, &g->d_ray_angle, g->n_rays));
+    CK(geom_list_rays(g->G, g->d_dirs, n_ang, comp, words, d_aro, g->d_ray_origin, g->d_ray_angle, g->st));
+    dfree(g, comp);
+    dfree(g, counts);
+    // segment counts, offsets, lists
+    int32_t *nseg = nullptr, *nback = nullptr;
+    RCK(dalloc(g, &nseg, g->n_rays));
+    RCK(dalloc(g, &nback, g->n_rays));
+    CK(geom_count_segs(g->G, g->d_dirs, g->n_rays, g->d_ray_origin, g->d_ray_angle, nseg, nback, g->d_lost, g->st));
+    RCK(dalloc(g, &g->d_ray_off, g->n_rays + 1));
+    int64_t *tmp = nullptr;
+    RCK(dalloc(g, &tmp, scan_tmp_elems(g->n_rays)));
+    CK(scan_i32(nseg, g->d_ray_off, g->n_rays, tmp, g->st));
+    dfree(g, tmp);
+    CK(cudaMemcpyAsync(&g->n_seg, g->d_ray_off + g->n_rays, sizeof(int64_t), cudaMemcpyDeviceToHost, g->st));
+    RCK(sync(g));
+    dfree(g, nseg);
+    RCK(dalloc(g, &g->d_vox, g->n_seg));
+    RCK(dalloc(g, &g->d_len64, g->n_seg));
+    RCK(dalloc(g, &g->d_len32, g->n_seg));
+    CK(cudaMemsetAsync(g->d_vox, 0, sizeof(uint32_t) * (size_t)g->n_seg, g->st));
+    CK(geom_write_segs(g->G, g->d_dirs, g->n_rays, g->d_ray_origin, g->d_ray_angle, g->d_ray_off, nback, g->d_vox,
+                       g->d_len64, g->d_len32, g->d_lost, g->st));
+    dfree(g, nback);
+    // segment offsets of every solid angle
+    RCK(dalloc(g, &g->d_ang_seg_off, n_ang + 1));
+    CK(gather_i64(g->d_ray_off, d_aro, g->d_ang_seg_off, n_ang + 1, g->st));
+    g->h_ang_seg_off.assign(n_ang + 1, 0);
+    CK(cudaMemcpyAsync(g->h_ang_seg_off.data(), g->d_ang_seg_off, sizeof(int64_t) * (n_ang + 1),
+                       cudaMemcpyDeviceToHost, g->st));
+    CK(cudaMemcpyAsync(&g->lost, g->d_lost, sizeof(int), cudaMemcpyDeviceToHost, g->st));
+    RCK(sync(g));
+    dfree(g, d_aro);
+    // angle blocks sized so one block's per-segment results stay in L2
+    double avg = (double)g->n_seg / n_ang;
+    int ablk = g->ablk;
+    if (ablk <= 0) ablk = (int)std::max(1.0, std::min((double)BLOCK_SEG_TARGET / std::max(avg, 1.0), (double)MAX_BLOCK_ANGLES));
+    ablk = std::min(ablk, n_ang);
+    g->ablk = ablk;
+    g->blk_w0.clear();
+    g->blk_nw.clear();
+    g->max_blk_seg = 0;
+    for (int w0 = 0; w0 < n_ang; w0 += ablk) {
+        int nw = std::min(ablk, n_ang - w0);
+        g->blk_w0.push_back(w0);
+        g->blk_nw.push_back(nw);
+        int64_t ns = g->h_ang_seg_off[w0 + nw] - g->h_ang_seg_off[w0];
+        if (ns >= ((int64_t)1 << 31)) return fail(RT_EINVAL, "angle block %d holds too many segments; lower angle_block", w0);
+        g->max_blk_seg = std::max(g->max_blk_seg, ns);
+    }
+    g->nblk = (int)g->blk_w0.size();
+    // ownership (CSR) lists and inverse path lengths per (angle, voxel)
+    RCK(dalloc(g, &g->d_csr_off, (size_t)g->nblk * (nvox + 1)));
+    RCK(dalloc(g, &g->d_perm, g->n_seg));
+    RCK(dalloc(g, &g->d_invL, (size_t)n_ang * nvox));
+    int32_t *cnt = nullptr, *cursor = nullptr;
+    int64_t *ctmp = nullptr;
+    RCK(dalloc(g, &cnt, nvox));
+    RCK(dalloc(g, &cursor, nvox));
+    RCK(dalloc(g, &ctmp, (nvox + 1) + scan_tmp_elems(nvox)));
+    for (int b = 0; b < g->nblk; ++b) {
+        int w0 = g->blk_w0[b], nw = g->blk_nw[b];
+        int64_t lo = g->h_ang_seg_off[w0], ns = g->h_ang_seg_off[w0 + nw] - lo;
+        int32_t *off = g->d_csr_off + (size_t)b * (nvox + 1);
+        CK(csr_build(nvox, g->d_vox + lo, ns, cnt, off, cursor, g->d_perm + lo, ctmp, g->st));
+        CK(csr_invL(nvox, off, g->d_perm + lo, g->d_len64 + lo, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->st));
+    }
+    RCK(sync(g));
+    dfree(g, cnt);
+    dfree(g, cursor);
+    dfree(g, ctmp);
+    g->geom_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return RT_OK;
+}
+
+int alloc_fields(rt_grid *g)
+{
+    const int n = g->nvox;
+    RCK(dalloc(g, &g->d_chi, n));
+    RCK(dalloc(g, &g->d_eps, n));
+    RCK(dalloc(g, &g->d_B, n));
+    RCK(dalloc(g, &g->d_S, n));
+    RCK(dalloc(g, &g->d_J, n));
+    RCK(dalloc(g, &g->d_L, n));
+    RCK(dalloc(g, &g->d_Fc, 3 * (size_t)n));
+    RCK(dalloc(g, &g->d_F, 3 * (size_t)n));
+    RCK(dalloc(g, &g->d_cs64, n));
+    RCK(dalloc(g, &g->d_cs32, n));
+    RCK(dalloc(g, &g->d_B32, n));
+    RCK(dalloc(g, &g->d_H, 4 * (size_t)n));
+    RCK(dalloc(g, &g->d_ng_part, ng_partial_elems(n)));
+    RCK(dalloc(g, &g->d_ng_coef, 4));
+    RCK(dalloc(g, &g->d_maxrel, 1));
+    RCK(dalloc(g, &g->d_r, n));
+    RCK(dalloc(g, &g->d_delta, n));
+    RCK(dalloc(g, &g->d_Jd, n));
+    RCK(dalloc(g, &g->d_Ld, n));
+    RCK(dalloc(g, &g->d_Fcd, 3 * (size_t)n));
+    RCK(dalloc(g, &g->d_Lkeep, n));
+    void *seg = nullptr;
+    cudaError_t e = cudaMalloc(&seg, sizeof(double2) * (size_t)std::max<int64_t>(1, g->max_blk_seg));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RT_ENOMEM, "segment buffer allocation failed");
+    }
+    g->allocs.push_back(seg);
+    g->bytes += (int64_t)(sizeof(double2) * (size_t)std::max<int64_t>(1, g->max_blk_seg));
+    g->d_segbuf = seg;
+    CK(cudaMallocHost((void **)&g->h_pin, 8 * sizeof(double)));
+    CK(fill_const(n, g->d_chi, 1.0, g->st));
+    CK(fill_const(n, g->d_eps, 1.0, g->st));
+    CK(fill_const(n, g->d_B, 0.0, g->st));
+    CK(fill_const(n, g->d_S, 0.0, g->st));
+    CK(fill_const(n, g->d_J, 0.0, g->st));
+    CK(fill_const(n, g->d_L, 0.0, g->st));
+    CK(fill_const(3 * n, g->d_F, 0.0, g->st));
+    return RT_OK;
+}
+
+// Formal solution of every angle block with the FP64 or FP32 march.
+int run_fs(rt_grid *g, int prec, int homog, const double *S_src, double *J, double *L, double *Fc, double *F)
+{
+    const int n = g->nvox;
+    const int para = g->interp == RT_PARABOLIC;
+    if (prec == RT_FP64) CK(pack_chiS64(n, g->d_chi, S_src, g->d_cs64, g->st));
+    else CK(pack_chiS32(n, g->d_chi, S_src, g->d_B, g->d_cs32, g->d_B32, g->st));
+    for (int b = 0; b < g->nblk; ++b) {
+        int w0 = g->blk_w0[b], nw = g->blk_nw[b];
+        int64_t r_lo = g->h_ang_ray_off[w0], r_hi = g->h_ang_ray_off[w0 + nw];
+        int64_t lo = g->h_ang_seg_off[w0], ns = g->h_ang_seg_off[w0 + nw] - lo;
+        const int32_t *off = g->d_csr_off + (size_t)b * (n + 1);
+        if (prec == RT_FP64) {
+            double2 *buf = (double2 *)g->d_segbuf;
+            CK(march_block<double, double2>(g->d_vox, g->d_len64, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs64, g->d_B,
+                                            g->I_outer, homog, para, buf, MARCH_CHUNK, g->st));
+            CK(gather_block<double2>(n, off, g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->d_wt,
+                                     g->d_dirs, J, L, Fc, b == 0, g->st));
+        } else {
+            float2 *buf = (float2 *)g->d_segbuf;
+            CK(march_block<float, float2>(g->d_vox, g->d_len32, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs32, g->d_B32,
+                                          (float)g->I_outer, homog, para, buf, MARCH_CHUNK, g->st));
+            CK(gather_block<float2>(n, off, g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->d_wt,
+                                    g->d_dirs, J, L, Fc, b == 0, g->st));
+        }
+    }
+    if (F) CK(flux_local(g->G, Fc, F, g->st));
+    return RT_OK;
+}
+
+int read_maxrel(rt_grid *g, double *rel)
+{
+    CK(cudaMemcpyAsync(g->h_pin, g->d_maxrel, sizeof(double), cudaMemcpyDeviceToHost, g->st));
+    RCK(sync(g));
+    *rel = g->h_pin[0];  // the device word holds the bits of a non-negative double
+    return RT_OK;
+}
+
+void reset_ng(rt_grid *g)
+{
+    for (int q = 0; q < 4; ++q) g->hs[q] = q;
+    g->nh = 0;
+}
+
+double *ng_append_slot(rt_grid *g)
+{
+    if (g->nh == 4) {
+        int t = g->hs[0];
+        g->hs[0] = g->hs[1];
+        g->hs[1] = g->hs[2];
+        g->hs[2] = g->hs[3];
+        g->hs[3] = t;
+        g->nh = 3;
+    }
+    return g->d_H + (size_t)g->hs[g->nh] * g->nvox;
+}
+
+// After an iterate was written to the slot from ng_append_slot: extrapolate
+// into `out` once four iterates are stored; clears the history if applied.
+int ng_maybe(rt_grid *g, double *out, const double *wref)
+{
+    g->nh++;
+    if (g->nh < 4) return RT_OK;
+    const size_t n = g->nvox;
+    CK(ng_extrapolate(g->nvox, g->d_H + g->hs[3] * n, g->d_H + g->hs[2] * n, g->d_H + g->hs[1] * n,
+                      g->d_H + g->hs[0] * n, wref, g->d_ng_part, g->d_ng_coef, out, g->st));
+    CK(cudaMemcpyAsync(g->h_pin + 1, g->d_ng_coef + 2, sizeof(double), cudaMemcpyDeviceToHost, g->st));
+    RCK(sync(g));
+    if (g->h_pin[1] != 0.0) g->nh = 0;
+    return RT_OK;
+}
+
+int ali_step_impl(rt_grid *g, int prec, double *rel_out)
+{
+    RCK(run_fs(g, prec, 0, g->d_S, g->d_J, g->d_L, g->d_Fc, g->d_F));
+    CK(cudaMemsetAsync(g->d_maxrel, 0, sizeof(unsigned long long), g->st));
+    double *slot = g->ng ? ng_append_slot(g) : nullptr;
+    CK(ali_update(g->nvox, g->d_S, g->d_J, g->d_L, g->d_eps, g->d_B, g->use_lstar, slot, g->d_maxrel, g->st));
+    double rel = 0.0;
+    RCK(read_maxrel(g, &rel));
+    *rel_out = rel;
+    g->history.push_back(rel);
+    return RT_OK;
+}
+
+int copy_out(rt_grid *g, const double *src, double *out, size_t n, int where)
+{
+    if (!out) return fail(RT_EINVAL, "output pointer is NULL");
+    if (where != RT_HOST && where != RT_DEVICE) return fail(RT_EINVAL, "where must be RT_HOST or RT_DEVICE");
+    CK(cudaMemcpyAsync(out, src, sizeof(double) * n, where == RT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                       g->st));
+    if (where == RT_HOST) RCK(sync(g));
+    return RT_OK;
+}
+
+int check_lost(rt_grid *g)
+{
+    if (g->lost) return fail(RT_EDEVICE, "%d characteristics could not be tracked", g->lost);
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rt_last_error(void) { return g_err.c_str(); }
+
+int rt_grid_create(rt_grid **out, const rt_grid_desc *d)
+{
+    if (!out) return fail(RT_EINVAL, "out is NULL");
+    RCK(check_desc(d));
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return fail(RT_ECUDA, "no CUDA device available");
+    }
+    if (d->device < 0 || d->device >= ndev) return fail(RT_EINVAL, "device %d out of range", d->device);
+    CK(cudaSetDevice(d->device));
+    rt_grid *g = new rt_grid();
+    g->device = d->device;
+    g->st = (cudaStream_t)d->stream;
+    g->coord = d->coord;
+    g->n1 = d->n[0];
+    g->n2 = d->n[1];
+    g->n3 = d->n[2];
+    g->nvox = g->n1 * g->n2 * g->n3;
+    g->n_ang = d->n_angles;
+    g->nphi = (d->coord == RT_SPHERICAL) ? g->n3 : g->n2;
+    g->inner_bc = d->inner_bc;
+    g->interp = d->interp;
+    g->precision = d->precision;
+    g->use_lstar = d->use_lstar ? 1 : 0;
+    g->ng = d->ng ? 1 : 0;
+    g->refine_every = d->refine_every > 0 ? d->refine_every : 16;
+    g->I_outer = d->I_outer;
+    g->ablk = d->angle_block;
+    for (int a = 0; a < 3; ++a) g->h_e[a].assign(d->edges[a], d->edges[a] + d->n[a] + 1);
+    g->h_dirs.assign(d->dirs, d->dirs + 3 * (size_t)d->n_angles);
+    g->h_wt.assign(d->weights, d->weights + d->n_angles);
+    int rc = upload_tables(g);
+    if (rc == RT_OK) rc = build_geometry(g);
+    if (rc == RT_OK) rc = alloc_fields(g);
+    if (rc == RT_OK) rc = sync(g);
+    if (rc != RT_OK) {
+        std::string keep = g_err;
+        cudaStreamSynchronize(g->st);
+        release(g);
+        delete g;
+        g_err = keep;
+        return rc;
+    }
+    *out = g;
+    return RT_OK;
+}
+
+int rt_grid_destroy(rt_grid *g)
+{
+    if (!g) return RT_OK;
+    cudaSetDevice(g->device);
+    cudaStreamSynchronize(g->st);
+    release(g);
+    delete g;
+    return RT_OK;
+}
+
+int rt_get_info(const rt_grid *g, rt_info *info)
+{
+    if (!g || !info) return fail(RT_EINVAL, "NULL argument");
+    info->n_vox = g->nvox;
+    info->n_angles = g->n_ang;
+    info->n_rays = g->n_rays;
+    info->n_segments = g->n_seg;
+    info->device_bytes = g->bytes;
+    info->n_blocks = g->nblk;
+    info->angle_block = g->ablk;
+    info->lost_rays = g->lost;
+    info->precision = g->precision;
+    info->geometry_ms = g->geom_ms;
+    return RT_OK;
+}
+
+int rt_set_opacity(rt_grid *g, const double *chi, const double *eps, const double *B, int where)
+{
+    if (!g || !chi || !eps || !B) return fail(RT_EINVAL, "NULL argument");
+    if (where != RT_HOST && where != RT_DEVICE) return fail(RT_EINVAL, "where must be RT_HOST or RT_DEVICE");
+    CK(cudaSetDevice(g->device));
+    const size_t n = g->nvox;
+    if (where == RT_HOST) {
+        for (size_t v = 0; v < n; ++v) {
+            if (!(chi[v] > 0.0) || !std::isfinite(chi[v])) return fail(RT_EINVAL, "chi[%zu] must be > 0 and finite", v);
+            if (!(eps[v] > 0.0 && eps[v] <= 1.0)) return fail(RT_EINVAL, "eps[%zu] must be in (0, 1]", v);
+            if (!(B[v] >= 0.0) || !std::isfinite(B[v])) return fail(RT_EINVAL, "B[%zu] must be >= 0 and finite", v);
+        }
+    }
+    cudaMemcpyKind kind = where == RT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(g->d_chi, chi, sizeof(double) * n, kind, g->st));
+    CK(cudaMemcpyAsync(g->d_eps, eps, sizeof(double) * n, kind, g->st));
+    CK(cudaMemcpyAsync(g->d_B, B, sizeof(double) * n, kind, g->st));
+    CK(cudaMemcpyAsync(g->d_S, g->d_B, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->st));
+    if (where == RT_HOST) RCK(sync(g));
+    reset_ng(g);
+    g->history.clear();
+    return RT_OK;
+}
+
+int rt_set_S(rt_grid *g, const double *S, int where)
+{
+    if (!g || !S) return fail(RT_EINVAL, "NULL argument");
+    if (where != RT_HOST && where != RT_DEVICE) return fail(RT_EINVAL, "where must be RT_HOST or RT_DEVICE");
+    CK(cudaSetDevice(g->device));
+    CK(cudaMemcpyAsync(g->d_S, S, sizeof(double) * g->nvox,
+                       where == RT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->st));
+    if (where == RT_HOST) RCK(sync(g));
+    reset_ng(g);
+    g->history.clear();
+    return RT_OK;
+}
+
+int rt_formal_solution_ex(rt_grid *g, int precision, int homog)
+{
+    if (!g) return fail(RT_EINVAL, "grid is NULL");
+    if (precision != RT_FP64 && precision != RT_MIXED) return fail(RT_EINVAL, "bad precision");
+    RCK(check_lost(g));
+    CK(cudaSetDevice(g->device));
+    RCK(run_fs(g, precision, homog ? 1 : 0, g->d_S, g->d_J, g->d_L, g->d_Fc, g->d_F));
+    CK(cudaGetLastError());
+    return RT_OK;
+}
+
+int rt_formal_solution(rt_grid *g)
+{
+    if (!g) return fail(RT_EINVAL, "grid is NULL");
+    return rt_formal_solution_ex(g, g->precision, 0);
+}
+
+int rt_ali_step(rt_grid *g, double *max_rel_dS)
+{
+    if (!g) return fail(RT_EINVAL, "grid is NULL");
+    RCK(check_lost(g));
+    CK(cudaSetDevice(g->device));
+    double rel = 0.0;
+    RCK(ali_step_impl(g, g->precision, &rel));
+    if (g->ng) RCK(ng_maybe(g, g->d_S, nullptr));
+    if (max_rel_dS) *max_rel_dS = rel;
+    return RT_OK;
+}
+
+int rt_solve(rt_grid *g, double tol, int max_iter, int *iters)
+{
+    if (!g) return fail(RT_EINVAL, "grid is NULL");
+    if (!(tol > 0.0) || max_iter < 1) return fail(RT_EINVAL, "need tol > 0 and max_iter >= 1");
+    RCK(check_lost(g));
+    CK(cudaSetDevice(g->device));
+    reset_ng(g);
+    g->history.clear();
+    if (iters) *iters = 0;
+    if (g->precision == RT_FP64) {
+        for (int it = 1; it <= max_iter; ++it) {
+            double rel = 0.0;
+            RCK(ali_step_impl(g, RT_FP64, &rel));
+            if (iters) *iters = it;
+            if (rel < tol) return RT_OK;
+            if (g->ng) RCK(ng_maybe(g, g->d_S, nullptr));
+        }
+        return fail(RT_ENOTCONVERGED, "no convergence to %g in %d iterations", tol, max_iter);
+    }
+    // mixed precision: FP64 residual, FP32 correction sweeps, FP64 update
+    const int n = g->nvox;
+    int total = 0;
+    while (total < max_iter) {
+        RCK(run_fs(g, RT_FP64, 0, g->d_S, g->d_J, g->d_L, g->d_Fc, g->d_F));
+        total++;
+        CK(cudaMemsetAsync(g->d_maxrel, 0, sizeof(unsigned long long), g->st));
+        CK(residual(n, g->d_S, g->d_J, g->d_L, g->d_eps, g->d_B, g->use_lstar, g->d_r, g->d_maxrel, g->st));
+        double rel = 0.0;
+        RCK(read_maxrel(g, &rel));
+        g->history.push_back(rel);
+        if (iters) *iters = total;
+        if (rel < tol) return RT_OK;
+        CK(cudaMemcpyAsync(g->d_Lkeep, g->d_L, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->st));
+        CK(cudaMemsetAsync(g->d_delta, 0, sizeof(double) * n, g->st));
+        reset_ng(g);
+        const double inner_tol = std::max(0.01 * rel, 0.1 * tol);
+        for (int k = 0; k < g->refine_every && total < max_iter; ++k) {
+            RCK(run_fs(g, RT_MIXED, 1, g->d_delta, g->d_Jd, g->d_Ld, g->d_Fcd, nullptr));
+            total++;
+            CK(cudaMemsetAsync(g->d_maxrel, 0, sizeof(unsigned long long), g->st));
+            double *slot = g->ng ? ng_append_slot(g) : nullptr;
+            CK(ali_correction(n, g->d_delta, g->d_Jd, g->d_r, g->d_Lkeep, g->d_eps, g->d_S, g->use_lstar, slot,
+                              g->d_maxrel, g->st));
+            double rd = 0.0;
+            RCK(read_maxrel(g, &rd));
+            if (rd < inner_tol) break;
+            if (g->ng) RCK(ng_maybe(g, g->d_delta, g->d_S));
+        }
+        CK(add_inplace(n, g->d_S, g->d_delta, g->st));
+    }
+    if (iters) *iters = total;
+    return fail(RT_ENOTCONVERGED, "no convergence to %g in %d formal solutions", tol, max_iter);
+}
+
+int rt_get_J(const rt_grid *g, double *out, int where)
+{
+    if (!g) return fail(RT_EINVAL, "grid is NULL");
+    return copy_out((rt_grid *)g, g->d_J, out, g->nvox, where);
+}
+
+int rt_get_S(const rt_grid *g, double *out, int where)
+{
+    if (!g) return fail(RT_EINVAL, "grid is NULL");
+    return copy_out((rt_grid *)g, g->d_S, out, g->nvox, where);
+}
+
+int rt_get_Lstar(const rt_grid *g, double *out, int where)
+{
+    if (!g) return fail(RT_EINVAL, "grid is NULL");
+    return copy_out((rt_grid *)g, g->d_L, out, g->nvox, where);
+}
+
+int rt_get_flux(const rt_grid *g, double *out3, int where)
+{
+    if (!g) return fail(RT_EINVAL, "grid is NULL");
+    return copy_out((rt_grid *)g, g->d_F, out3, 3 * (size_t)g->nvox, where);
+}
+
+int rt_get_history(const rt_grid *g, double *hist, int max, int *n)
+{
+    if (!g || !n) return fail(RT_EINVAL, "NULL argument");
+    int c = (int)std::min<size_t>(g->history.size(), max > 0 ? (size_t)max : 0);
+    if (hist)
+        for (int q = 0; q < c; ++q) hist[q] = g->history[q];
+    *n = hist ? c : (int)g->history.size();
+    return RT_OK;
+}
+
+int rt_get_crossings(const rt_grid *g, int omega, int64_t *n_rays, int64_t *n_seg, int32_t *ray_off,
+                     int32_t *ray_origin, int32_t *ray_core, int32_t *vox, double *len, uint8_t *restart)
+{
+    if (!g || !n_rays || !n_seg) return fail(RT_EINVAL, "NULL argument");
+    if (omega < 0 || omega >= g->n_ang) return fail(RT_EINVAL, "omega %d out of range", omega);
+    rt_grid *gg = (rt_grid *)g;
+    CK(cudaSetDevice(g->device));
+    int64_t r0 = g->h_ang_ray_off[omega], r1 = g->h_ang_ray_off[omega + 1];
+    int64_t s0 = g->h_ang_seg_off[omega], s1 = g->h_ang_seg_off[omega + 1];
+    *n_rays = r1 - r0;
+    *n_seg = s1 - s0;
+    if (!ray_off && !ray_origin && !ray_core && !vox && !len && !restart) return RT_OK;
+    if (!ray_off || !ray_origin || !ray_core || !vox || !len || !restart) return fail(RT_EINVAL, "all buffers are needed");
+    std::vector<int64_t> ro(r1 - r0 + 1);
+    std::vector<uint32_t> vw(s1 - s0);
+    CK(cudaMemcpyAsync(ro.data(), g->d_ray_off + r0, sizeof(int64_t) * ro.size(), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaMemcpyAsync(ray_origin, g->d_ray_origin + r0, sizeof(int32_t) * (r1 - r0), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaMemcpyAsync(vw.data(), g->d_vox + s0, sizeof(uint32_t) * vw.size(), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaMemcpyAsync(len, g->d_len64 + s0, sizeof(double) * vw.size(), cudaMemcpyDeviceToHost, g->st));
+    RCK(sync(gg));
+    for (size_t r = 0; r < ro.size(); ++r) ray_off[r] = (int32_t)(ro[r] - s0);
+    for (size_t s = 0; s < vw.size(); ++s) {
+        vox[s] = (int32_t)(vw[s] & RTK_VOXMASK);
+        restart[s] = (vw[s] & RTK_RESTART) ? 1 : 0;
+    }
+    for (int64_t r = 0; r < r1 - r0; ++r) ray_core[r] = (vw[ro[r] - s0] & RTK_CORE) ? 1 : 0;
+    return RT_OK;
+}
+
+int rt_fs_angles(rt_grid *g, const int32_t *omegas, int n, int precision, double *Ibar, double *Lbar, int where)
+{
+    if (!g || (!omegas && n > 0) || !Ibar || !Lbar) return fail(RT_EINVAL, "NULL argument");
+    if (precision != RT_FP64 && precision != RT_MIXED) return fail(RT_EINVAL, "bad precision");
+    if (where != RT_HOST && where != RT_DEVICE) return fail(RT_EINVAL, "where must be RT_HOST or RT_DEVICE");
+    for (int q = 0; q < n; ++q)
+        if (omegas[q] < 0 || omegas[q] >= g->n_ang) return fail(RT_EINVAL, "omega %d out of range", omegas[q]);
+    RCK(check_lost(g));
+    CK(cudaSetDevice(g->device));
+    const int nv = g->nvox;
+    const int para = g->interp == RT_PARABOLIC;
+    if (precision == RT_FP64) CK(pack_chiS64(nv, g->d_chi, g->d_S, g->d_cs64, g->st));
+    else CK(pack_chiS32(nv, g->d_chi, g->d_S, g->d_B, g->d_cs32, g->d_B32, g->st));
+    double *tI = g->d_Jd, *tL = g->d_Ld;  // scratch vectors of the correction sweep
+    int marched = -1;  // block whose per-segment results are in the buffer
+    for (int q = 0; q < n; ++q) {
+        int w = omegas[q];
+        int b = w / g->ablk;
+        int w0 = g->blk_w0[b], nw = g->blk_nw[b];
+        int64_t r_lo = g->h_ang_ray_off[w0], r_hi = g->h_ang_ray_off[w0 + nw];
+        int64_t lo = g->h_ang_seg_off[w0], ns = g->h_ang_seg_off[w0 + nw] - lo;
+        const int32_t *off = g->d_csr_off + (size_t)b * (nv + 1);
+        if (b == marched) {
+            // results of this block are still in the buffer
+        } else if (precision == RT_FP64)
+            CK(march_block<double, double2>(g->d_vox, g->d_len64, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs64, g->d_B,
+                                            g->I_outer, 0, para, (double2 *)g->d_segbuf, MARCH_CHUNK, g->st));
+        else
+            CK(march_block<float, float2>(g->d_vox, g->d_len32, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs32, g->d_B32,
+                                          (float)g->I_outer, 0, para, (float2 *)g->d_segbuf, MARCH_CHUNK, g->st));
+        marched = b;
+        CK(gather_angle_range(nv, off, g->d_perm + lo, g->d_segbuf, precision == RT_MIXED,
+                              g->h_ang_seg_off[w] - lo, g->h_ang_seg_off[w + 1] - lo, g->d_invL + (size_t)w * nv, tI,
+                              tL, g->st));
+        cudaMemcpyKind kind = where == RT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+        CK(cudaMemcpyAsync(Ibar + (size_t)q * nv, tI, sizeof(double) * nv, kind, g->st));
+        CK(cudaMemcpyAsync(Lbar + (size_t)q * nv, tL, sizeof(double) * nv, kind, g->st));
+    }
+    RCK(sync(g));
+    return RT_OK;
+}
+
+}  // extern "C"

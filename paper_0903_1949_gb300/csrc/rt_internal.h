@@ -1,0 +1,98 @@
+// rt_internal.h -- device data layout and kernel entry points shared by the
+// translation units of the GB300 radiative-transfer library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rt.h"
+
+// Segment word: voxel id in the low 29 bits plus three flags.
+#define RTK_RAYSTART 0x80000000u  // first segment of a characteristic
+#define RTK_CORE 0x40000000u      // the characteristic starts on the core (I_in = B of this voxel)
+#define RTK_RESTART 0x20000000u   // first segment after a transparent hole (I carries over)
+#define RTK_VOXMASK 0x1FFFFFFFu
+
+#define RTK_END_EXIT 1
+#define RTK_END_CORE 2
+#define RTK_END_LOST 3
+
+namespace rtk {
+
+// Grid geometry as seen by the geometry kernels (device pointers).
+struct GeomDev {
+    int coord, n1, n2, n3, nphi, inner_bc, nvox;
+    const double *e1, *e2, *e3;
+    const double *ct;          // cos(theta_j), j = 0..n2 (spherical)
+    const double *ctm, *stm;   // cos/sin of theta mid-points (spherical)
+    const double *cp, *sp;     // cos/sin of phi_k, k = 0..nphi-1
+    const double *cpm, *spm;   // cos/sin of phi mid-points
+};
+
+// ---- geometry (geom.cu, compiled without FMA contraction) ----
+// Marks every voxel hit by the characteristics of the boundary and core voxels.
+cudaError_t geom_mark_boundary(const GeomDev &G, const double *dirs, int w0, int nw, uint32_t *hit, int words,
+                               int *lost, cudaStream_t st);
+// Coverage completion in increasing voxel order, one warp per solid angle.
+cudaError_t geom_complete(const GeomDev &G, const double *dirs, int w0, int nw, uint32_t *hit, uint32_t *comp,
+                          int words, int32_t *scratch, int cap, int *lost, cudaStream_t st);
+cudaError_t geom_count_rays(const GeomDev &G, const double *dirs, int n_ang, const uint32_t *comp, int words,
+                            int32_t *counts, cudaStream_t st);
+cudaError_t geom_list_rays(const GeomDev &G, const double *dirs, int n_ang, const uint32_t *comp, int words,
+                           const int64_t *ang_ray_off, int32_t *ray_origin, int32_t *ray_angle, cudaStream_t st);
+cudaError_t geom_count_segs(const GeomDev &G, const double *dirs, int64_t n_rays, const int32_t *ray_origin,
+                            const int32_t *ray_angle, int32_t *nseg, int32_t *nback, int *lost, cudaStream_t st);
+cudaError_t geom_write_segs(const GeomDev &G, const double *dirs, int64_t n_rays, const int32_t *ray_origin,
+                            const int32_t *ray_angle, const int64_t *ray_off, const int32_t *nback, uint32_t *vox,
+                            double *len64, float *len32, int *lost, cudaStream_t st);
+int geom_scratch_cap(const GeomDev &G);
+
+// ---- scans and small helpers (scan.cu) ----
+// out[0] = 0, out[i+1] = out[i] + in[i]  (n + 1 outputs); tmp holds >= scan_tmp_elems(n) int64.
+int64_t scan_tmp_elems(int64_t n);
+cudaError_t scan_i32(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t st);
+cudaError_t gather_i64(const int64_t *src, const int64_t *idx, int64_t *dst, int n, cudaStream_t st);
+
+// ---- ownership lists and gather (gather.cu) ----
+cudaError_t csr_build(int nvox, const uint32_t *vox_blk, int64_t nseg_blk, int32_t *counts, int32_t *csr_off,
+                      int32_t *cursor, int32_t *perm_blk, int64_t *tmp, cudaStream_t st);
+cudaError_t csr_invL(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const double *len64_blk,
+                     const int64_t *ang_seg_off, int w0, int nw, int64_t seg_lo, double *invL, cudaStream_t st);
+template <typename P>
+cudaError_t gather_block(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const P *buf,
+                         const int64_t *ang_seg_off, int w0, int nw, int64_t seg_lo, const double *invL,
+                         const double *wt, const double *dirs, double *J, double *Lst, double *Fc, int first,
+                         cudaStream_t st);
+// Ibar, Lbar of one solid angle whose segments are [s_lo, s_hi) of the block.
+cudaError_t gather_angle_range(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const void *buf, int fp32,
+                               int64_t s_lo, int64_t s_hi, const double *invL_w, double *Ibar, double *Lbar,
+                               cudaStream_t st);
+cudaError_t flux_local(const GeomDev &G, const double *Fc, double *F, cudaStream_t st);
+
+// ---- ray march (march.cu) ----
+// One warp per bundle of whole characteristics holding about `chunk` segments.
+template <typename T, typename P>
+cudaError_t march_block(const uint32_t *vox, const T *len, const int64_t *ray_off, int64_t r_lo, int64_t r_hi,
+                        int64_t seg_lo, int64_t nseg, const P *chiS, const T *B, T I_outer, int homog,
+                        int parabolic, P *out, int chunk, cudaStream_t st);
+
+// ---- ALI, Ng, refinement (ali.cu) ----
+cudaError_t pack_chiS64(int nvox, const double *chi, const double *S, double2 *cs, cudaStream_t st);
+cudaError_t pack_chiS32(int nvox, const double *chi, const double *S, const double *B, float2 *cs, float *B32,
+                        cudaStream_t st);
+cudaError_t ali_update(int nvox, double *S, const double *J, const double *Lst, const double *eps, const double *B,
+                       int use_lstar, double *hist_slot, unsigned long long *maxrel, cudaStream_t st);
+// Order-2 Ng from four iterates (y0 newest), weights 1/wref^2 (wref = y0 when null);
+// writes the extrapolation to out only when the 2x2 system is regular (coef[2] = 1).
+cudaError_t ng_extrapolate(int nvox, const double *y0, const double *y1, const double *y2, const double *y3,
+                           const double *wref, double *partial, double *coef, double *out, cudaStream_t st);
+int ng_partial_elems(int nvox);
+cudaError_t residual(int nvox, const double *S, const double *J, const double *Lst, const double *eps,
+                     const double *B, int use_lstar, double *r, unsigned long long *maxrel, cudaStream_t st);
+cudaError_t ali_correction(int nvox, double *delta, const double *Jd, const double *r, const double *Lst,
+                           const double *eps, const double *S, int use_lstar, double *hist_slot,
+                           unsigned long long *maxrel, cudaStream_t st);
+cudaError_t add_inplace(int nvox, double *S, const double *delta, cudaStream_t st);
+cudaError_t fill_const(int n, double *x, double v, cudaStream_t st);
+
+}  // namespace rtk

@@ -1,0 +1,305 @@
+"""ctypes binding of the C ABI in include/rt.h (argument marshalling only).
+
+Every computation happens in the CUDA library librt3d.so; if it is missing
+this module raises instead of falling back to anything else.  Arrays may be
+numpy arrays (host memory) or CUDA tensors (device memory, passed by
+pointer); results come back as numpy arrays unless a device buffer is given.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librt3d.so")
+
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOTCONVERGED, RT_ETIMEOUT, RT_EDEVICE = range(7)
+RT_SPHERICAL, RT_CYLINDRICAL = 0, 1
+RT_CORE_B, RT_TRANSPARENT = 0, 1
+RT_FP64, RT_MIXED = 0, 1
+RT_PARABOLIC, RT_LINEAR = 0, 1
+RT_HOST, RT_DEVICE = 0, 1
+
+_STATUS = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONVERGED", 5: "RT_ETIMEOUT",
+           6: "RT_EDEVICE"}
+
+
+class RtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_STATUS.get(code, code), msg))
+        self.code = code
+
+
+class rt_grid_desc(ctypes.Structure):
+    _fields_ = [("coord", ctypes.c_int), ("n", ctypes.c_int * 3), ("edges", ctypes.c_void_p * 3),
+                ("n_angles", ctypes.c_int), ("dirs", ctypes.c_void_p), ("weights", ctypes.c_void_p),
+                ("inner_bc", ctypes.c_int), ("interp", ctypes.c_int), ("I_outer", ctypes.c_double),
+                ("precision", ctypes.c_int), ("use_lstar", ctypes.c_int), ("ng", ctypes.c_int),
+                ("refine_every", ctypes.c_int), ("angle_block", ctypes.c_int), ("device", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class rt_info(ctypes.Structure):
+    _fields_ = [("n_vox", ctypes.c_int64), ("n_angles", ctypes.c_int64), ("n_rays", ctypes.c_int64),
+                ("n_segments", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("n_blocks", ctypes.c_int32),
+                ("angle_block", ctypes.c_int32), ("lost_rays", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("geometry_ms", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+
+
+def load():
+    """Load librt3d.so (built by paper_0903_1949_gb300.build); raise if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("librt3d.so not found at %s: build it first (paper_0903_1949_gb300.build.build())"
+                           % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    L.rt_last_error.restype = ctypes.c_char_p
+    L.rt_last_error.argtypes = []
+    sig = {
+        "rt_grid_create": [ctypes.POINTER(_P), ctypes.POINTER(rt_grid_desc)],
+        "rt_grid_destroy": [_P],
+        "rt_get_info": [_P, ctypes.POINTER(rt_info)],
+        "rt_set_opacity": [_P, _P, _P, _P, _I],
+        "rt_set_S": [_P, _P, _I],
+        "rt_formal_solution": [_P],
+        "rt_formal_solution_ex": [_P, _I, _I],
+        "rt_ali_step": [_P, ctypes.POINTER(ctypes.c_double)],
+        "rt_solve": [_P, ctypes.c_double, _I, ctypes.POINTER(_I)],
+        "rt_get_J": [_P, _P, _I],
+        "rt_get_S": [_P, _P, _I],
+        "rt_get_Lstar": [_P, _P, _I],
+        "rt_get_flux": [_P, _P, _I],
+        "rt_get_history": [_P, _P, _I, ctypes.POINTER(_I)],
+        "rt_get_crossings": [_P, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _P, _P, _P,
+                             _P, _P, _P],
+        "rt_fs_angles": [_P, _P, _I, _I, _P, _P, _I],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = _I
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != RT_OK:
+        raise RtError(rc, load().rt_last_error().decode())
+    return rc
+
+
+def _ptr(x):
+    """(pointer, where, keepalive) of a host numpy array or a CUDA tensor of float64."""
+    if hasattr(x, "data_ptr") and getattr(x, "is_cuda", False):
+        if str(x.dtype) != "torch.float64" or not x.is_contiguous():
+            raise TypeError("device arrays must be contiguous float64 CUDA tensors")
+        return ctypes.c_void_p(x.data_ptr()), RT_DEVICE, x
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    return ctypes.c_void_p(a.ctypes.data), RT_HOST, a
+
+
+# ---- the C ABI, one function per entry point ----------------------------------
+
+def rt_last_error():
+    return load().rt_last_error().decode()
+
+
+def rt_grid_create(coord, edges, dirs, weights, inner_bc=RT_CORE_B, interp=RT_PARABOLIC, I_outer=0.0,
+                   precision=RT_FP64, use_lstar=True, ng=True, refine_every=0, angle_block=0, device=0, stream=None):
+    L = load()
+    keep = [np.ascontiguousarray(e, dtype=np.float64) for e in edges]
+    dirs = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 3))
+    wts = np.ascontiguousarray(weights, dtype=np.float64)
+    d = rt_grid_desc()
+    d.coord = int(coord)
+    for a in range(3):
+        d.n[a] = len(keep[a]) - 1
+        d.edges[a] = keep[a].ctypes.data
+    d.n_angles = len(wts)
+    d.dirs = dirs.ctypes.data
+    d.weights = wts.ctypes.data
+    d.inner_bc, d.interp, d.I_outer = int(inner_bc), int(interp), float(I_outer)
+    d.precision, d.use_lstar, d.ng = int(precision), 1 if use_lstar else 0, 1 if ng else 0
+    d.refine_every, d.angle_block, d.device = int(refine_every), int(angle_block), int(device)
+    d.stream = stream if stream else None
+    h = ctypes.c_void_p()
+    _check(L.rt_grid_create(ctypes.byref(h), ctypes.byref(d)))
+    return h
+
+
+def rt_grid_destroy(h):
+    return _check(load().rt_grid_destroy(h))
+
+
+def rt_get_info(h):
+    info = rt_info()
+    _check(load().rt_get_info(h, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in rt_info._fields_}
+
+
+def rt_set_opacity(h, chi, eps, B):
+    pc, wc, k1 = _ptr(chi)
+    pe, we, k2 = _ptr(eps)
+    pb, wb, k3 = _ptr(B)
+    if not (wc == we == wb):
+        raise TypeError("chi, eps and B must live in the same memory space")
+    return _check(load().rt_set_opacity(h, pc, pe, pb, wc))
+
+
+def rt_set_S(h, S):
+    p, w, k = _ptr(S)
+    return _check(load().rt_set_S(h, p, w))
+
+
+def rt_formal_solution(h):
+    return _check(load().rt_formal_solution(h))
+
+
+def rt_formal_solution_ex(h, precision, homog=False):
+    return _check(load().rt_formal_solution_ex(h, int(precision), 1 if homog else 0))
+
+
+def rt_ali_step(h):
+    rel = ctypes.c_double()
+    _check(load().rt_ali_step(h, ctypes.byref(rel)))
+    return rel.value
+
+
+def rt_solve(h, tol, max_iter):
+    it = ctypes.c_int()
+    rc = load().rt_solve(h, float(tol), int(max_iter), ctypes.byref(it))
+    if rc not in (RT_OK, RT_ENOTCONVERGED):
+        _check(rc)
+    return it.value, rc == RT_OK
+
+
+def _get(fn, h, n, out):
+    if out is None:
+        out = np.empty(n)
+    p, w, k = _ptr(out)
+    _check(fn(h, p, w))
+    return out
+
+
+def rt_get_J(h, n_vox, out=None):
+    return _get(load().rt_get_J, h, n_vox, out)
+
+
+def rt_get_S(h, n_vox, out=None):
+    return _get(load().rt_get_S, h, n_vox, out)
+
+
+def rt_get_Lstar(h, n_vox, out=None):
+    return _get(load().rt_get_Lstar, h, n_vox, out)
+
+
+def rt_get_flux(h, n_vox, out=None):
+    f = _get(load().rt_get_flux, h, 3 * n_vox, out)
+    return f.reshape(n_vox, 3) if isinstance(f, np.ndarray) else f
+
+
+def rt_get_history(h):
+    n = ctypes.c_int()
+    _check(load().rt_get_history(h, None, 0, ctypes.byref(n)))
+    buf = np.empty(max(1, n.value))
+    _check(load().rt_get_history(h, ctypes.c_void_p(buf.ctypes.data), n.value, ctypes.byref(n)))
+    return buf[:n.value]
+
+
+def rt_get_crossings(h, omega):
+    nr, ns = ctypes.c_int64(), ctypes.c_int64()
+    L = load()
+    _check(L.rt_get_crossings(h, int(omega), ctypes.byref(nr), ctypes.byref(ns), None, None, None, None, None, None))
+    nr, ns = nr.value, ns.value
+    out = dict(ray_off=np.empty(nr + 1, np.int32), ray_origin=np.empty(nr, np.int32), ray_core=np.empty(nr, np.int32),
+               vox=np.empty(ns, np.int32), len=np.empty(ns, np.float64), restart=np.empty(ns, np.uint8))
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(L.rt_get_crossings(h, int(omega), ctypes.byref(a), ctypes.byref(b),
+                              *(ctypes.c_void_p(out[k].ctypes.data)
+                                for k in ("ray_off", "ray_origin", "ray_core", "vox", "len", "restart"))))
+    return out
+
+
+def rt_fs_angles(h, omegas, precision, n_vox):
+    om = np.ascontiguousarray(omegas, dtype=np.int32)
+    Ib = np.empty((len(om), n_vox))
+    Lb = np.empty((len(om), n_vox))
+    _check(load().rt_fs_angles(h, ctypes.c_void_p(om.ctypes.data), len(om), int(precision),
+                               ctypes.c_void_p(Ib.ctypes.data), ctypes.c_void_p(Lb.ctypes.data), RT_HOST))
+    return Ib, Lb
+
+
+class Grid:
+    """Owning handle around rt_grid with numpy-friendly accessors."""
+
+    def __init__(self, coord, edges, dirs, weights, **kw):
+        self.n = tuple(len(e) - 1 for e in edges)
+        self.nvox = int(np.prod(self.n))
+        self.n_ang = len(weights)
+        self.h = rt_grid_create(coord, edges, dirs, weights, **kw)
+
+    def close(self):
+        if self.h:
+            rt_grid_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return rt_get_info(self.h)
+
+    def set_opacity(self, chi, eps, B):
+        rt_set_opacity(self.h, chi, eps, B)
+
+    def set_S(self, S):
+        rt_set_S(self.h, S)
+
+    def formal_solution(self, precision=None, homog=False):
+        if precision is None and not homog:
+            rt_formal_solution(self.h)
+        else:
+            rt_formal_solution_ex(self.h, RT_FP64 if precision is None else precision, homog)
+
+    def ali_step(self):
+        return rt_ali_step(self.h)
+
+    def solve(self, tol=1e-8, max_iter=1000):
+        return rt_solve(self.h, tol, max_iter)
+
+    def J(self, out=None):
+        return rt_get_J(self.h, self.nvox, out)
+
+    def S(self, out=None):
+        return rt_get_S(self.h, self.nvox, out)
+
+    def Lstar(self, out=None):
+        return rt_get_Lstar(self.h, self.nvox, out)
+
+    def flux(self, out=None):
+        return rt_get_flux(self.h, self.nvox, out)
+
+    def history(self):
+        return rt_get_history(self.h)
+
+    def crossings(self, omega):
+        return rt_get_crossings(self.h, omega)
+
+    def fs_angles(self, omegas, precision=RT_FP64):
+        return rt_fs_angles(self.h, omegas, precision, self.nvox)

@@ -1,0 +1,87 @@
+"""The C-ABI library builds, loads and exports every entry point of include/rt.h;
+argument validation answers without touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_0903_1949_gb300 import build as B
+from paper_0903_1949_gb300 import inputs as I
+from paper_0903_1949_gb300 import rt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return rt.load()
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "rt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rt_[A-Za-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_names_match_abi(lib):
+    for n in declared():
+        assert hasattr(rt, n), n
+
+
+def _desc(**over):
+    e = I.sph_edges(4, 3, 5)
+    dirs, w = I.angle_set(2, 2)
+    kw = dict(coord=I.SPHERICAL, edges=e, dirs=dirs, weights=w)
+    kw.update(over)
+    return kw
+
+
+@pytest.mark.parametrize("bad", [
+    dict(coord=7),
+    dict(edges=[np.array([1.0, 0.5, 2.0]), I.sph_edges(4, 3, 5)[1], I.sph_edges(4, 3, 5)[2]]),
+    dict(edges=[np.array([0.0, 1.0, 2.0]), I.sph_edges(4, 3, 5)[1], I.sph_edges(4, 3, 5)[2]]),
+    dict(edges=[I.sph_edges(4, 3, 5)[0], np.linspace(0.0, 3.0, 4), I.sph_edges(4, 3, 5)[2]]),
+    dict(edges=[I.sph_edges(4, 3, 5)[0], I.sph_edges(4, 3, 5)[1], np.linspace(0.0, 6.0, 6)]),
+    dict(weights=np.full(4, 0.3)),
+    dict(dirs=np.ones((4, 3))),
+    dict(inner_bc=5),
+    dict(precision=3),
+    dict(angle_block=300),
+    dict(I_outer=-1.0),
+])
+def test_invalid_descriptions_are_rejected(lib, bad):
+    kw = _desc(**bad)
+    with pytest.raises(rt.RtError) as ei:
+        rt.rt_grid_create(**kw)
+    assert ei.value.code == rt.RT_EINVAL
+    assert len(rt.rt_last_error()) > 0
+
+
+def test_zero_angles_rejected(lib):
+    with pytest.raises(rt.RtError) as ei:
+        rt.rt_grid_create(**_desc(dirs=np.zeros((0, 3)), weights=np.zeros(0)))
+    assert ei.value.code == rt.RT_EINVAL
+
+
+def test_null_handles_rejected(lib):
+    assert lib.rt_formal_solution(None) == rt.RT_EINVAL
+    assert lib.rt_ali_step(None, None) == rt.RT_EINVAL
+    assert lib.rt_grid_destroy(None) == rt.RT_OK
+    out = np.zeros(4)
+    assert lib.rt_get_J(None, ctypes.c_void_p(out.ctypes.data), rt.RT_HOST) == rt.RT_EINVAL
+
+
+def test_struct_layout_matches_header(lib):
+    # rt_grid_desc / rt_info sizes as laid out by the C compiler for x86-64 and aarch64
+    assert ctypes.sizeof(rt.rt_grid_desc) == 112
+    assert ctypes.sizeof(rt.rt_info) == 64

@@ -1,0 +1,247 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle.
+
+Acceptance: crossing lists bit-exact (ids, flags and FP64 lengths); FP64
+J, Lambda*, flux and ALI iterates within 1e-12 relative; the FP32 march
+within 1e-5 relative; the mixed-precision solve within 1e-5 of the
+converged FP64 oracle solution.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_0903_1949_gb300 import build as B
+from paper_0903_1949_gb300 import inputs as I
+from paper_0903_1949_gb300 import rt
+from tests.helpers import tiny_problem
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    B.build()
+    rt.load()
+
+
+def pair(p, I_outer=0.0, interp=O.PARABOLIC, **kw):
+    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"], I_outer, interp)
+    g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], I_outer=I_outer,
+                interp=interp, **kw)
+    return o, g
+
+
+def relerr(a, b, floor=0.0):
+    scale = np.maximum(np.abs(b), floor)
+    return float(np.max(np.abs(a - b) / scale))
+
+
+GEOMS = {
+    "sph_core": lambda: tiny_problem(I.SPHERICAL, (7, 5, 9), 4, 4, I.CORE_B),
+    "sph_hole": lambda: tiny_problem(I.SPHERICAL, (6, 7, 5), 4, 4, I.TRANSPARENT),
+    "cyl_hole": lambda: tiny_problem(I.CYLINDRICAL, (6, 7, 5), 4, 4, I.TRANSPARENT),
+    "cyl_core": lambda: tiny_problem(I.CYLINDRICAL, (5, 9, 6), 4, 6, I.CORE_B),
+    "cyl_axis": lambda: tiny_problem(I.CYLINDRICAL, (5, 7, 4), 4, 4, I.TRANSPARENT, R_min=0.0),
+    "sph_1x1x1": lambda: tiny_problem(I.SPHERICAL, (1, 1, 1), 2, 2, I.CORE_B),
+    "cyl_1x1x1": lambda: tiny_problem(I.CYLINDRICAL, (1, 1, 1), 2, 2, I.TRANSPARENT),
+    "sph_ragged": lambda: tiny_problem(I.SPHERICAL, (11, 3, 2), 3, 5, I.CORE_B),
+}
+
+
+def _same_crossings(o, g, w):
+    a = o.angle(w)
+    b = g.crossings(w)
+    assert a["n_lost"] == 0
+    for k in ("ray_off", "ray_origin", "ray_core", "vox", "restart"):
+        assert np.array_equal(a[k].astype(np.int64), b[k].astype(np.int64)), (w, k)
+    # FP64 lengths are bit-identical, not merely close
+    assert np.array_equal(a["len"].view(np.uint64), b["len"].view(np.uint64)), w
+
+
+@pytest.mark.parametrize("name", sorted(GEOMS))
+def test_crossings_bit_exact(name):
+    p = GEOMS[name]()
+    o, g = pair(p)
+    assert g.info()["lost_rays"] == 0
+    for w in range(p["n_ang"]):
+        _same_crossings(o, g, w)
+    g.close()
+
+
+def test_crossings_bit_exact_small_spherical_all_angles():
+    p = I.make_problem("sph17")
+    o, g = pair(p)
+    info = g.info()
+    assert info["lost_rays"] == 0
+    total = 0
+    for w in range(p["n_ang"]):
+        _same_crossings(o, g, w)
+        total += len(o.angle(w)["vox"])
+    assert total == info["n_segments"]
+    g.close()
+
+
+@pytest.mark.parametrize("name,interp,I_outer", [("sph_core", O.PARABOLIC, 0.0), ("sph_hole", O.PARABOLIC, 0.3),
+                                                 ("cyl_hole", O.PARABOLIC, 0.0), ("cyl_core", O.LINEAR, 0.0),
+                                                 ("cyl_axis", O.PARABOLIC, 0.0), ("sph_ragged", O.LINEAR, 0.2)])
+def test_formal_solution_fp64_matches_oracle(name, interp, I_outer):
+    p = GEOMS[name]()
+    o, g = pair(p, I_outer=I_outer, interp=interp)
+    rng = np.random.default_rng(3)
+    S = rng.uniform(0.5, 2.0, p["nvox"])
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    g.set_S(S)
+    g.formal_solution(rt.RT_FP64)
+    J, L, F, miss = o.formal_solution(S, p["chi"], p["B"])
+    assert miss == 0
+    assert relerr(g.J(), J) < TOL64
+    assert relerr(g.Lstar(), L) < TOL64
+    assert float(np.max(np.abs(g.flux() - F))) < TOL64 * float(np.max(np.abs(F)))
+    # homogeneous boundaries: the pure Lambda operator
+    g.formal_solution(rt.RT_FP64, homog=True)
+    Jh, _, _, _ = o.formal_solution(S, p["chi"], p["B"], homog=True)
+    assert relerr(g.J(), Jh) < TOL64
+    # FP32 march
+    g.formal_solution(rt.RT_MIXED)
+    assert relerr(g.J(), J) < TOL32
+    g.close()
+
+
+def test_formal_solution_is_deterministic():
+    p = I.make_problem("sph17")
+    _, g = pair(p)
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    out = []
+    for prec in (rt.RT_FP64, rt.RT_FP64, rt.RT_MIXED, rt.RT_MIXED):
+        g.formal_solution(prec)
+        out.append((g.J(), g.Lstar()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[2][0], out[3][0]) and np.array_equal(out[2][1], out[3][1])
+    g.close()
+
+
+def test_ali_iterates_match_oracle():
+    p = I.make_problem("sph17")
+    o, g = pair(p, ng=True)
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    it, ok = g.solve(p["tol"], 500)
+    assert ok
+    S_o, it_o, hist_o = o.solve(p["chi"], p["eps"], p["B"], tol=p["tol"], max_iter=500)
+    assert it == it_o
+    assert relerr(g.history(), hist_o, 1e-300) < 1e-9
+    assert relerr(g.S(), S_o) < 1e-11
+    g.close()
+
+
+def test_ali_single_step_matches_oracle_update():
+    p = GEOMS["cyl_hole"]()
+    o, g = pair(p, ng=False)
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    S0 = g.S()
+    rel = g.ali_step()
+    J, L, _, _ = o.formal_solution(S0, p["chi"], p["B"])
+    S1, rel_o = O.ali_update(S0, J, L, p["eps"], p["B"])
+    assert relerr(g.S(), S1) < TOL64
+    assert abs(rel - rel_o) <= TOL64 * rel_o
+    g.close()
+
+
+def test_mixed_precision_solve_reaches_fp64_solution():
+    p = I.make_problem("sph17", eps=1e-4, tau=20.0)
+    o, g = pair(p, precision=rt.RT_MIXED, refine_every=32)
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    it, ok = g.solve(1e-10, 3000)
+    assert ok, g.history()[-5:]
+    S_o, it_o, _ = o.solve(p["chi"], p["eps"], p["B"], tol=1e-13, max_iter=5000)
+    assert it_o > 0
+    assert relerr(g.S(), S_o) < TOL32
+    g.formal_solution(rt.RT_FP64)
+    J_o, _, _, _ = o.formal_solution(S_o, p["chi"], p["B"])
+    assert relerr(g.J(), J_o) < TOL32
+    g.close()
+
+
+def test_lambda_iteration_mode():
+    p = GEOMS["sph_core"]()
+    o, g = pair(p, use_lstar=False, ng=False)
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    it, ok = g.solve(1e-9, 2000)
+    S_o, it_o, _ = o.solve(p["chi"], p["eps"], p["B"], tol=1e-9, max_iter=2000, use_lstar=False, ng=False)
+    assert ok and it == it_o
+    assert relerr(g.S(), S_o) < 1e-11
+    g.close()
+
+
+def test_device_pointer_inputs_and_outputs():
+    torch = pytest.importorskip("torch")
+    p = GEOMS["sph_core"]()
+    o, g = pair(p)
+    dev = torch.device("cuda:0")
+    chi = torch.tensor(p["chi"], dtype=torch.float64, device=dev)
+    eps = torch.tensor(p["eps"], dtype=torch.float64, device=dev)
+    Bt = torch.tensor(p["B"], dtype=torch.float64, device=dev)
+    g.set_opacity(chi, eps, Bt)
+    g.formal_solution(rt.RT_FP64)
+    torch.cuda.synchronize()
+    Jd = torch.empty(p["nvox"], dtype=torch.float64, device=dev)
+    g.J(out=Jd)
+    torch.cuda.synchronize()
+    J, _, _, _ = o.formal_solution(p["B"], p["chi"], p["B"])
+    assert relerr(Jd.cpu().numpy(), J) < TOL64
+    g.close()
+
+
+@pytest.fixture(scope="module")
+def sph65():
+    """The paper-sized spherical workload (65x33x65 voxels, 32x32 solid angles), full size on the GPU."""
+    p = I.make_problem("sph65")
+    g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=rt.RT_MIXED)
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    yield p, g
+    g.close()
+
+
+SAMPLED = [0, 1, 341, 517, 1023]
+
+
+def test_full_size_sph65_sampled_crossings(sph65):
+    p, g = sph65
+    info = g.info()
+    assert info["lost_rays"] == 0
+    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"])
+    for w in SAMPLED:
+        _same_crossings(o, g, w)
+        o.free_angle(w)
+
+
+def test_full_size_sph65_sampled_angle_intensities(sph65):
+    p, g = sph65
+    rng = np.random.default_rng(5)
+    S = p["B"] * rng.uniform(0.8, 1.2, p["B"].size)
+    g.set_S(S)
+    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"])
+    Ib64, Lb64 = g.fs_angles(SAMPLED, rt.RT_FP64)
+    Ib32, Lb32 = g.fs_angles(SAMPLED, rt.RT_MIXED)
+    for q, w in enumerate(SAMPLED):
+        Ib, Lb, _, miss = o.fs_angle(w, S, p["chi"], p["B"])
+        assert miss == 0
+        assert relerr(Ib64[q], Ib) < TOL64
+        assert relerr(Lb64[q], Lb) < TOL64
+        assert relerr(Ib32[q], Ib) < TOL32
+        o.free_angle(w)
+
+
+def test_full_size_sph65_J_is_weighted_angle_sum(sph65):
+    """Property at full size: J from the blocked FS equals sum_w wt_w Ibar_w of single-angle solves."""
+    p, g = sph65
+    g.set_S(p["B"])
+    g.formal_solution(rt.RT_FP64)
+    J = g.J()
+    ws = np.arange(0, p["n_ang"], 1)
+    acc = np.zeros(p["nvox"])
+    for c in range(0, len(ws), 128):
+        Ib, _ = g.fs_angles(ws[c:c + 128], rt.RT_FP64)
+        acc += (p["weights"][ws[c:c + 128], None] * Ib).sum(0)
+    assert relerr(J, acc) < 1e-12
