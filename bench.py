@@ -1,0 +1,397 @@
+#!/usr/bin/env python3
+"""Formal-solution throughput on the paper-sized spherical workload.
+
+Workload (default "sph65"): spherical voxel grid 65 x 33 x 65 (r log-spaced
+1..100, regular theta_c, phi_c), 32 x 32 solid angles (Gauss mu x uniform phi),
+chi = chi0 r^-2 with radial tau = 100 and B = 1, both with seeded 20%
+lognormal voxel noise, eps = 1e-4, I = B on characteristics leaving the core,
+0 at the outer boundary.  Synthetic inputs.
+
+One step = one ALI iteration of the mixed-precision path: FP32 ray march
+over all 1024 solid angles, FP64 ownership gather of J / Lambda* / flux,
+FP64 ALI update (+ Ng when four iterates have accumulated).  The metric is
+voxel-angle updates per second (n_vox * n_angles per step).  The crossing
+lists streamed by every step (about 12 GB) are far larger than L2, so no L2
+flush is needed between steps.
+
+Also reported: the FP64 path's step throughput, the kernel roofline of the
+FP32 ray march (event-timed inside the timed region), an end-to-end figure
+through the C ABI with host buffers, the CPU oracle on a bounded sample, and
+an equal-J-error comparison of the mixed and FP64 solvers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "formal-solution voxel·angle updates/s; FP32-mixed vs FP64 at equal J error"
+UNIT = "voxel-angle updates/s"
+DEFAULT_HBM_FALLBACK = 6800.0
+MARCH_BYTES_PER_SEG = 8  # int32 voxel word + fp32 path length streamed per crossing segment
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="sph65")
+    ap.add_argument("--no-equal-error", action="store_true", help="skip the equal-J-error solver comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-angles", type=int, default=48, help="solid angles in the CPU oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def hbm_peak():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return DEFAULT_HBM_FALLBACK, "fallback"
+
+
+def ncu_traffic(segments_per_launch):
+    """DRAM bytes per march launch from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", "march_fp32_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None, None
+    src = open(os.path.join(ROOT, "paper_0903_1949_gb300", "csrc", "march.cu"), "rb").read()
+    if d.get("march_cu_sha256") != hashlib.sha256(src).hexdigest():
+        return None, "stale"
+    return d["dram_bytes_per_segment"] * segments_per_launch, d.get("capture")
+
+
+def workload_text(p):
+    n = p["n"]
+    kind = "spherical" if p["coord"] == 0 else "cylindrical"
+    return "%s: %s %dx%dx%d voxels, %d solid angles" % (p["name"], kind, n[0], n[1], n[2], p["n_ang"])
+
+
+def cpu_oracle_sample(p, n_angles):
+    """Oracle FS of a bounded, evenly spaced sample of solid angles (geometry untimed)."""
+    from oracle import oracle as O
+
+    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"])
+    ws = np.linspace(0, p["n_ang"] - 1, n_angles).astype(int)
+    for w in ws:
+        o.angle(w)
+    S = p["B"].copy()
+    t0 = time.perf_counter()
+    for w in ws:
+        o.fs_angle(w, S, p["chi"], p["B"])
+    dt = time.perf_counter() - t0
+    o.close()
+    nvox = p["chi"].size
+    return {"value": len(ws) * nvox / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "serial FP64 oracle formal solution of %d of the %d solid angles (evenly spaced), "
+                      "%.1f s, geometry excluded" % (len(ws), p["n_ang"], dt)}
+
+
+def run_reference(args):
+    rank, local, world = dist_env()
+    if rank != 0:
+        return
+    from paper_0903_1949_gb300 import inputs as I
+
+    p = I.make_problem(args.workload)
+    from oracle import oracle as O
+
+    O.build()
+    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"])
+    nper = 4
+    ws = np.linspace(0, p["n_ang"] - 1, nper).astype(int)
+    for w in ws:
+        o.angle(w)
+    S = p["B"].copy()
+    for _ in range(args.warmup):
+        for w in ws:
+            o.fs_angle(w, S, p["chi"], p["B"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for w in ws:
+            o.fs_angle(w, S, p["chi"], p["B"])
+    dt = (time.perf_counter() - t0) / args.steps
+    nvox = p["chi"].size
+    val = nper * nvox / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_text(p), "step": "serial CPU oracle formal solution of %d solid angles"
+                       % nper},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d of %d solid angles per step" % (nper, p["n_ang"])},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, local, world = dist_env()
+    import torch
+
+    from paper_0903_1949_gb300 import build as libbuild
+    from paper_0903_1949_gb300 import inputs as I
+    from paper_0903_1949_gb300 import rt
+
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    if rank == 0:
+        libbuild.build()
+    if dist:
+        dist.barrier()
+    rt.load()
+    p = I.make_problem(args.workload)
+    nvox, nang = p["chi"].size, p["n_ang"]
+    units = nvox * nang
+    stream = torch.cuda.current_stream()
+    g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=rt.RT_MIXED,
+                device=local, stream=stream.cuda_stream)
+    info = g.info()
+    assert info["lost_rays"] == 0
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+
+    def barrier_sync():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, k):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier_sync()
+        ev0.record(stream)
+        for _ in range(k):
+            fn()
+        ev1.record(stream)
+        barrier_sync()
+        ms = ev0.elapsed_time(ev1) / k
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # ---- mixed-precision ALI iterations (the headline) ----
+    for _ in range(args.warmup):
+        g.ali_step()
+    clocks = Clocks(local)
+    g.set_timing(True)
+    clocks.start()
+    ms = timed(g.ali_step, args.steps)
+    ck = clocks.stop()
+    tm = g.timing()
+    g.set_timing(False)
+    value = world * units / (ms / 1e3)
+    march_avg_ms = tm["march_ms"] / max(1, tm["march_launches"])
+    seg_per_launch = tm["march_segments"] / max(1, tm["march_launches"])
+    achieved = seg_per_launch * MARCH_BYTES_PER_SEG / (march_avg_ms / 1e3) / 1e9
+    peak, peak_src = hbm_peak()
+    traffic, traffic_src = ncu_traffic(seg_per_launch)
+    launches_per_step = tm["kernel_launches"] / args.steps
+
+    # ---- FP64 path, same step ----
+    g.set_precision(rt.RT_FP64)
+    g.set_S(p["B"])
+    for _ in range(max(1, args.warmup // 3)):
+        g.ali_step()
+    k64 = max(2, args.steps // 4)
+    ms64 = timed(g.ali_step, k64)
+    value64 = world * units / (ms64 / 1e3)
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    g.set_precision(rt.RT_MIXED)
+    S_host = torch.empty(nvox, dtype=torch.float64, pin_memory=True).numpy()
+    J_host = torch.empty(nvox, dtype=torch.float64, pin_memory=True).numpy()
+    S_host[:] = p["B"]
+
+    def e2e_step():
+        g.set_S(S_host)
+        g.ali_step()
+        g.J(out=J_host)
+
+    for _ in range(2):
+        e2e_step()
+    barrier_sync()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier_sync()
+    ms_e2e = (time.perf_counter() - t0) * 1e3 / args.steps
+    if dist:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e = {"value": world * units / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": 8 * nvox,
+           "d2h_bytes_per_step": 8 * nvox, "ms_per_step": ms_e2e,
+           "path": "rt_set_S(pinned host S) + rt_ali_step + rt_get_J(pinned host J) per step"}
+
+    # ---- FP32-mixed vs FP64 at equal J error ----
+    equal = None
+    if not args.no_equal_error and rank == 0:
+        equal = equal_error(g, p, rt, torch)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 march, f64 gather/ALI/Ng", "data": "synthetic",
+            "config": {"workload": workload_text(p), "step": "one ALI iteration, mixed precision: FP32 ray march "
+                       "of all solid angles + FP64 gather + FP64 ALI/Ng update", "voxel_angles_per_step": units,
+                       "segments_per_step": info["n_segments"],
+                       "segments_per_voxel_angle": info["n_segments"] / units,
+                       "angle_block": info["angle_block"], "l2": "inputs larger than L2 (crossing lists %.1f GB "
+                       "streamed per step)" % (info["n_segments"] * 8 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "geometry_ms": info["geometry_ms"], "device_gb": info["device_bytes"] / 1e9},
+            "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "steps": k64,
+                     "mixed_over_fp64": value / value64},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_march<float> (FP32 ray march)",
+                         "algorithmic_bytes": "%d B per crossing segment (voxel word + fp32 length)"
+                                              % MARCH_BYTES_PER_SEG,
+                         "segments_per_launch": seg_per_launch, "avg_launch_ms": march_avg_ms,
+                         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src if peak_src == "measured"
+                         else "fallback 6800 GB/s", "traffic_source": traffic_src,
+                         "march_share_of_step": tm["march_ms"] / (ms * args.steps),
+                         "gather_share_of_step": tm["gather_ms"] / (ms * args.steps)},
+            "e2e": e2e, "gpu_launches": int(tm["kernel_launches"]), "gpu_launches_per_step": launches_per_step,
+            "clocks": ck}
+    if equal is not None:
+        line["equal_error"] = equal
+    if rank == 0 and not args.no_cpu:
+        try:
+            line["cpu_baseline"] = cpu_oracle_sample(p, args.cpu_angles)
+        except Exception as exc:  # the oracle is a baseline, never the product path
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "failed: %s" % exc}
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def equal_error(g, p, rt, torch, target=1e-5):
+    """Time for each path to bring J within `target` (max relative) of a tightly converged FP64 J."""
+    nvox = p["chi"].size
+    # reference: FP64 ALI to a tight tolerance
+    g.set_precision(rt.RT_FP64)
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    t0 = time.perf_counter()
+    Js, times = [], []
+    it_ref = 0
+    for it in range(1, 3001):
+        rel = g.ali_step()
+        times.append(time.perf_counter() - t0)
+        Js.append(g.J())
+        it_ref = it
+        if rel < 1e-12:
+            break
+    g.formal_solution(rt.RT_FP64)
+    J_ref = g.J()
+    err = [float(np.max(np.abs(J - J_ref) / np.abs(J_ref))) for J in Js]
+    hit = next((q for q, e in enumerate(err) if e <= target), None)
+    fp64_s = times[hit] if hit is not None else None
+    # mixed: refinement solve, tightened until J meets the target
+    out = {"target_max_rel_J_err": target, "reference": "FP64 ALI+Ng converged to max rel dS < 1e-12 "
+           "(%d iterations)" % it_ref, "fp64_iterations_to_target": (hit + 1) if hit is not None else None,
+           "fp64_s": fp64_s}
+    g.set_precision(rt.RT_MIXED)
+    for tol in (1e-7, 1e-8, 1e-9, 1e-10):
+        g.set_opacity(p["chi"], p["eps"], p["B"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_fs, ok = g.solve(tol, 20000)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        g.formal_solution(rt.RT_FP64)
+        e = float(np.max(np.abs(g.J() - J_ref) / np.abs(J_ref)))
+        out.update({"mixed_s": dt, "mixed_tol": tol, "mixed_formal_solutions": n_fs, "mixed_J_err": e,
+                    "mixed_converged": bool(ok)})
+        if e <= target:
+            break
+    if fp64_s and out.get("mixed_J_err", 1.0) <= target:
+        out["speedup_mixed_over_fp64"] = fp64_s / out["mixed_s"]
+    return out
+
+
+if __name__ == "__main__":
+    main()

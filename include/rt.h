@@ -127,6 +127,16 @@ int rt_set_opacity(rt_grid *g, const double *chi, const double *eps, const doubl
 /* Replace the source function S (warm restart). */
 int rt_set_S(rt_grid *g, const double *S, int where);
 
+/* Switch the grid between RT_FP64 and RT_MIXED (affects rt_formal_solution,
+ * rt_ali_step and rt_solve; the crossing lists serve both). */
+int rt_set_precision(rt_grid *g, int precision);
+
+/* Runtime tuning knobs (rt_tune).  RT_TUNE_MARCH_CHUNK: crossing segments per
+ * warp bundle in the ray march, 64..16384 (default 512); a bundle always holds
+ * whole characteristics, so results do not depend on it beyond rounding. */
+#define RT_TUNE_MARCH_CHUNK 1
+int rt_tune(rt_grid *g, int knob, int value);
+
 /* Formal solution from the current S with the grid's precision: J, the
  * diagonal Lambda* and the flux vector per voxel (Sect. 2, 3.2). */
 int rt_formal_solution(rt_grid *g);
@@ -177,6 +187,22 @@ int rt_get_crossings(const rt_grid *g, int omega, int64_t *n_rays, int64_t *n_se
  * the given precision.  Used to compare single solid angles. */
 int rt_fs_angles(rt_grid *g, const int32_t *omegas, int n, int precision, double *Ibar, double *Lbar,
                  int where);
+
+/* Device timing of the hot kernels.  rt_set_timing(g, 1) resets the counters
+ * and brackets every ray-march and gather launch of later calls with CUDA
+ * events on the grid's stream; rt_set_timing(g, 0) stops recording (counters
+ * are kept).  rt_get_timing synchronises the stream and returns the sums. */
+typedef struct rt_timing {
+    double march_ms;          /* summed event time of ray-march launches */
+    double gather_ms;         /* summed event time of ownership-gather launches */
+    int64_t march_launches;
+    int64_t gather_launches;
+    int64_t march_segments;   /* crossing segments processed by the timed march launches */
+    int64_t kernel_launches;  /* every kernel this library launched on the grid since the reset */
+} rt_timing;
+
+int rt_set_timing(rt_grid *g, int enable);
+int rt_get_timing(rt_grid *g, rt_timing *t);
 
 #ifdef __cplusplus
 }

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librt3d.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["geom.cu", "scan.cu", "gather.cu", "march.cu", "ali.cu", "rt_api.cu"]
+SOURCES = sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
 EXTRA = {"geom.cu": ["-fmad=false"]}
 
 
@@ -34,7 +34,8 @@ def _stale(out, deps):
 
 def build(force=False, verbose=False, ptxas_info=False):
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "rt_internal.h"), os.path.join(ROOT, "include", "rt.h")]
+    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    headers.append(os.path.join(ROOT, "include", "rt.h"))
     base = [nvcc(), *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
             "-I", os.path.join(ROOT, "include"), "-I", CSRC]
     if ptxas_info:

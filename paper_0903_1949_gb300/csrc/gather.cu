@@ -18,6 +18,7 @@ namespace {
 
 constexpr double FOUR_PI = 12.566370614359172953850573533118;
 constexpr int MAX_BLOCK_ANGLES = 256;
+constexpr int UNIT_LEN = 512;  // ownership-list entries per gather work unit
 
 __global__ void k_count_vox(const uint32_t *vox, int64_t n, int32_t *counts)
 {
@@ -88,72 +89,6 @@ __global__ void k_invL(int nvox, const int32_t *off, const int32_t *perm, const 
 }
 
 template <typename P>
-__global__ void __launch_bounds__(256) k_gather(int nvox, const int32_t *__restrict__ off, const int32_t *__restrict__ perm,
-                                                const P *__restrict__ buf, const int64_t *__restrict__ ang_seg_off, int w0,
-                                                int nw, int64_t seg_lo, const double *__restrict__ invL,
-                                                const double *__restrict__ wt, const double *__restrict__ dirs,
-                                                double *J, double *Lst, double *Fc, int first)
-{
-    __shared__ int64_t soff[MAX_BLOCK_ANGLES + 1];
-    __shared__ double swt[MAX_BLOCK_ANGLES], sdir[3 * MAX_BLOCK_ANGLES];
-    for (int q = threadIdx.x; q <= nw; q += blockDim.x) soff[q] = ang_seg_off[w0 + q] - seg_lo;
-    for (int q = threadIdx.x; q < nw; q += blockDim.x) {
-        swt[q] = wt[w0 + q];
-        sdir[3 * q] = dirs[3 * (w0 + q)];
-        sdir[3 * q + 1] = dirs[3 * (w0 + q) + 1];
-        sdir[3 * q + 2] = dirs[3 * (w0 + q) + 2];
-    }
-    __syncthreads();
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nvox) return;
-    int lo = off[v], hi = off[v + 1];
-    int q = 0;
-    int64_t next = soff[1];
-    double aI = 0.0, aL = 0.0;
-    double j = 0.0, l = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
-    for (int e = lo; e < hi; ++e) {
-        int s = perm[e];
-        while (s >= next && q < nw) {
-            double il = invL[(int64_t)(w0 + q) * nvox + v];
-            double Ib = aI * il, wq = swt[q];
-            j += wq * Ib;
-            l += wq * (aL * il);
-            fx += wq * sdir[3 * q] * Ib;
-            fy += wq * sdir[3 * q + 1] * Ib;
-            fz += wq * sdir[3 * q + 2] * Ib;
-            aI = 0.0;
-            aL = 0.0;
-            ++q;
-            next = (q < nw) ? soff[q + 1] : INT64_MAX;
-        }
-        P val = buf[s];
-        aI += (double)val.x;
-        aL += (double)val.y;
-    }
-    if (q < nw) {
-        double il = invL[(int64_t)(w0 + q) * nvox + v];
-        double Ib = aI * il, wq = swt[q];
-        j += wq * Ib;
-        l += wq * (aL * il);
-        fx += wq * sdir[3 * q] * Ib;
-        fy += wq * sdir[3 * q + 1] * Ib;
-        fz += wq * sdir[3 * q + 2] * Ib;
-    }
-    if (!first) {
-        j += J[v];
-        l += Lst[v];
-        fx += Fc[3 * (int64_t)v];
-        fy += Fc[3 * (int64_t)v + 1];
-        fz += Fc[3 * (int64_t)v + 2];
-    }
-    J[v] = j;
-    Lst[v] = l;
-    Fc[3 * (int64_t)v] = fx;
-    Fc[3 * (int64_t)v + 1] = fy;
-    Fc[3 * (int64_t)v + 2] = fz;
-}
-
-template <typename P>
 __global__ void k_gather_angle(int nvox, const int32_t *off, const int32_t *perm, const P *buf, int64_t s_lo,
                                int64_t s_hi, const double *invL_w, double *Ibar, double *Lbar)
 {
@@ -194,6 +129,114 @@ __global__ void k_flux_local(GeomDev G, const double *Fc, double *F)
     F[3 * (int64_t)v + 2] = e2x * x + e2y * y + e2z * z;
 }
 
+// Work units: every ownership list is cut into pieces of at most UNIT_LEN
+// entries so one warp never walks more than UNIT_LEN / 32 steps, whatever
+// the visit count of the voxel (outer voxels on the line of sight through the
+// core collect thousands of visits per solid angle).
+__global__ void k_unit_count(int nvox, const int32_t *off, int32_t *nu)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    int len = off[v + 1] - off[v];
+    nu[v] = len <= UNIT_LEN ? 1 : (len + UNIT_LEN - 1) / UNIT_LEN;
+}
+
+__global__ void k_unit_fill(int nvox, const int32_t *off, const int64_t *ufirst, int32_t *urow, int32_t *ubeg)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    int64_t u0 = ufirst[v], u1 = ufirst[v + 1];
+    for (int64_t u = u0; u < u1; ++u) {
+        urow[u] = v;
+        ubeg[u] = off[v] + (int32_t)((u - u0) * UNIT_LEN);
+    }
+}
+
+// One warp per work unit: weighted sums of the unit's entries,
+//   J += wt_q / L_qv * (l I),  Lambda* += wt_q / L_qv * (l lambda),  F += n_q * (J term),
+// reduced across the warp in a fixed shuffle order.
+template <typename P>
+__global__ void __launch_bounds__(256) k_gather_units(int nvox, int64_t nunits, const int32_t *__restrict__ urow,
+                                                      const int32_t *__restrict__ ubeg, const int32_t *__restrict__ off,
+                                                      const int32_t *__restrict__ perm, const P *__restrict__ buf,
+                                                      const int64_t *__restrict__ ang_seg_off, int w0, int nw,
+                                                      int64_t seg_lo, const double *__restrict__ invL,
+                                                      const double *__restrict__ wt, const double *__restrict__ dirs,
+                                                      double *__restrict__ part)
+{
+    __shared__ int32_t soff[MAX_BLOCK_ANGLES + 1];
+    __shared__ double swt[MAX_BLOCK_ANGLES], sdir[3 * MAX_BLOCK_ANGLES];
+    for (int q = threadIdx.x; q <= nw; q += blockDim.x) soff[q] = (int32_t)(ang_seg_off[w0 + q] - seg_lo);
+    for (int q = threadIdx.x; q < nw; q += blockDim.x) {
+        swt[q] = wt[w0 + q];
+        sdir[3 * q] = dirs[3 * (w0 + q)];
+        sdir[3 * q + 1] = dirs[3 * (w0 + q) + 1];
+        sdir[3 * q + 2] = dirs[3 * (w0 + q) + 2];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (u >= nunits) return;
+    const int v = urow[u];
+    const int e0 = ubeg[u];
+    const int e1 = (u + 1 < nunits && urow[u + 1] == v) ? ubeg[u + 1] : off[v + 1];
+    double aj = 0.0, al = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+    for (int e = e0 + lane; e < e1; e += 32) {
+        int s = perm[e];
+        int lo = 0, hi = nw;  // angle of segment s: soff[q] <= s < soff[q+1]
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (soff[mid] <= s) lo = mid;
+            else hi = mid;
+        }
+        double f = swt[lo] * invL[(int64_t)(w0 + lo) * nvox + v];
+        P val = buf[s];
+        double cj = f * (double)val.x;
+        aj += cj;
+        al += f * (double)val.y;
+        fx += sdir[3 * lo] * cj;
+        fy += sdir[3 * lo + 1] * cj;
+        fz += sdir[3 * lo + 2] * cj;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        aj += __shfl_xor_sync(0xffffffffu, aj, o);
+        al += __shfl_xor_sync(0xffffffffu, al, o);
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    }
+    if (lane == 0) {
+        double *o = part + 5 * u;
+        o[0] = aj; o[1] = al; o[2] = fx; o[3] = fy; o[4] = fz;
+    }
+}
+
+// Thread per voxel: add the voxel's unit sums in unit order to J, Lambda*, F.
+__global__ void k_gather_rows(int nvox, const int64_t *__restrict__ ufirst, const double *__restrict__ part, double *J,
+                              double *Lst, double *Fc, int first)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    double j = 0.0, l = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+    for (int64_t u = ufirst[v]; u < ufirst[v + 1]; ++u) {
+        const double *o = part + 5 * u;
+        j += o[0]; l += o[1]; fx += o[2]; fy += o[3]; fz += o[4];
+    }
+    if (!first) {
+        j += J[v];
+        l += Lst[v];
+        fx += Fc[3 * (int64_t)v];
+        fy += Fc[3 * (int64_t)v + 1];
+        fz += Fc[3 * (int64_t)v + 2];
+    }
+    J[v] = j;
+    Lst[v] = l;
+    Fc[3 * (int64_t)v] = fx;
+    Fc[3 * (int64_t)v + 1] = fy;
+    Fc[3 * (int64_t)v + 2] = fz;
+}
+
 int grid_for(int64_t n, int threads)
 {
     int64_t b = (n + threads - 1) / threads;
@@ -229,15 +272,32 @@ cudaError_t csr_invL(int nvox, const int32_t *csr_off, const int32_t *perm_blk, 
     return cudaGetLastError();
 }
 
+cudaError_t gather_units_build(int nvox, const int32_t *csr_off, int32_t *nu, int64_t *ufirst, int64_t *tmp,
+                               cudaStream_t st)
+{
+    k_unit_count<<<(nvox + 255) / 256, 256, 0, st>>>(nvox, csr_off, nu);
+    return scan_i32(nu, ufirst, nvox, tmp, st);
+}
+
+cudaError_t gather_units_fill(int nvox, const int32_t *csr_off, const int64_t *ufirst, int32_t *urow, int32_t *ubeg,
+                              cudaStream_t st)
+{
+    k_unit_fill<<<(nvox + 255) / 256, 256, 0, st>>>(nvox, csr_off, ufirst, urow, ubeg);
+    return cudaGetLastError();
+}
+
 template <typename P>
 cudaError_t gather_block(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const P *buf,
                          const int64_t *ang_seg_off, int w0, int nw, int64_t seg_lo, const double *invL,
-                         const double *wt, const double *dirs, double *J, double *Lst, double *Fc, int first,
-                         cudaStream_t st)
+                         const double *wt, const double *dirs, const int32_t *urow, const int32_t *ubeg,
+                         const int64_t *ufirst, int64_t nunits, double *part, double *J, double *Lst, double *Fc,
+                         int first, cudaStream_t st)
 {
     if (nw > MAX_BLOCK_ANGLES) return cudaErrorInvalidValue;
-    k_gather<P><<<(nvox + 255) / 256, 256, 0, st>>>(nvox, csr_off, perm_blk, buf, ang_seg_off, w0, nw, seg_lo, invL,
-                                                    wt, dirs, J, Lst, Fc, first);
+    int64_t blocks = (nunits * 32 + 255) / 256;
+    k_gather_units<P><<<(unsigned)blocks, 256, 0, st>>>(nvox, nunits, urow, ubeg, csr_off, perm_blk, buf, ang_seg_off,
+                                                        w0, nw, seg_lo, invL, wt, dirs, part);
+    k_gather_rows<<<(nvox + 255) / 256, 256, 0, st>>>(nvox, ufirst, part, J, Lst, Fc, first);
     return cudaGetLastError();
 }
 
@@ -261,10 +321,12 @@ cudaError_t flux_local(const GeomDev &G, const double *Fc, double *F, cudaStream
 }
 
 template cudaError_t gather_block<float2>(int, const int32_t *, const int32_t *, const float2 *, const int64_t *, int,
-                                          int, int64_t, const double *, const double *, const double *, double *,
-                                          double *, double *, int, cudaStream_t);
+                                          int, int64_t, const double *, const double *, const double *, const int32_t *,
+                                          const int32_t *, const int64_t *, int64_t, double *, double *, double *,
+                                          double *, int, cudaStream_t);
 template cudaError_t gather_block<double2>(int, const int32_t *, const int32_t *, const double2 *, const int64_t *, int,
-                                           int, int64_t, const double *, const double *, const double *, double *,
-                                           double *, double *, int, cudaStream_t);
+                                           int, int64_t, const double *, const double *, const double *, const int32_t *,
+                                           const int32_t *, const int64_t *, int64_t, double *, double *, double *,
+                                           double *, int, cudaStream_t);
 
 }  // namespace rtk

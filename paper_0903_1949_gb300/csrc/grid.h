@@ -1,0 +1,63 @@
+// grid.h -- host-side state of one rt_grid (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "rt_internal.h"
+
+struct rt_grid {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    int coord = 0, n1 = 0, n2 = 0, n3 = 0, nvox = 0, n_ang = 0, nphi = 0;
+    int inner_bc = 0, interp = 0, precision = 0, use_lstar = 1, ng = 1, refine_every = 16;
+    double I_outer = 0.0;
+    std::vector<double> h_e[3], h_dirs, h_wt;
+    std::vector<void *> allocs;
+    int64_t bytes = 0;
+    rtk::GeomDev G{};
+    double *d_dirs = nullptr, *d_wt = nullptr;
+    int64_t n_rays = 0, n_seg = 0;
+    std::vector<int64_t> h_ang_ray_off, h_ang_seg_off;
+    int64_t *d_ang_seg_off = nullptr, *d_ray_off = nullptr;
+    int32_t *d_ray_origin = nullptr, *d_ray_angle = nullptr;
+    uint32_t *d_vox = nullptr;
+    double *d_len64 = nullptr;
+    float *d_len32 = nullptr;
+    int ablk = 1, nblk = 0;
+    std::vector<int> blk_w0, blk_nw;
+    int64_t max_blk_seg = 0;
+    int32_t *d_csr_off = nullptr, *d_perm = nullptr;
+    double *d_invL = nullptr;
+    // gather work units per block: unit voxel / first entry (concatenated), per-voxel unit offsets
+    std::vector<int64_t> h_ubase, h_nunits;
+    int32_t *d_urow = nullptr, *d_ubeg = nullptr;
+    int64_t *d_ufirst = nullptr;
+    double *d_part = nullptr;
+    void *d_segbuf = nullptr;
+    double *d_chi = nullptr, *d_eps = nullptr, *d_B = nullptr, *d_S = nullptr;
+    double *d_J = nullptr, *d_L = nullptr, *d_Fc = nullptr, *d_F = nullptr;
+    double2 *d_cs64 = nullptr;
+    float2 *d_cs32 = nullptr;
+    float *d_B32 = nullptr;
+    double *d_H = nullptr, *d_ng_part = nullptr, *d_ng_coef = nullptr;
+    unsigned long long *d_maxrel = nullptr;
+    double *d_r = nullptr, *d_delta = nullptr, *d_Jd = nullptr, *d_Ld = nullptr, *d_Fcd = nullptr, *d_Lkeep = nullptr;
+    double *h_pin = nullptr;  // pinned scalars read back by the iteration control
+    int *d_lost = nullptr;
+    int lost = 0;
+    double geom_ms = 0.0;
+    int hs[4] = {0, 1, 2, 3};
+    int nh = 0;
+    std::vector<double> history;
+    // kernel timing (rt_set_timing) and launch accounting
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;      // event pool, two per timed launch
+    size_t ev_used = 0;
+    std::vector<int> ev_kind;         // 0 march, 1 gather
+    std::vector<int64_t> ev_segs;
+    int64_t launches = 0;
+    int march_chunk = 512;  // segments per warp bundle (RT_TUNE_MARCH_CHUNK)
+};

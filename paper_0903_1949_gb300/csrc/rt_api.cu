@@ -46,52 +46,16 @@ int fail(int code, const char *fmt, ...)
         if (r_ != RT_OK) return r_; \
     } while (0)
 
-constexpr int MARCH_CHUNK = 512;
 constexpr int64_t BLOCK_SEG_TARGET = 6000000;  // segments per angle block (FP32 pair buffer ~48 MB, L2-resident)
 constexpr int MAX_BLOCK_ANGLES = 256;
 
 }  // namespace
 
-struct rt_grid {
-    int device = 0;
-    cudaStream_t st = nullptr;
-    int coord = 0, n1 = 0, n2 = 0, n3 = 0, nvox = 0, n_ang = 0, nphi = 0;
-    int inner_bc = 0, interp = 0, precision = 0, use_lstar = 1, ng = 1, refine_every = 16;
-    double I_outer = 0.0;
-    std::vector<double> h_e[3], h_dirs, h_wt;
-    std::vector<void *> allocs;
-    int64_t bytes = 0;
-    GeomDev G{};
-    double *d_dirs = nullptr, *d_wt = nullptr;
-    int64_t n_rays = 0, n_seg = 0;
-    std::vector<int64_t> h_ang_ray_off, h_ang_seg_off;
-    int64_t *d_ang_seg_off = nullptr, *d_ray_off = nullptr;
-    int32_t *d_ray_origin = nullptr, *d_ray_angle = nullptr;
-    uint32_t *d_vox = nullptr;
-    double *d_len64 = nullptr;
-    float *d_len32 = nullptr;
-    int ablk = 1, nblk = 0;
-    std::vector<int> blk_w0, blk_nw;
-    int64_t max_blk_seg = 0;
-    int32_t *d_csr_off = nullptr, *d_perm = nullptr;
-    double *d_invL = nullptr;
-    void *d_segbuf = nullptr;
-    double *d_chi = nullptr, *d_eps = nullptr, *d_B = nullptr, *d_S = nullptr;
-    double *d_J = nullptr, *d_L = nullptr, *d_Fc = nullptr, *d_F = nullptr;
-    double2 *d_cs64 = nullptr;
-    float2 *d_cs32 = nullptr;
-    float *d_B32 = nullptr;
-    double *d_H = nullptr, *d_ng_part = nullptr, *d_ng_coef = nullptr;
-    unsigned long long *d_maxrel = nullptr;
-    double *d_r = nullptr, *d_delta = nullptr, *d_Jd = nullptr, *d_Ld = nullptr, *d_Fcd = nullptr, *d_Lkeep = nullptr;
-    double *h_pin = nullptr;  // pinned scalars read back by the iteration control
-    int *d_lost = nullptr;
-    int lost = 0;
-    double geom_ms = 0.0;
-    int hs[4] = {0, 1, 2, 3};
-    int nh = 0;
-    std::vector<double> history;
-};
+namespace rtk {
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace rtk
+
+#include "grid.h"
 
 namespace {
 
@@ -123,6 +87,8 @@ void dfree(rt_grid *g, void *p)
 
 void release(rt_grid *g)
 {
+    for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+    g->ev.clear();
     for (void *p : g->allocs) cudaFree(p);
     g->allocs.clear();
     if (g->h_pin) cudaFreeHost(g->h_pin);
@@ -133,6 +99,31 @@ int sync(rt_grid *g)
 {
     CK(cudaStreamSynchronize(g->st));
     return RT_OK;
+}
+
+// Start event of a timed launch (returns its slot, or -1 when timing is off).
+int tstart(rt_grid *g)
+{
+    if (!g->timing) return -1;
+    if (g->ev_used + 2 > g->ev.size()) {
+        for (int q = 0; q < 64; ++q) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            g->ev.push_back(e);
+        }
+    }
+    int slot = (int)g->ev_used;
+    g->ev_used += 2;
+    cudaEventRecord(g->ev[slot], g->st);
+    return slot;
+}
+
+void tstop(rt_grid *g, int slot, int kind, int64_t segs)
+{
+    if (slot < 0) return;
+    cudaEventRecord(g->ev[slot + 1], g->st);
+    g->ev_kind.push_back(kind);
+    g->ev_segs.push_back(segs);
 }
 
 int check_desc(const rt_grid_desc *d)
@@ -344,12 +335,32 @@ int build_geometry(rt_grid *g)
     RCK(dalloc(g, &cnt, nvox));
     RCK(dalloc(g, &cursor, nvox));
     RCK(dalloc(g, &ctmp, (nvox + 1) + scan_tmp_elems(nvox)));
+    RCK(dalloc(g, &g->d_ufirst, (size_t)g->nblk * (nvox + 1)));
+    g->h_ubase.assign(g->nblk + 1, 0);
+    g->h_nunits.assign(g->nblk, 0);
     for (int b = 0; b < g->nblk; ++b) {
         int w0 = g->blk_w0[b], nw = g->blk_nw[b];
         int64_t lo = g->h_ang_seg_off[w0], ns = g->h_ang_seg_off[w0 + nw] - lo;
         int32_t *off = g->d_csr_off + (size_t)b * (nvox + 1);
         CK(csr_build(nvox, g->d_vox + lo, ns, cnt, off, cursor, g->d_perm + lo, ctmp, g->st));
         CK(csr_invL(nvox, off, g->d_perm + lo, g->d_len64 + lo, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->st));
+        int64_t *uf = g->d_ufirst + (size_t)b * (nvox + 1);
+        CK(gather_units_build(nvox, off, cnt, uf, ctmp, g->st));
+        CK(cudaMemcpyAsync(&g->h_nunits[b], uf + nvox, sizeof(int64_t), cudaMemcpyDeviceToHost, g->st));
+    }
+    RCK(sync(g));
+    int64_t max_units = 0;
+    for (int b = 0; b < g->nblk; ++b) {
+        g->h_ubase[b + 1] = g->h_ubase[b] + g->h_nunits[b];
+        max_units = std::max(max_units, g->h_nunits[b]);
+    }
+    RCK(dalloc(g, &g->d_urow, g->h_ubase[g->nblk]));
+    RCK(dalloc(g, &g->d_ubeg, g->h_ubase[g->nblk]));
+    RCK(dalloc(g, &g->d_part, 5 * (size_t)max_units));
+    for (int b = 0; b < g->nblk; ++b) {
+        const int32_t *off = g->d_csr_off + (size_t)b * (nvox + 1);
+        CK(gather_units_fill(nvox, off, g->d_ufirst + (size_t)b * (nvox + 1), g->d_urow + g->h_ubase[b],
+                             g->d_ubeg + g->h_ubase[b], g->st));
     }
     RCK(sync(g));
     dfree(g, cnt);
@@ -410,26 +421,44 @@ int run_fs(rt_grid *g, int prec, int homog, const double *S_src, double *J, doub
     const int para = g->interp == RT_PARABOLIC;
     if (prec == RT_FP64) CK(pack_chiS64(n, g->d_chi, S_src, g->d_cs64, g->st));
     else CK(pack_chiS32(n, g->d_chi, S_src, g->d_B, g->d_cs32, g->d_B32, g->st));
+    g->launches++;
     for (int b = 0; b < g->nblk; ++b) {
         int w0 = g->blk_w0[b], nw = g->blk_nw[b];
         int64_t r_lo = g->h_ang_ray_off[w0], r_hi = g->h_ang_ray_off[w0 + nw];
         int64_t lo = g->h_ang_seg_off[w0], ns = g->h_ang_seg_off[w0 + nw] - lo;
         const int32_t *off = g->d_csr_off + (size_t)b * (n + 1);
+        int t0, t1;
         if (prec == RT_FP64) {
             double2 *buf = (double2 *)g->d_segbuf;
+            t0 = tstart(g);
             CK(march_block<double, double2>(g->d_vox, g->d_len64, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs64, g->d_B,
-                                            g->I_outer, homog, para, buf, MARCH_CHUNK, g->st));
+                                            g->I_outer, homog, para, buf, g->march_chunk, g->st));
+            tstop(g, t0, 0, ns);
+            t1 = tstart(g);
             CK(gather_block<double2>(n, off, g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->d_wt,
-                                     g->d_dirs, J, L, Fc, b == 0, g->st));
+                                     g->d_dirs, g->d_urow + g->h_ubase[b], g->d_ubeg + g->h_ubase[b],
+                                     g->d_ufirst + (size_t)b * (n + 1), g->h_nunits[b], g->d_part, J, L, Fc, b == 0,
+                                     g->st));
+            tstop(g, t1, 1, ns);
         } else {
             float2 *buf = (float2 *)g->d_segbuf;
+            t0 = tstart(g);
             CK(march_block<float, float2>(g->d_vox, g->d_len32, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs32, g->d_B32,
-                                          (float)g->I_outer, homog, para, buf, MARCH_CHUNK, g->st));
+                                          (float)g->I_outer, homog, para, buf, g->march_chunk, g->st));
+            tstop(g, t0, 0, ns);
+            t1 = tstart(g);
             CK(gather_block<float2>(n, off, g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->d_wt,
-                                    g->d_dirs, J, L, Fc, b == 0, g->st));
+                                     g->d_dirs, g->d_urow + g->h_ubase[b], g->d_ubeg + g->h_ubase[b],
+                                     g->d_ufirst + (size_t)b * (n + 1), g->h_nunits[b], g->d_part, J, L, Fc, b == 0,
+                                     g->st));
+            tstop(g, t1, 1, ns);
         }
+        g->launches += 3;
     }
-    if (F) CK(flux_local(g->G, Fc, F, g->st));
+    if (F) {
+        CK(flux_local(g->G, Fc, F, g->st));
+        g->launches++;
+    }
     return RT_OK;
 }
 
@@ -469,6 +498,7 @@ int ng_maybe(rt_grid *g, double *out, const double *wref)
     const size_t n = g->nvox;
     CK(ng_extrapolate(g->nvox, g->d_H + g->hs[3] * n, g->d_H + g->hs[2] * n, g->d_H + g->hs[1] * n,
                       g->d_H + g->hs[0] * n, wref, g->d_ng_part, g->d_ng_coef, out, g->st));
+    g->launches += 3;
     CK(cudaMemcpyAsync(g->h_pin + 1, g->d_ng_coef + 2, sizeof(double), cudaMemcpyDeviceToHost, g->st));
     RCK(sync(g));
     if (g->h_pin[1] != 0.0) g->nh = 0;
@@ -481,6 +511,7 @@ int ali_step_impl(rt_grid *g, int prec, double *rel_out)
     CK(cudaMemsetAsync(g->d_maxrel, 0, sizeof(unsigned long long), g->st));
     double *slot = g->ng ? ng_append_slot(g) : nullptr;
     CK(ali_update(g->nvox, g->d_S, g->d_J, g->d_L, g->d_eps, g->d_B, g->use_lstar, slot, g->d_maxrel, g->st));
+    g->launches++;
     double rel = 0.0;
     RCK(read_maxrel(g, &rel));
     *rel_out = rel;
@@ -621,6 +652,26 @@ int rt_set_S(rt_grid *g, const double *S, int where)
     return RT_OK;
 }
 
+int rt_tune(rt_grid *g, int knob, int value)
+{
+    if (!g) return fail(RT_EINVAL, "grid is NULL");
+    if (knob == RT_TUNE_MARCH_CHUNK) {
+        if (value < 64 || value > 16384) return fail(RT_EINVAL, "march chunk must be in [64, 16384]");
+        g->march_chunk = value;
+        return RT_OK;
+    }
+    return fail(RT_EINVAL, "unknown tuning knob %d", knob);
+}
+
+int rt_set_precision(rt_grid *g, int precision)
+{
+    if (!g) return fail(RT_EINVAL, "grid is NULL");
+    if (precision != RT_FP64 && precision != RT_MIXED) return fail(RT_EINVAL, "bad precision");
+    g->precision = precision;
+    reset_ng(g);
+    return RT_OK;
+}
+
 int rt_formal_solution_ex(rt_grid *g, int precision, int homog)
 {
     if (!g) return fail(RT_EINVAL, "grid is NULL");
@@ -677,6 +728,7 @@ int rt_solve(rt_grid *g, double tol, int max_iter, int *iters)
         total++;
         CK(cudaMemsetAsync(g->d_maxrel, 0, sizeof(unsigned long long), g->st));
         CK(residual(n, g->d_S, g->d_J, g->d_L, g->d_eps, g->d_B, g->use_lstar, g->d_r, g->d_maxrel, g->st));
+        g->launches++;
         double rel = 0.0;
         RCK(read_maxrel(g, &rel));
         g->history.push_back(rel);
@@ -685,7 +737,10 @@ int rt_solve(rt_grid *g, double tol, int max_iter, int *iters)
         CK(cudaMemcpyAsync(g->d_Lkeep, g->d_L, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->st));
         CK(cudaMemsetAsync(g->d_delta, 0, sizeof(double) * n, g->st));
         reset_ng(g);
-        const double inner_tol = std::max(0.01 * rel, 0.1 * tol);
+        // the correction sweeps stop early only when the update is far below the
+        // outer tolerance; a small per-sweep change alone says little when ALI
+        // converges slowly (thick media, small eps)
+        const double inner_tol = 0.01 * tol;
         for (int k = 0; k < g->refine_every && total < max_iter; ++k) {
             RCK(run_fs(g, RT_MIXED, 1, g->d_delta, g->d_Jd, g->d_Ld, g->d_Fcd, nullptr));
             total++;
@@ -693,12 +748,14 @@ int rt_solve(rt_grid *g, double tol, int max_iter, int *iters)
             double *slot = g->ng ? ng_append_slot(g) : nullptr;
             CK(ali_correction(n, g->d_delta, g->d_Jd, g->d_r, g->d_Lkeep, g->d_eps, g->d_S, g->use_lstar, slot,
                               g->d_maxrel, g->st));
+            g->launches++;
             double rd = 0.0;
             RCK(read_maxrel(g, &rd));
             if (rd < inner_tol) break;
             if (g->ng) RCK(ng_maybe(g, g->d_delta, g->d_S));
         }
         CK(add_inplace(n, g->d_S, g->d_delta, g->st));
+        g->launches++;
     }
     if (iters) *iters = total;
     return fail(RT_ENOTCONVERGED, "no convergence to %g in %d formal solutions", tol, max_iter);
@@ -793,10 +850,10 @@ int rt_fs_angles(rt_grid *g, const int32_t *omegas, int n, int precision, double
             // results of this block are still in the buffer
         } else if (precision == RT_FP64)
             CK(march_block<double, double2>(g->d_vox, g->d_len64, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs64, g->d_B,
-                                            g->I_outer, 0, para, (double2 *)g->d_segbuf, MARCH_CHUNK, g->st));
+                                            g->I_outer, 0, para, (double2 *)g->d_segbuf, g->march_chunk, g->st));
         else
             CK(march_block<float, float2>(g->d_vox, g->d_len32, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs32, g->d_B32,
-                                          (float)g->I_outer, 0, para, (float2 *)g->d_segbuf, MARCH_CHUNK, g->st));
+                                          (float)g->I_outer, 0, para, (float2 *)g->d_segbuf, g->march_chunk, g->st));
         marched = b;
         CK(gather_angle_range(nv, off, g->d_perm + lo, g->d_segbuf, precision == RT_MIXED,
                               g->h_ang_seg_off[w] - lo, g->h_ang_seg_off[w + 1] - lo, g->d_invL + (size_t)w * nv, tI,
@@ -806,6 +863,43 @@ int rt_fs_angles(rt_grid *g, const int32_t *omegas, int n, int precision, double
         CK(cudaMemcpyAsync(Lbar + (size_t)q * nv, tL, sizeof(double) * nv, kind, g->st));
     }
     RCK(sync(g));
+    return RT_OK;
+}
+
+int rt_set_timing(rt_grid *g, int enable)
+{
+    if (!g) return fail(RT_EINVAL, "grid is NULL");
+    CK(cudaSetDevice(g->device));
+    if (enable) {
+        RCK(sync(g));
+        g->ev_used = 0;
+        g->ev_kind.clear();
+        g->ev_segs.clear();
+        g->launches = 0;
+    }
+    g->timing = enable != 0;
+    return RT_OK;
+}
+
+int rt_get_timing(rt_grid *g, rt_timing *t)
+{
+    if (!g || !t) return fail(RT_EINVAL, "NULL argument");
+    CK(cudaSetDevice(g->device));
+    RCK(sync(g));
+    std::memset(t, 0, sizeof(*t));
+    for (size_t q = 0; q < g->ev_kind.size(); ++q) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, g->ev[2 * q], g->ev[2 * q + 1]));
+        if (g->ev_kind[q] == 0) {
+            t->march_ms += ms;
+            t->march_launches++;
+            t->march_segments += g->ev_segs[q];
+        } else {
+            t->gather_ms += ms;
+            t->gather_launches++;
+        }
+    }
+    t->kernel_launches = g->launches;
     return RT_OK;
 }
 

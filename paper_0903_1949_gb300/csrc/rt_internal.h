@@ -19,6 +19,9 @@
 
 namespace rtk {
 
+// Message returned by rt_last_error() on this thread (for other translation units).
+void set_last_error(const char *msg);
+
 // Grid geometry as seen by the geometry kernels (device pointers).
 struct GeomDev {
     int coord, n1, n2, n3, nphi, inner_bc, nvox;
@@ -58,11 +61,19 @@ cudaError_t csr_build(int nvox, const uint32_t *vox_blk, int64_t nseg_blk, int32
                       int32_t *cursor, int32_t *perm_blk, int64_t *tmp, cudaStream_t st);
 cudaError_t csr_invL(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const double *len64_blk,
                      const int64_t *ang_seg_off, int w0, int nw, int64_t seg_lo, double *invL, cudaStream_t st);
+// Work units of one block's ownership lists (pieces of at most 512 entries):
+// nu[v] units per voxel, ufirst = exclusive scan (nvox + 1), then per unit its voxel and first entry.
+cudaError_t gather_units_build(int nvox, const int32_t *csr_off, int32_t *nu, int64_t *ufirst, int64_t *tmp,
+                               cudaStream_t st);
+cudaError_t gather_units_fill(int nvox, const int32_t *csr_off, const int64_t *ufirst, int32_t *urow, int32_t *ubeg,
+                              cudaStream_t st);
+// J, Lambda*, flux (Cartesian) of one block from the per-segment (l I, l lambda); first = 1 overwrites.
 template <typename P>
 cudaError_t gather_block(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const P *buf,
                          const int64_t *ang_seg_off, int w0, int nw, int64_t seg_lo, const double *invL,
-                         const double *wt, const double *dirs, double *J, double *Lst, double *Fc, int first,
-                         cudaStream_t st);
+                         const double *wt, const double *dirs, const int32_t *urow, const int32_t *ubeg,
+                         const int64_t *ufirst, int64_t nunits, double *part, double *J, double *Lst, double *Fc,
+                         int first, cudaStream_t st);
 // Ibar, Lbar of one solid angle whose segments are [s_lo, s_hi) of the block.
 cudaError_t gather_angle_range(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const void *buf, int fp32,
                                int64_t s_lo, int64_t s_hi, const double *invL_w, double *Ibar, double *Lbar,

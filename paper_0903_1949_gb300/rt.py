@@ -19,6 +19,7 @@ RT_CORE_B, RT_TRANSPARENT = 0, 1
 RT_FP64, RT_MIXED = 0, 1
 RT_PARABOLIC, RT_LINEAR = 0, 1
 RT_HOST, RT_DEVICE = 0, 1
+RT_TUNE_MARCH_CHUNK = 1
 
 _STATUS = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONVERGED", 5: "RT_ETIMEOUT",
            6: "RT_EDEVICE"}
@@ -44,6 +45,12 @@ class rt_info(ctypes.Structure):
                 ("n_segments", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("n_blocks", ctypes.c_int32),
                 ("angle_block", ctypes.c_int32), ("lost_rays", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("geometry_ms", ctypes.c_double)]
+
+
+class rt_timing(ctypes.Structure):
+    _fields_ = [("march_ms", ctypes.c_double), ("gather_ms", ctypes.c_double), ("march_launches", ctypes.c_int64),
+                ("gather_launches", ctypes.c_int64), ("march_segments", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
 
 
 _lib = None
@@ -80,6 +87,10 @@ def load():
         "rt_get_crossings": [_P, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _P, _P, _P,
                              _P, _P, _P],
         "rt_fs_angles": [_P, _P, _I, _I, _P, _P, _I],
+        "rt_set_timing": [_P, _I],
+        "rt_set_precision": [_P, _I],
+        "rt_tune": [_P, _I, _I],
+        "rt_get_timing": [_P, ctypes.POINTER(rt_timing)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -236,6 +247,24 @@ def rt_fs_angles(h, omegas, precision, n_vox):
     return Ib, Lb
 
 
+def rt_set_precision(h, precision):
+    return _check(load().rt_set_precision(h, int(precision)))
+
+
+def rt_tune(h, knob, value):
+    return _check(load().rt_tune(h, int(knob), int(value)))
+
+
+def rt_set_timing(h, enable=True):
+    return _check(load().rt_set_timing(h, 1 if enable else 0))
+
+
+def rt_get_timing(h):
+    t = rt_timing()
+    _check(load().rt_get_timing(h, ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in rt_timing._fields_}
+
+
 class Grid:
     """Owning handle around rt_grid with numpy-friendly accessors."""
 
@@ -303,3 +332,15 @@ class Grid:
 
     def fs_angles(self, omegas, precision=RT_FP64):
         return rt_fs_angles(self.h, omegas, precision, self.nvox)
+
+    def set_precision(self, precision):
+        rt_set_precision(self.h, precision)
+
+    def tune(self, knob, value):
+        rt_tune(self.h, knob, value)
+
+    def set_timing(self, enable=True):
+        rt_set_timing(self.h, enable)
+
+    def timing(self):
+        return rt_get_timing(self.h)
