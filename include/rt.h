@@ -188,6 +188,24 @@ int rt_get_crossings(const rt_grid *g, int omega, int64_t *n_rays, int64_t *n_se
 int rt_fs_angles(rt_grid *g, const int32_t *omegas, int n, int precision, double *Ibar, double *Lbar,
                  int where);
 
+/* Formal solution of one solid angle for callers that cannot allocate device
+ * memory at call time: code running inside another framework's memory pool or
+ * under a device-memory budget that is already fully handed out, or a thread
+ * that must not take the CUDA allocator's locks.  The paper has no counterpart;
+ * this is a library service.  The call allocates nothing: its per-segment
+ * scratch is a static device array of 16 MiB inside the library (held by every
+ * GPU that loads it until the process exits), so the solid angle must have at
+ * most 1 Mi crossing segments in RT_FP64 or 2 Mi in RT_MIXED (else RT_EINVAL
+ * with the counts in rt_last_error()).  The grid must exist (rt_grid_create
+ * allocates); Ibar and Lbar are caller-owned DEVICE buffers of n_vox doubles
+ * that receive what rt_fs_angles returns for this angle, from the current S.
+ * Work is queued on the grid's stream and not waited for.  The first call on a
+ * device looks up the scratch's device address; make that first call before any
+ * stream capture.  All calls share the one scratch array, which keeps the last
+ * call's contents (nothing in it needs clearing: every entry read is written
+ * first); calls whose GPU work overlaps (other streams, other threads) race. */
+int rt_fs_angle_noalloc(rt_grid *g, int omega, int precision, double *Ibar, double *Lbar);
+
 /* Device timing of the hot kernels.  rt_set_timing(g, 1) resets the counters
  * and brackets every ray-march and gather launch of later calls with CUDA
  * events on the grid's stream; rt_set_timing(g, 0) stops recording (counters

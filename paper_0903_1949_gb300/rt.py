@@ -90,6 +90,7 @@ def load():
         "rt_set_timing": [_P, _I],
         "rt_set_precision": [_P, _I],
         "rt_tune": [_P, _I, _I],
+        "rt_fs_angle_noalloc": [_P, _I, _I, _P, _P],
         "rt_get_timing": [_P, ctypes.POINTER(rt_timing)],
     }
     for name, args in sig.items():
@@ -249,6 +250,14 @@ def rt_fs_angles(h, omegas, precision, n_vox):
 
 def rt_set_precision(h, precision):
     return _check(load().rt_set_precision(h, int(precision)))
+
+
+def rt_fs_angle_noalloc(h, omega, precision, Ibar_dev, Lbar_dev):
+    """One solid angle's Ibar / Lambda* into caller-owned CUDA tensors; allocates nothing."""
+    if not (getattr(Ibar_dev, "is_cuda", False) and getattr(Lbar_dev, "is_cuda", False)):
+        raise TypeError("rt_fs_angle_noalloc writes device buffers: pass CUDA tensors")
+    return _check(load().rt_fs_angle_noalloc(h, int(omega), int(precision), ctypes.c_void_p(Ibar_dev.data_ptr()),
+                                             ctypes.c_void_p(Lbar_dev.data_ptr())))
 
 
 def rt_tune(h, knob, value):
