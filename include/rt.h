@@ -149,7 +149,11 @@ int rt_formal_solution_ex(rt_grid *g, int precision, int homog);
 /* One ALI iteration: formal solution, S <- S + [(1-eps) J + eps B - S] /
  * (1 - (1-eps) Lambda*), and Ng extrapolation when four iterates have
  * accumulated (if enabled).  *max_rel_dS (may be NULL) receives
- * max_v |dS| / |S_new| of the update. */
+ * max_v |dS| / |S_new| of the update.  Lambda* depends on chi and the path
+ * lengths only, so it is computed by the first iteration after rt_set_opacity
+ * (or taken from an earlier rt_formal_solution of the same or higher
+ * precision) and reused; later iterations compute J alone and leave the flux
+ * of rt_get_flux unchanged (call rt_formal_solution for the flux of S). */
 int rt_ali_step(rt_grid *g, double *max_rel_dS);
 
 /* Iterate to max rel dS < tol.  RT_FP64: plain ALI(+Ng) with the FP64 formal

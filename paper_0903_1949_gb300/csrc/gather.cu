@@ -18,7 +18,7 @@ namespace {
 
 constexpr double FOUR_PI = 12.566370614359172953850573533118;
 constexpr int MAX_BLOCK_ANGLES = 256;
-constexpr int UNIT_LEN = 512;  // ownership-list entries per gather work unit
+constexpr int UNIT_LEN = 32;  // ownership-list entries per gather work unit (one thread each)
 
 __global__ void k_count_vox(const uint32_t *vox, int64_t n, int32_t *counts)
 {
@@ -152,72 +152,172 @@ __global__ void k_unit_fill(int nvox, const int32_t *off, const int64_t *ufirst,
     }
 }
 
-// One warp per work unit: weighted sums of the unit's entries,
-//   J += wt_q / L_qv * (l I),  Lambda* += wt_q / L_qv * (l lambda),  F += n_q * (J term),
-// reduced across the warp in a fixed shuffle order.
-template <typename P>
-__global__ void __launch_bounds__(256) k_gather_units(int nvox, int64_t nunits, const int32_t *__restrict__ urow,
-                                                      const int32_t *__restrict__ ubeg, const int32_t *__restrict__ off,
-                                                      const int32_t *__restrict__ perm, const P *__restrict__ buf,
-                                                      const int64_t *__restrict__ ang_seg_off, int w0, int nw,
-                                                      int64_t seg_lo, const double *__restrict__ invL,
-                                                      const double *__restrict__ wt, const double *__restrict__ dirs,
-                                                      double *__restrict__ part)
+// Compensated (Kahan) FP32 accumulation: the running error term c keeps the
+// sum accurate to about one rounding of the total, independent of its length.
+__device__ __forceinline__ void kadd(float &s, float &c, float x)
+{
+    float y = x - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// A voxel whose list fits one unit is finished by that unit's thread; the
+// units of longer lists leave their sums for k_gather_rows.
+__device__ __forceinline__ void finish_unit(int64_t u, int v, int64_t nunits, const int32_t *urow, double r0, double r1,
+                                            double r2, double r3, double r4, double *part, double *J, double *Lst,
+                                            double *Fc, int first)
+{
+    const bool single = (u == 0 || urow[u - 1] != v) && (u + 1 == nunits || urow[u + 1] != v);
+    if (single) {
+        if (!first) {
+            r0 += J[v];
+            r1 += Lst[v];
+            r2 += Fc[3 * (int64_t)v];
+            r3 += Fc[3 * (int64_t)v + 1];
+            r4 += Fc[3 * (int64_t)v + 2];
+        }
+        J[v] = r0;
+        Lst[v] = r1;
+        Fc[3 * (int64_t)v] = r2;
+        Fc[3 * (int64_t)v + 1] = r3;
+        Fc[3 * (int64_t)v + 2] = r4;
+    } else {
+        double *o = part + 5 * u;
+        o[0] = r0; o[1] = r1; o[2] = r2; o[3] = r3; o[4] = r4;
+    }
+}
+
+// One thread per work unit (at most UNIT_LEN consecutive entries of one
+// voxel's ownership list, sorted by segment hence by solid angle):
+//   J += (wt_q / L_qv) (l I),  Lambda* += (wt_q / L_qv) (l lambda),  F += n_q (J term).
+// FP32 ray march: FP32 weights and Kahan-compensated FP32 sums.
+__global__ void __launch_bounds__(256) k_gather_units32(int nvox, int64_t nunits, const int32_t *__restrict__ urow,
+                                                        const int32_t *__restrict__ order, const int32_t *__restrict__ ulen,
+                                                        const int64_t *__restrict__ gbase, const int32_t *__restrict__ sell,
+                                                        const float2 *__restrict__ buf,
+                                                        const int64_t *__restrict__ ang_seg_off, int w0, int nw,
+                                                        int64_t seg_lo, const float *__restrict__ wL,
+                                                        const double *__restrict__ dirs, double *__restrict__ part,
+                                                        double *J, double *Lst, double *Fc, int first)
 {
     __shared__ int32_t soff[MAX_BLOCK_ANGLES + 1];
-    __shared__ double swt[MAX_BLOCK_ANGLES], sdir[3 * MAX_BLOCK_ANGLES];
+    __shared__ float sdir[3 * MAX_BLOCK_ANGLES];
     for (int q = threadIdx.x; q <= nw; q += blockDim.x) soff[q] = (int32_t)(ang_seg_off[w0 + q] - seg_lo);
-    for (int q = threadIdx.x; q < nw; q += blockDim.x) {
-        swt[q] = wt[w0 + q];
-        sdir[3 * q] = dirs[3 * (w0 + q)];
-        sdir[3 * q + 1] = dirs[3 * (w0 + q) + 1];
-        sdir[3 * q + 2] = dirs[3 * (w0 + q) + 2];
-    }
+    for (int q = threadIdx.x; q < 3 * nw; q += blockDim.x) sdir[q] = (float)dirs[3 * w0 + q];
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (u >= nunits) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nunits) return;
+    const int u = order[i];
     const int v = urow[u];
-    const int e0 = ubeg[u];
-    const int e1 = (u + 1 < nunits && urow[u + 1] == v) ? ubeg[u + 1] : off[v + 1];
-    double aj = 0.0, al = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
-    for (int e = e0 + lane; e < e1; e += 32) {
-        int s = perm[e];
-        int lo = 0, hi = nw;  // angle of segment s: soff[q] <= s < soff[q+1]
+    const int len = ulen[u];
+    const int32_t *lst = sell + gbase[i >> 5] + (i & 31);
+    float sj = 0.f, cj = 0.f, sl = 0.f, cl = 0.f, sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
+    if (len > 0) {
+        int s = lst[0];
+        int lo = 0, hi = nw;
         while (hi - lo > 1) {
             int mid = (lo + hi) >> 1;
             if (soff[mid] <= s) lo = mid;
             else hi = mid;
         }
-        double f = swt[lo] * invL[(int64_t)(w0 + lo) * nvox + v];
-        P val = buf[s];
-        double cj = f * (double)val.x;
-        aj += cj;
-        al += f * (double)val.y;
-        fx += sdir[3 * lo] * cj;
-        fy += sdir[3 * lo + 1] * cj;
-        fz += sdir[3 * lo + 2] * cj;
-    }
+        int q = lo;
+        float f = wL[(int64_t)(w0 + q) * nvox + v];
+        // four entries per step: independent (coalesced) index loads, then buffer loads
+        for (int k = 0; k < len; k += 4) {
+            int ss[4];
+            float2 val[4];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        aj += __shfl_xor_sync(0xffffffffu, aj, o);
-        al += __shfl_xor_sync(0xffffffffu, al, o);
-        fx += __shfl_xor_sync(0xffffffffu, fx, o);
-        fy += __shfl_xor_sync(0xffffffffu, fy, o);
-        fz += __shfl_xor_sync(0xffffffffu, fz, o);
+            for (int j = 0; j < 4; ++j) ss[j] = (k + j < len) ? lst[32 * (k + j)] : -1;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (ss[j] >= 0) val[j] = buf[ss[j]];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (ss[j] < 0) continue;
+                while (ss[j] >= soff[q + 1]) {
+                    ++q;
+                    f = wL[(int64_t)(w0 + q) * nvox + v];
+                }
+                float tj = f * val[j].x;
+                kadd(sj, cj, tj);
+                kadd(sl, cl, f * val[j].y);
+                kadd(sx, cx, sdir[3 * q] * tj);
+                kadd(sy, cy, sdir[3 * q + 1] * tj);
+                kadd(sz, cz, sdir[3 * q + 2] * tj);
+            }
+        }
     }
-    if (lane == 0) {
-        double *o = part + 5 * u;
-        o[0] = aj; o[1] = al; o[2] = fx; o[3] = fy; o[4] = fz;
-    }
+    const double r0 = (double)sj - (double)cj, r1 = (double)sl - (double)cl, r2 = (double)sx - (double)cx,
+                 r3 = (double)sy - (double)cy, r4 = (double)sz - (double)cz;
+    finish_unit(u, v, nunits, urow, r0, r1, r2, r3, r4, part, J, Lst, Fc, first);
 }
 
-// Thread per voxel: add the voxel's unit sums in unit order to J, Lambda*, F.
-__global__ void k_gather_rows(int nvox, const int64_t *__restrict__ ufirst, const double *__restrict__ part, double *J,
-                              double *Lst, double *Fc, int first)
+// FP64 ray march: FP64 weights and sums.
+__global__ void __launch_bounds__(256) k_gather_units64(int nvox, int64_t nunits, const int32_t *__restrict__ urow,
+                                                        const int32_t *__restrict__ order, const int32_t *__restrict__ ulen,
+                                                        const int64_t *__restrict__ gbase, const int32_t *__restrict__ sell,
+                                                        const double2 *__restrict__ buf,
+                                                        const int64_t *__restrict__ ang_seg_off, int w0, int nw,
+                                                        int64_t seg_lo, const double *__restrict__ invL,
+                                                        const double *__restrict__ wt, const double *__restrict__ dirs,
+                                                        double *__restrict__ part, double *J, double *Lst, double *Fc,
+                                                        int first)
 {
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nvox) return;
+    __shared__ int32_t soff[MAX_BLOCK_ANGLES + 1];
+    __shared__ double swt[MAX_BLOCK_ANGLES], sdir[3 * MAX_BLOCK_ANGLES];
+    for (int q = threadIdx.x; q <= nw; q += blockDim.x) soff[q] = (int32_t)(ang_seg_off[w0 + q] - seg_lo);
+    for (int q = threadIdx.x; q < nw; q += blockDim.x) swt[q] = wt[w0 + q];
+    for (int q = threadIdx.x; q < 3 * nw; q += blockDim.x) sdir[q] = dirs[3 * w0 + q];
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nunits) return;
+    const int u = order[i];
+    const int v = urow[u];
+    const int len = ulen[u];
+    const int32_t *lst = sell + gbase[i >> 5] + (i & 31);
+    double aj = 0.0, al = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+    if (len > 0) {
+        int s = lst[0];
+        int lo = 0, hi = nw;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (soff[mid] <= s) lo = mid;
+            else hi = mid;
+        }
+        int q = lo;
+        double f = swt[q] * invL[(int64_t)(w0 + q) * nvox + v];
+        for (int k = 0; k < len; ++k) {
+            s = lst[32 * k];
+            while (s >= soff[q + 1]) {
+                ++q;
+                f = swt[q] * invL[(int64_t)(w0 + q) * nvox + v];
+            }
+            double2 val = buf[s];
+            double tj = f * val.x;
+            aj += tj;
+            al += f * val.y;
+            fx += sdir[3 * q] * tj;
+            fy += sdir[3 * q + 1] * tj;
+            fz += sdir[3 * q + 2] * tj;
+        }
+    }
+    finish_unit(u, v, nunits, urow, aj, al, fx, fy, fz, part, J, Lst, Fc, first);
+}
+
+__global__ void k_make_wL32(int64_t n, int nvox, const double *invL, const double *wt, float *wL)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        wL[i] = (float)(wt[i / nvox] * invL[i]);
+}
+
+// One thread per voxel with more than one unit: add its unit sums in order.
+__global__ void k_gather_rows(int nmulti, const int32_t *__restrict__ multi, const int64_t *__restrict__ ufirst,
+                              const double *__restrict__ part, double *J, double *Lst, double *Fc, int first)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nmulti) return;
+    const int v = multi[i];
     double j = 0.0, l = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
     for (int64_t u = ufirst[v]; u < ufirst[v + 1]; ++u) {
         const double *o = part + 5 * u;
@@ -235,6 +335,291 @@ __global__ void k_gather_rows(int nvox, const int64_t *__restrict__ ufirst, cons
     Fc[3 * (int64_t)v] = fx;
     Fc[3 * (int64_t)v + 1] = fy;
     Fc[3 * (int64_t)v + 2] = fz;
+}
+
+// Voxels whose ownership list needs more than one unit (compacted in voxel order).
+__global__ void k_multi_flags(int nvox, const int64_t *ufirst, int32_t *flag)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < nvox) flag[v] = (ufirst[v + 1] - ufirst[v] > 1) ? 1 : 0;
+}
+
+__global__ void k_multi_fill(int nvox, const int32_t *flag, const int64_t *pos, int32_t *multi)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < nvox && flag[v]) multi[pos[v]] = v;
+}
+
+// Sliced-ELL layout of the work units for coalesced list reads: units are
+// bucketed by length (longest first), cut into groups of 32, and the entries
+// of a group interleaved: entry k of the group's unit t sits at
+// sell[base_g + 32 k + t] (-1 pads short units).  Thread t then reads entry k
+// at consecutive addresses with its 31 neighbours.
+__global__ void k_unit_len(int64_t nunits, const int32_t *urow, const int32_t *ubeg, const int32_t *off, int32_t *ulen,
+                           int32_t *hist)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nunits; u += (int64_t)gridDim.x * blockDim.x) {
+        const int v = urow[u];
+        const int e1 = (u + 1 < nunits && urow[u + 1] == v) ? ubeg[u + 1] : off[v + 1];
+        const int len = e1 - ubeg[u];
+        ulen[u] = len;
+        atomicAdd(hist + (UNIT_LEN - len), 1);
+    }
+}
+
+__global__ void k_hist_scan(int32_t *hist)  // exclusive scan of UNIT_LEN + 1 buckets, in place
+{
+    int run = 0;
+    for (int b = 0; b <= UNIT_LEN; ++b) {
+        int c = hist[b];
+        hist[b] = run;
+        run += c;
+    }
+}
+
+__global__ void k_bucket_fill(int64_t nunits, const int32_t *ulen, int32_t *cursor, int32_t *order)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nunits; u += (int64_t)gridDim.x * blockDim.x) {
+        int pos = atomicAdd(cursor + (UNIT_LEN - ulen[u]), 1);
+        order[pos] = (int32_t)u;
+    }
+}
+
+__global__ void k_group_width(int64_t ngroups, const int32_t *order, const int32_t *ulen, int32_t *gw)
+{
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g < ngroups) gw[g] = 32 * ulen[order[32 * g]];
+}
+
+__global__ void k_sell_fill(int64_t nunits, const int32_t *order, const int32_t *ulen, const int32_t *ubeg,
+                            const int32_t *perm, const int64_t *gbase, int32_t *sell)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nunits; i += (int64_t)gridDim.x * blockDim.x) {
+        const int u = order[i];
+        const int64_t g = i >> 5;
+        const int t = (int)(i & 31);
+        const int width = ulen[order[32 * g]];
+        const int len = ulen[u], e0 = ubeg[u];
+        int32_t *dst = sell + gbase[g] + t;
+        for (int k = 0; k < width; ++k) dst[32 * k] = (k < len) ? perm[e0 + k] : -1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// J-only gather of the ALI iteration.  Lists of at most SHORT_LEN entries are
+// summed by one thread each, from a sliced-ELL copy (voxels sorted by list
+// length, 32 per group, entries interleaved so the 32 threads of a warp read
+// consecutive words); longer lists are cut into chunks of CHUNK_LEN entries,
+// one warp per chunk reading the list coalesced, and the warp that finishes a
+// voxel's last chunk adds the chunk sums in chunk order.
+constexpr int SHORT_LEN = 64;
+constexpr int CHUNK_LEN = 1024;
+
+__global__ void k_jclass(int nvox, const int32_t *off, int32_t *hist, int32_t *longflag, int32_t *nch)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    int L = off[v + 1] - off[v];
+    if (L <= SHORT_LEN) {
+        atomicAdd(hist + (SHORT_LEN - L), 1);
+        longflag[v] = 0;
+        nch[v] = 0;
+    } else {
+        longflag[v] = 1;
+        nch[v] = (L + CHUNK_LEN - 1) / CHUNK_LEN;
+    }
+}
+
+__global__ void k_jhist_scan(int32_t *hist)
+{
+    int run = 0;
+    for (int b = 0; b <= SHORT_LEN; ++b) {
+        int c = hist[b];
+        hist[b] = run;
+        run += c;
+    }
+}
+
+__global__ void k_jshort_fill(int nvox, const int32_t *off, int32_t *cursor, int32_t *jorder)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    int L = off[v + 1] - off[v];
+    if (L <= SHORT_LEN) jorder[atomicAdd(cursor + (SHORT_LEN - L), 1)] = v;
+}
+
+__global__ void k_jwidth(int64_t ngroups, const int32_t *off, const int32_t *jorder, int32_t *gw)
+{
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g < ngroups) {
+        int v = jorder[32 * g];
+        gw[g] = 32 * (off[v + 1] - off[v]);
+    }
+}
+
+__global__ void k_jsell_fill(int64_t nshort, const int32_t *off, const int32_t *jorder, const int32_t *perm,
+                             const int64_t *gbase, int32_t *sell)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nshort; i += (int64_t)gridDim.x * blockDim.x) {
+        const int v = jorder[i];
+        const int64_t g = i >> 5;
+        const int v0 = jorder[32 * g];
+        const int width = off[v0 + 1] - off[v0];
+        const int L = off[v + 1] - off[v], e0 = off[v];
+        int32_t *dst = sell + gbase[g] + (i & 31);
+        for (int k = 0; k < width; ++k) dst[32 * k] = (k < L) ? perm[e0 + k] : -1;
+    }
+}
+
+__global__ void k_jlong_fill(int nvox, const int32_t *off, const int32_t *longflag, const int64_t *lpos,
+                             const int64_t *cpos, int32_t *lrows, int32_t *lfirst, int32_t *crow, int32_t *cbeg,
+                             int32_t *clr)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvox || !longflag[v]) return;
+    const int lr = (int)lpos[v];
+    const int c0 = (int)cpos[v], c1 = (int)cpos[v + 1];
+    lrows[lr] = v;
+    lfirst[lr] = c0;
+    for (int c = c0; c < c1; ++c) {
+        crow[c] = v;
+        cbeg[c] = off[v] + (c - c0) * CHUNK_LEN;
+        clr[c] = lr;
+    }
+}
+
+template <typename T> struct JW;
+template <> struct JW<float> {
+    __device__ static float weight(const float *wL, const double *, const double *, int w, int q, int nvox, int v)
+    {
+        (void)q;
+        return wL[(int64_t)w * nvox + v];
+    }
+};
+template <> struct JW<double> {
+    __device__ static double weight(const float *, const double *swt, const double *invL, int w, int q, int nvox, int v)
+    {
+        return swt[q] * invL[(int64_t)w * nvox + v];
+    }
+};
+
+template <typename T> struct JAcc;
+template <> struct JAcc<float> {  // Kahan-compensated FP32
+    float s = 0.f, c = 0.f;
+    __device__ void add(float x) { kadd(s, c, x); }
+    __device__ double value() const { return (double)s - (double)c; }
+    __device__ void warp_reduce()
+    {
+        for (int o = 16; o > 0; o >>= 1) {
+            float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+            float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+            float t = s + s2;
+            float bb = t - s;
+            float err = (s - (t - bb)) + (s2 - bb);  // s + s2 = t + err exactly
+            c = (c + c2) - err;
+            s = t;
+        }
+    }
+};
+template <> struct JAcc<double> {
+    double s = 0.0;
+    __device__ void add(double x) { s += x; }
+    __device__ double value() const { return s; }
+    __device__ void warp_reduce()
+    {
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+};
+
+__device__ __forceinline__ int angle_of(const int32_t *soff, int nw, int s)
+{
+    int lo = 0, hi = nw;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (soff[mid] <= s) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Blocks [0, nbs) sum short lists (thread per voxel); the rest are warps over chunks of long lists.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gatherJ(int nvox, int64_t nshort, int nbs, const int32_t *__restrict__ off,
+                                                 const int32_t *__restrict__ jorder, const int64_t *__restrict__ jgbase,
+                                                 const int32_t *__restrict__ jsell, int64_t nchunks,
+                                                 const int32_t *__restrict__ crow, const int32_t *__restrict__ cbeg,
+                                                 const int32_t *__restrict__ clr, const int32_t *__restrict__ lfirst,
+                                                 int nlong, int *cnt, double *part, const int32_t *__restrict__ perm,
+                                                 const T *__restrict__ buf, const int64_t *__restrict__ ang_seg_off,
+                                                 int w0, int nw, int64_t seg_lo, const float *__restrict__ wL,
+                                                 const double *__restrict__ invL, const double *__restrict__ wt,
+                                                 double *J, int first)
+{
+    __shared__ int32_t soff[MAX_BLOCK_ANGLES + 1];
+    __shared__ double swt[MAX_BLOCK_ANGLES];
+    for (int q = threadIdx.x; q <= nw; q += blockDim.x) soff[q] = (int32_t)(ang_seg_off[w0 + q] - seg_lo);
+    for (int q = threadIdx.x; q < nw; q += blockDim.x) swt[q] = wt[w0 + q];
+    __syncthreads();
+    if ((int)blockIdx.x < nbs) {
+        const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        if (i >= nshort) return;
+        const int v = jorder[i];
+        const int L = off[v + 1] - off[v];
+        const int32_t *lst = jsell + jgbase[i >> 5] + (i & 31);
+        JAcc<T> acc;
+        if (L > 0) {
+            int q = angle_of(soff, nw, lst[0]);
+            T f = JW<T>::weight(wL, swt, invL, w0 + q, q, nvox, v);
+            for (int k = 0; k < L; k += 4) {
+                int ss[4];
+                T val[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) ss[j] = (k + j < L) ? lst[32 * (k + j)] : -1;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (ss[j] >= 0) val[j] = buf[ss[j]];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (ss[j] < 0) continue;
+                    while (ss[j] >= soff[q + 1]) {
+                        ++q;
+                        f = JW<T>::weight(wL, swt, invL, w0 + q, q, nvox, v);
+                    }
+                    acc.add(f * val[j]);
+                }
+            }
+        }
+        const double r = acc.value();
+        J[v] = first ? r : J[v] + r;
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t c = ((int64_t)(blockIdx.x - nbs) * blockDim.x + threadIdx.x) >> 5;
+    if (c >= nchunks) return;
+    const int v = crow[c];
+    const int e0 = cbeg[c];
+    const int e1 = min(e0 + CHUNK_LEN, off[v + 1]);
+    JAcc<T> acc;
+    for (int e = e0 + lane; e < e1; e += 32) {
+        const int s = perm[e];
+        const int q = angle_of(soff, nw, s);
+        acc.add(JW<T>::weight(wL, swt, invL, w0 + q, q, nvox, v) * buf[s]);
+    }
+    acc.warp_reduce();
+    if (lane == 0) {
+        const int lr = clr[c];
+        __stcg(part + c, acc.value());
+        __threadfence();
+        const int c0 = lfirst[lr], c1 = (lr + 1 < nlong) ? lfirst[lr + 1] : (int)nchunks;
+        if (atomicAdd(cnt + lr, 1) == c1 - c0 - 1) {
+            // last chunk of this voxel: add all chunk sums in chunk order
+            __threadfence();
+            double r = 0.0;
+            for (int cc = c0; cc < c1; ++cc) r += __ldcg(part + cc);
+            J[v] = first ? r : J[v] + r;
+            cnt[lr] = 0;
+        }
+    }
 }
 
 int grid_for(int64_t n, int threads)
@@ -286,18 +671,68 @@ cudaError_t gather_units_fill(int nvox, const int32_t *csr_off, const int64_t *u
     return cudaGetLastError();
 }
 
+cudaError_t make_wL32(int n_ang, int nvox, const double *invL, const double *wt, float *wL, cudaStream_t st)
+{
+    int64_t n = (int64_t)n_ang * nvox;
+    k_make_wL32<<<grid_for(n, 256), 256, 0, st>>>(n, nvox, invL, wt, wL);
+    return cudaGetLastError();
+}
+
 template <typename P>
 cudaError_t gather_block(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const P *buf,
                          const int64_t *ang_seg_off, int w0, int nw, int64_t seg_lo, const double *invL,
-                         const double *wt, const double *dirs, const int32_t *urow, const int32_t *ubeg,
-                         const int64_t *ufirst, int64_t nunits, double *part, double *J, double *Lst, double *Fc,
-                         int first, cudaStream_t st)
+                         const float *wL32, const double *wt, const double *dirs, const int32_t *urow,
+                         const int32_t *ubeg, const int64_t *ufirst, int64_t nunits, const int32_t *multi,
+                         int nmulti, const int32_t *order, const int32_t *ulen, const int64_t *gbase,
+                         const int32_t *sell, double *part, double *J, double *Lst, double *Fc, int first,
+                         cudaStream_t st)
 {
+    (void)csr_off;
+    (void)perm_blk;
+    (void)ubeg;
     if (nw > MAX_BLOCK_ANGLES) return cudaErrorInvalidValue;
-    int64_t blocks = (nunits * 32 + 255) / 256;
-    k_gather_units<P><<<(unsigned)blocks, 256, 0, st>>>(nvox, nunits, urow, ubeg, csr_off, perm_blk, buf, ang_seg_off,
-                                                        w0, nw, seg_lo, invL, wt, dirs, part);
-    k_gather_rows<<<(nvox + 255) / 256, 256, 0, st>>>(nvox, ufirst, part, J, Lst, Fc, first);
+    unsigned blocks = (unsigned)((nunits + 255) / 256);
+    if constexpr (sizeof(P) == sizeof(float2))
+        k_gather_units32<<<blocks, 256, 0, st>>>(nvox, nunits, urow, order, ulen, gbase, sell, (const float2 *)buf,
+                                                 ang_seg_off, w0, nw, seg_lo, wL32, dirs, part, J, Lst, Fc, first);
+    else
+        k_gather_units64<<<blocks, 256, 0, st>>>(nvox, nunits, urow, order, ulen, gbase, sell, (const double2 *)buf,
+                                                 ang_seg_off, w0, nw, seg_lo, invL, wt, dirs, part, J, Lst, Fc, first);
+    if (nmulti > 0) k_gather_rows<<<(nmulti + 255) / 256, 256, 0, st>>>(nmulti, multi, ufirst, part, J, Lst, Fc, first);
+    return cudaGetLastError();
+}
+
+cudaError_t sell_order(int64_t nunits, const int32_t *urow, const int32_t *ubeg, const int32_t *csr_off, int32_t *ulen,
+                       int32_t *hist, int32_t *order, int32_t *gw, cudaStream_t st)
+{
+    if (nunits <= 0) return cudaSuccess;
+    if (!urow || !ubeg || !csr_off || !ulen || !hist || !order || !gw) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * (UNIT_LEN + 1), st);
+    if (e != cudaSuccess) return e;
+    k_unit_len<<<grid_for(nunits, 256), 256, 0, st>>>(nunits, urow, ubeg, csr_off, ulen, hist);
+    k_hist_scan<<<1, 1, 0, st>>>(hist);
+    k_bucket_fill<<<grid_for(nunits, 256), 256, 0, st>>>(nunits, ulen, hist, order);
+    int64_t ng = (nunits + 31) / 32;
+    k_group_width<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(ng, order, ulen, gw);
+    return cudaGetLastError();
+}
+
+cudaError_t sell_fill(int64_t nunits, const int32_t *order, const int32_t *ulen, const int32_t *ubeg,
+                      const int32_t *perm_blk, const int64_t *gbase, int32_t *sell, cudaStream_t st)
+{
+    if (nunits <= 0) return cudaSuccess;
+    if (!order || !ulen || !ubeg || !perm_blk || !gbase || !sell) return cudaErrorInvalidValue;
+    k_sell_fill<<<grid_for(nunits, 256), 256, 0, st>>>(nunits, order, ulen, ubeg, perm_blk, gbase, sell);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_multi_rows(int nvox, const int64_t *ufirst, int32_t *flag, int64_t *pos, int64_t *tmp,
+                              int32_t *multi, cudaStream_t st)
+{
+    k_multi_flags<<<(nvox + 255) / 256, 256, 0, st>>>(nvox, ufirst, flag);
+    cudaError_t e = scan_i32(flag, pos, nvox, tmp, st);
+    if (e != cudaSuccess) return e;
+    if (multi) k_multi_fill<<<(nvox + 255) / 256, 256, 0, st>>>(nvox, flag, pos, multi);
     return cudaGetLastError();
 }
 
@@ -320,13 +755,73 @@ cudaError_t flux_local(const GeomDev &G, const double *Fc, double *F, cudaStream
     return cudaGetLastError();
 }
 
+cudaError_t gatherJ_classify(int nvox, const int32_t *csr_off, int32_t *hist, int32_t *longflag, int32_t *nch,
+                             cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * (SHORT_LEN + 1), st);
+    if (e != cudaSuccess) return e;
+    k_jclass<<<(nvox + 255) / 256, 256, 0, st>>>(nvox, csr_off, hist, longflag, nch);
+    return cudaGetLastError();
+}
+
+cudaError_t gatherJ_short(int nvox, const int32_t *csr_off, int32_t *hist, int32_t *jorder, int64_t nshort, int32_t *gw,
+                          cudaStream_t st)
+{
+    k_jhist_scan<<<1, 1, 0, st>>>(hist);
+    k_jshort_fill<<<(nvox + 255) / 256, 256, 0, st>>>(nvox, csr_off, hist, jorder);
+    int64_t ng = (nshort + 31) / 32;
+    if (ng > 0) k_jwidth<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(ng, csr_off, jorder, gw);
+    return cudaGetLastError();
+}
+
+cudaError_t gatherJ_sell(int64_t nshort, const int32_t *csr_off, const int32_t *jorder, const int32_t *perm_blk,
+                         const int64_t *gbase, int32_t *sell, cudaStream_t st)
+{
+    if (nshort <= 0) return cudaSuccess;
+    k_jsell_fill<<<grid_for(nshort, 256), 256, 0, st>>>(nshort, csr_off, jorder, perm_blk, gbase, sell);
+    return cudaGetLastError();
+}
+
+cudaError_t gatherJ_long(int nvox, const int32_t *csr_off, const int32_t *longflag, const int64_t *lpos,
+                         const int64_t *cpos, int32_t *lrows, int32_t *lfirst, int32_t *crow, int32_t *cbeg,
+                         int32_t *clr, cudaStream_t st)
+{
+    k_jlong_fill<<<(nvox + 255) / 256, 256, 0, st>>>(nvox, csr_off, longflag, lpos, cpos, lrows, lfirst, crow, cbeg, clr);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t gather_J(int nvox, const int32_t *csr_off, const GatherJTables &t, const int32_t *perm_blk, const T *buf,
+                     const int64_t *ang_seg_off, int w0, int nw, int64_t seg_lo, const float *wL32,
+                     const double *invL, const double *wt, double *part, double *J, int first, cudaStream_t st)
+{
+    if (nw > MAX_BLOCK_ANGLES) return cudaErrorInvalidValue;
+    const int nbs = (int)((t.nshort + 255) / 256);
+    const int64_t nbc = (t.nchunks * 32 + 255) / 256;
+    const int64_t grid = nbs + nbc;
+    if (grid <= 0) return cudaSuccess;
+    k_gatherJ<T><<<(unsigned)grid, 256, 0, st>>>(nvox, t.nshort, nbs, csr_off, t.jorder, t.jgbase, t.jsell, t.nchunks,
+                                                 t.crow, t.cbeg, t.clr, t.lfirst, t.nlong, t.cnt, part, perm_blk, buf,
+                                                 ang_seg_off, w0, nw, seg_lo, wL32, invL, wt, J, first);
+    return cudaGetLastError();
+}
+
+template cudaError_t gather_J<float>(int, const int32_t *, const GatherJTables &, const int32_t *, const float *,
+                                     const int64_t *, int, int, int64_t, const float *, const double *, const double *,
+                                     double *, double *, int, cudaStream_t);
+template cudaError_t gather_J<double>(int, const int32_t *, const GatherJTables &, const int32_t *, const double *,
+                                      const int64_t *, int, int, int64_t, const float *, const double *, const double *,
+                                      double *, double *, int, cudaStream_t);
+
 template cudaError_t gather_block<float2>(int, const int32_t *, const int32_t *, const float2 *, const int64_t *, int,
-                                          int, int64_t, const double *, const double *, const double *, const int32_t *,
-                                          const int32_t *, const int64_t *, int64_t, double *, double *, double *,
-                                          double *, int, cudaStream_t);
+                                          int, int64_t, const double *, const float *, const double *, const double *,
+                                          const int32_t *, const int32_t *, const int64_t *, int64_t, const int32_t *,
+                                          int, const int32_t *, const int32_t *, const int64_t *, const int32_t *,
+                                          double *, double *, double *, double *, int, cudaStream_t);
 template cudaError_t gather_block<double2>(int, const int32_t *, const int32_t *, const double2 *, const int64_t *, int,
-                                           int, int64_t, const double *, const double *, const double *, const int32_t *,
-                                           const int32_t *, const int64_t *, int64_t, double *, double *, double *,
-                                           double *, int, cudaStream_t);
+                                           int, int64_t, const double *, const float *, const double *, const double *,
+                                           const int32_t *, const int32_t *, const int64_t *, int64_t, const int32_t *,
+                                           int, const int32_t *, const int32_t *, const int64_t *, const int32_t *,
+                                           double *, double *, double *, double *, int, cudaStream_t);
 
 }  // namespace rtk

@@ -36,6 +36,16 @@ struct rt_grid {
     int32_t *d_urow = nullptr, *d_ubeg = nullptr;
     int64_t *d_ufirst = nullptr;
     double *d_part = nullptr;
+    float *d_wL32 = nullptr;  // FP32 gather weights wt_w / L_wv
+    std::vector<int64_t> h_mbase;     // per block: offset of its multi-unit voxel list
+    int32_t *d_multi = nullptr;       // voxels whose list needs several units, per block
+    // sliced-ELL copy of the ownership lists (coalesced gather reads), per block
+    int32_t *d_ulen = nullptr, *d_order = nullptr, *d_sell = nullptr;
+    int64_t *d_gbase = nullptr;
+    std::vector<int64_t> h_goff, h_soff;  // per block offsets into d_gbase / d_sell
+    std::vector<rtk::GatherJTables> jt;  // J-only gather tables per block
+    double *d_partJ = nullptr;           // chunk sums of long lists (J-only gather)
+    int lstar_prec = -1;                 // precision of the FS that computed d_L (-1: none since the last chi)
     void *d_segbuf = nullptr;
     double *d_chi = nullptr, *d_eps = nullptr, *d_B = nullptr, *d_S = nullptr;
     double *d_J = nullptr, *d_L = nullptr, *d_Fc = nullptr, *d_F = nullptr;

@@ -142,12 +142,18 @@ __device__ __forceinline__ int64_t lower_bound64(const int64_t *a, int64_t lo, i
     return lo;
 }
 
-template <typename T, typename P>
-__global__ void __launch_bounds__(256) k_march(const uint32_t *__restrict__ vox, const T *__restrict__ len,
-                                               const int64_t *__restrict__ ray_off, int64_t r_lo, int64_t r_hi,
-                                               int64_t seg_lo, int64_t nseg, const P *__restrict__ cs,
-                                               const T *__restrict__ Bv, T I_outer, int homog, int parabolic,
-                                               P *__restrict__ out, int chunk)
+// One warp per bundle of whole characteristics; each lane owns K consecutive
+// segments of a 32K-segment tile, runs the recurrence over them serially and
+// contributes one composed affine map I -> A I + b to a warp shuffle scan, so
+// the scan, shuffle and index work per segment is divided by K.  The next
+// tile's segment words and lengths are fetched before the current tile is
+// processed.
+template <typename T, typename P, int K, bool LAM>
+__global__ void __launch_bounds__(256) k_march4(const uint32_t *__restrict__ vox, const T *__restrict__ len,
+                                                const int64_t *__restrict__ ray_off, int64_t r_lo, int64_t r_hi,
+                                                int64_t seg_lo, int64_t nseg, const P *__restrict__ cs,
+                                                const T *__restrict__ Bv, T I_outer, int homog,
+                                                void *__restrict__ outv, int chunk)
 {
     using C = typename Traits<T>::C;
     const unsigned FULL = 0xffffffffu;
@@ -156,92 +162,187 @@ __global__ void __launch_bounds__(256) k_march(const uint32_t *__restrict__ vox,
     const int64_t c_lo = wg * chunk;
     if (c_lo >= nseg) return;
     const int64_t c_hi = (c_lo + chunk < nseg) ? c_lo + chunk : nseg;
-    // the bundle: whole characteristics that start inside [c_lo, c_hi)
     const int64_t ra = lower_bound64(ray_off, r_lo, r_hi, seg_lo + c_lo);
     const int64_t rb = lower_bound64(ray_off, r_lo, r_hi, seg_lo + c_hi);
-    const int64_t s_begin = ray_off[ra] - seg_lo;
-    const int64_t s_end = ray_off[rb] - seg_lo;
+    const int s_begin = (int)(ray_off[ra] - seg_lo);
+    const int s_end = (int)(ray_off[rb] - seg_lo);
     if (s_begin >= s_end) return;
     const uint32_t *vx = vox + seg_lo;
     const T *ln = len + seg_lo;
     T Icarry = 0, Sprev = 0, gprev = 0;
-    for (int64_t base = s_begin; base < s_end; base += 32) {
-        const int64_t s = base + lane;
-        const bool valid = s < s_end;
-        uint32_t w = 0;
-        T l = 0, chi = 0, S = 0;
-        if (valid) {
-            w = __ldcs(vx + s);
-            l = __ldcs(ln + s);
-            P c = cs[w & RTK_VOXMASK];
-            chi = c.x;
-            S = c.y;
+    // segment words and lengths of the current tile; the next tile's are
+    // fetched before the current one is processed (software pipelining)
+    uint32_t w[K];
+    T l[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int s = s_begin + K * lane + j;
+        w[j] = (s < s_end) ? __ldcs(vx + s) : 0u;
+        l[j] = (s < s_end) ? __ldcs(ln + s) : (T)0;
+    }
+    for (int base = s_begin; base < s_end; base += 32 * K) {
+        const int s0 = base + K * lane;
+        uint32_t wN[K];
+        T lN[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int s = base + 32 * K + K * lane + j;
+            wN[j] = (s < s_end) ? __ldcs(vx + s) : 0u;
+            lN[j] = (s < s_end) ? __ldcs(ln + s) : (T)0;
         }
-        uint32_t wn = __shfl_down_sync(FULL, w, 1);
-        T lnx = __shfl_down_sync(FULL, l, 1);
-        T chin = __shfl_down_sync(FULL, chi, 1);
-        T Sn = __shfl_down_sync(FULL, S, 1);
+        T chi[K], S[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            chi[j] = 0;
+            S[j] = 0;
+            if (s0 + j < s_end) {
+                P c = cs[w[j] & RTK_VOXMASK];
+                chi[j] = c.x;
+                S[j] = c.y;
+            }
+        }
+        // the segment after this lane's last one (lane 31: first of the next tile)
+        uint32_t wn = __shfl_down_sync(FULL, w[0], 1);
+        T lnx = __shfl_down_sync(FULL, l[0], 1);
+        T chin = __shfl_down_sync(FULL, chi[0], 1);
+        T Snx = __shfl_down_sync(FULL, S[0], 1);
+        const uint32_t wn31 = __shfl_sync(FULL, wN[0], 0);
+        const T ln31 = __shfl_sync(FULL, lN[0], 0);
         if (lane == 31) {
-            if (valid && s + 1 < s_end) {
-                wn = vx[s + 1];
-                lnx = ln[s + 1];
+            const int sn = base + 32 * K;
+            if (sn < s_end) {
+                wn = wn31;
+                lnx = ln31;
                 P c = cs[wn & RTK_VOXMASK];
                 chin = c.x;
-                Sn = c.y;
+                Snx = c.y;
             } else {
                 wn = RTK_RAYSTART;
             }
         }
-        const bool rstart = (w & RTK_RAYSTART) != 0u;
-        const bool run0 = (w & (RTK_RAYSTART | RTK_RESTART)) != 0u;
-        const bool last = (s + 1 >= s_end) || ((wn & (RTK_RAYSTART | RTK_RESTART)) != 0u);
-        const T x = valid ? chi * l : (T)1;
-        const T p = last ? (T)0 : chin * lnx;
-        const bool para = parabolic && !last && (p >= (T)0.5 * x);
-        T E, al, be, ga;
-        C::eval(x, p, para, E, al, be, ga);
-        T Sp = __shfl_up_sync(FULL, S, 1);
-        T gp = __shfl_up_sync(FULL, ga, 1);
-        if (lane == 0) {
-            Sp = Sprev;
-            gp = gprev;
+        // the segment before this lane's first one
+        T Sp = __shfl_up_sync(FULL, S[K - 1], 1);
+        if (lane == 0) Sp = Sprev;
+        T A[K], b[K], lam[K];
+        T gam_prev_lane;  // gamma of the previous lane's last segment, filled after the coefficients
+        T E[K], al[K], be[K], ga[K];
+        bool run0[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int s = s0 + j;
+            const bool valid = s < s_end;
+            const uint32_t wnx = (j + 1 < K) ? w[j + 1] : wn;
+            const T lnn = (j + 1 < K) ? l[j + 1] : lnx;
+            const T chn = (j + 1 < K) ? chi[j + 1] : chin;
+            const bool last = (s + 1 >= s_end) || ((wnx & (RTK_RAYSTART | RTK_RESTART)) != 0u);
+            run0[j] = (w[j] & (RTK_RAYSTART | RTK_RESTART)) != 0u;
+            const T x = valid ? chi[j] * l[j] : (T)1;
+            const T pp = last ? (T)0 : chn * lnn;
+            const bool para = (w[j] & RTK_PARA) != 0u;
+            C::eval(x, pp, para, E[j], al[j], be[j], ga[j]);
         }
-        const T Skm = run0 ? S : Sp;
-        const T src = al * Skm + be * S + (para ? ga * Sn : (T)0);
-        const T lam = be + (run0 ? al : gp * E);
-        T A = E, b = src;
-        if (rstart) {
-            T Iin = homog ? (T)0 : ((w & RTK_CORE) ? Bv[w & RTK_VOXMASK] : I_outer);
-            b = E * Iin + src;
-            A = 0;
+        gam_prev_lane = __shfl_up_sync(FULL, ga[K - 1], 1);
+        if (lane == 0) gam_prev_lane = gprev;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int s = s0 + j;
+            const bool valid = s < s_end;
+            const T Sm = (j == 0) ? Sp : S[j - 1];
+            const T gm = (j == 0) ? gam_prev_lane : ga[j - 1];
+            const T Sn = (j + 1 < K) ? S[j + 1] : Snx;
+            const bool para = (w[j] & RTK_PARA) != 0u;
+            const T Skm = run0[j] ? S[j] : Sm;
+            const T src = al[j] * Skm + be[j] * S[j] + (para ? ga[j] * Sn : (T)0);
+            if (LAM) lam[j] = be[j] + (run0[j] ? al[j] : gm * E[j]);
+            A[j] = E[j];
+            b[j] = src;
+            if (w[j] & RTK_RAYSTART) {
+                T Iin = homog ? (T)0 : ((w[j] & RTK_CORE) ? Bv[w[j] & RTK_VOXMASK] : I_outer);
+                b[j] = E[j] * Iin + src;
+                A[j] = 0;
+            }
+            if (!valid) {
+                A[j] = 1;
+                b[j] = 0;
+            }
         }
-        if (!valid) {
-            A = 1;
-            b = 0;
+        // compose this lane's maps, then an exclusive warp scan over lanes
+        T LA = A[0], LB = b[0];
+#pragma unroll
+        for (int j = 1; j < K; ++j) {
+            LB = A[j] * LB + b[j];
+            LA = A[j] * LA;
         }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            T Ao = __shfl_up_sync(FULL, A, o);
-            T bo = __shfl_up_sync(FULL, b, o);
+            T Ao = __shfl_up_sync(FULL, LA, o);
+            T bo = __shfl_up_sync(FULL, LB, o);
             if (lane >= o) {
-                b = A * bo + b;
-                A = A * Ao;
+                LB = LA * bo + LB;
+                LA = LA * Ao;
             }
         }
-        const T I = A * Icarry + b;
-        if (valid) {
-            P o;
-            o.x = l * I;
-            o.y = l * lam;
-            __stcg(out + s, o);
+        // exclusive prefix = inclusive prefix of the previous lane
+        T PA = __shfl_up_sync(FULL, LA, 1);
+        T PB = __shfl_up_sync(FULL, LB, 1);
+        if (lane == 0) {
+            PA = 1;
+            PB = 0;
+        }
+        T I = PA * Icarry + PB;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            I = A[j] * I + b[j];
+            if (s0 + j < s_end) {
+                if (LAM) {
+                    P o;
+                    o.x = l[j] * I;
+                    o.y = l[j] * lam[j];
+                    __stcg((P *)outv + s0 + j, o);
+                } else {
+                    __stcg((T *)outv + s0 + j, l[j] * I);
+                }
+            }
         }
         Icarry = __shfl_sync(FULL, I, 31);
-        Sprev = __shfl_sync(FULL, S, 31);
-        gprev = __shfl_sync(FULL, ga, 31);
+        Sprev = __shfl_sync(FULL, S[K - 1], 31);
+        gprev = __shfl_sync(FULL, ga[K - 1], 31);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            w[j] = wN[j];
+            l[j] = lN[j];
+        }
+    }
+}
+
+__global__ void k_mark_parabola(uint32_t *vox, const double *len64, const double *chi, int64_t nseg, int parabolic)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nseg; s += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t w = vox[s];
+        bool para = false;
+        if (parabolic && s + 1 < nseg) {
+            uint32_t wn = vox[s + 1];
+            if (!(wn & (RTK_RAYSTART | RTK_RESTART))) {
+                double x = chi[w & RTK_VOXMASK] * len64[s];
+                double p = chi[wn & RTK_VOXMASK] * len64[s + 1];
+                para = p >= 0.5 * x;
+            }
+        }
+        vox[s] = para ? (w | RTK_PARA) : (w & ~RTK_PARA);
     }
 }
 
 }  // namespace
+
+cudaError_t mark_parabola(uint32_t *vox, const double *len64, const double *chi, int64_t nseg, int parabolic,
+                          cudaStream_t st)
+{
+    if (nseg <= 0) return cudaSuccess;
+    int64_t blocks = (nseg + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_mark_parabola<<<(unsigned)blocks, 256, 0, st>>>(vox, len64, chi, nseg, parabolic);
+    return cudaGetLastError();
+}
 
 template <typename T, typename P>
 cudaError_t march_block(const uint32_t *vox, const T *len, const int64_t *ray_off, int64_t r_lo, int64_t r_hi,
@@ -251,11 +352,39 @@ cudaError_t march_block(const uint32_t *vox, const T *len, const int64_t *ray_of
     if (nseg <= 0) return cudaSuccess;
     int64_t warps = (nseg + chunk - 1) / chunk;
     int64_t blocks = (warps + 7) / 8;
-    k_march<T, P><<<(unsigned)blocks, 256, 0, st>>>(vox, len, ray_off, r_lo, r_hi, seg_lo, nseg, chiS, B, I_outer, homog,
-                                                    parabolic, out, chunk);
+    (void)parabolic;  // the interpolant of every segment is in its RTK_PARA bit
+    if constexpr (sizeof(T) == sizeof(float))
+        k_march4<T, P, 2, true><<<(unsigned)blocks, 256, 0, st>>>(vox, len, ray_off, r_lo, r_hi, seg_lo, nseg, chiS, B,
+                                                                  I_outer, homog, out, chunk);
+    else
+        k_march4<T, P, 1, true><<<(unsigned)blocks, 256, 0, st>>>(vox, len, ray_off, r_lo, r_hi, seg_lo, nseg, chiS, B,
+                                                                  I_outer, homog, out, chunk);
     return cudaGetLastError();
 }
 
+template <typename T, typename P>
+cudaError_t march_block_J(const uint32_t *vox, const T *len, const int64_t *ray_off, int64_t r_lo, int64_t r_hi,
+                          int64_t seg_lo, int64_t nseg, const P *chiS, const T *B, T I_outer, int homog, T *out,
+                          int chunk, cudaStream_t st)
+{
+    if (nseg <= 0) return cudaSuccess;
+    int64_t warps = (nseg + chunk - 1) / chunk;
+    int64_t blocks = (warps + 7) / 8;
+    if constexpr (sizeof(T) == sizeof(float))
+        k_march4<T, P, 2, false><<<(unsigned)blocks, 256, 0, st>>>(vox, len, ray_off, r_lo, r_hi, seg_lo, nseg, chiS, B,
+                                                                   I_outer, homog, out, chunk);
+    else
+        k_march4<T, P, 1, false><<<(unsigned)blocks, 256, 0, st>>>(vox, len, ray_off, r_lo, r_hi, seg_lo, nseg, chiS, B,
+                                                                   I_outer, homog, out, chunk);
+    return cudaGetLastError();
+}
+
+template cudaError_t march_block_J<double, double2>(const uint32_t *, const double *, const int64_t *, int64_t, int64_t,
+                                                    int64_t, int64_t, const double2 *, const double *, double, int,
+                                                    double *, int, cudaStream_t);
+template cudaError_t march_block_J<float, float2>(const uint32_t *, const float *, const int64_t *, int64_t, int64_t,
+                                                  int64_t, int64_t, const float2 *, const float *, float, int, float *,
+                                                  int, cudaStream_t);
 template cudaError_t march_block<double, double2>(const uint32_t *, const double *, const int64_t *, int64_t, int64_t,
                                                   int64_t, int64_t, const double2 *, const double *, double, int, int,
                                                   double2 *, int, cudaStream_t);

@@ -354,6 +354,33 @@ int build_geometry(rt_grid *g)
         g->h_ubase[b + 1] = g->h_ubase[b] + g->h_nunits[b];
         max_units = std::max(max_units, g->h_nunits[b]);
     }
+    // voxels whose ownership list spans several units, per block
+    {
+        int32_t *flag = nullptr;
+        int64_t *pos = nullptr, *stmp = nullptr;
+        RCK(dalloc(g, &flag, nvox));
+        RCK(dalloc(g, &pos, (size_t)g->nblk * (nvox + 1)));
+        RCK(dalloc(g, &stmp, scan_tmp_elems(nvox)));
+        std::vector<int64_t> nm(g->nblk);
+        for (int b = 0; b < g->nblk; ++b) {
+            int64_t *pb = pos + (size_t)b * (nvox + 1);
+            CK(gather_multi_rows(nvox, g->d_ufirst + (size_t)b * (nvox + 1), flag, pb, stmp, nullptr, g->st));
+            CK(cudaMemcpyAsync(&nm[b], pb + nvox, sizeof(int64_t), cudaMemcpyDeviceToHost, g->st));
+        }
+        RCK(sync(g));
+        g->h_mbase.assign(g->nblk + 1, 0);
+        for (int b = 0; b < g->nblk; ++b) g->h_mbase[b + 1] = g->h_mbase[b] + nm[b];
+        RCK(dalloc(g, &g->d_multi, std::max<int64_t>(1, g->h_mbase[g->nblk])));
+        for (int b = 0; b < g->nblk; ++b)
+            CK(gather_multi_rows(nvox, g->d_ufirst + (size_t)b * (nvox + 1), flag, pos + (size_t)b * (nvox + 1), stmp,
+                                 g->d_multi + g->h_mbase[b], g->st));
+        RCK(sync(g));
+        dfree(g, flag);
+        dfree(g, pos);
+        dfree(g, stmp);
+    }
+    RCK(dalloc(g, &g->d_wL32, (size_t)n_ang * nvox));
+    CK(make_wL32(n_ang, nvox, g->d_invL, g->d_wt, g->d_wL32, g->st));
     RCK(dalloc(g, &g->d_urow, g->h_ubase[g->nblk]));
     RCK(dalloc(g, &g->d_ubeg, g->h_ubase[g->nblk]));
     RCK(dalloc(g, &g->d_part, 5 * (size_t)max_units));
@@ -363,6 +390,123 @@ int build_geometry(rt_grid *g)
                              g->d_ubeg + g->h_ubase[b], g->st));
     }
     RCK(sync(g));
+    // sliced-ELL layout of every block's work units
+    {
+        const int64_t U = g->h_ubase[g->nblk];
+        RCK(dalloc(g, &g->d_ulen, std::max<int64_t>(1, U)));
+        RCK(dalloc(g, &g->d_order, std::max<int64_t>(1, U)));
+        g->h_goff.assign(g->nblk + 1, 0);
+        int64_t maxg = 0;
+        for (int b = 0; b < g->nblk; ++b) {
+            int64_t ng = (g->h_nunits[b] + 31) / 32;
+            g->h_goff[b + 1] = g->h_goff[b] + ng + 1;
+            maxg = std::max(maxg, ng);
+        }
+        RCK(dalloc(g, &g->d_gbase, g->h_goff[g->nblk]));
+        int32_t *hist = nullptr, *gw = nullptr;
+        int64_t *stmp = nullptr;
+        RCK(dalloc(g, &hist, 64));
+        RCK(dalloc(g, &gw, std::max<int64_t>(1, maxg)));
+        RCK(dalloc(g, &stmp, scan_tmp_elems(std::max<int64_t>(1, maxg))));
+        std::vector<int64_t> tot(g->nblk, 0);
+        for (int b = 0; b < g->nblk; ++b) {
+            const int64_t u0 = g->h_ubase[b], nu = g->h_nunits[b], ng = (nu + 31) / 32;
+            const int32_t *off = g->d_csr_off + (size_t)b * (nvox + 1);
+            CK(sell_order(nu, g->d_urow + u0, g->d_ubeg + u0, off, g->d_ulen + u0, hist, g->d_order + u0, gw, g->st));
+            CK(scan_i32(gw, g->d_gbase + g->h_goff[b], ng, stmp, g->st));
+            CK(cudaMemcpyAsync(&tot[b], g->d_gbase + g->h_goff[b] + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, g->st));
+        }
+        RCK(sync(g));
+        g->h_soff.assign(g->nblk + 1, 0);
+        for (int b = 0; b < g->nblk; ++b) g->h_soff[b + 1] = g->h_soff[b] + tot[b];
+        RCK(dalloc(g, &g->d_sell, std::max<int64_t>(1, g->h_soff[g->nblk])));
+        for (int b = 0; b < g->nblk; ++b) {
+            const int w0 = g->blk_w0[b];
+            const int64_t u0 = g->h_ubase[b], lo = g->h_ang_seg_off[w0];
+            CK(sell_fill(g->h_nunits[b], g->d_order + u0, g->d_ulen + u0, g->d_ubeg + u0, g->d_perm + lo,
+                         g->d_gbase + g->h_goff[b], g->d_sell + g->h_soff[b], g->st));
+        }
+        RCK(sync(g));
+        dfree(g, hist);
+        dfree(g, gw);
+        dfree(g, stmp);
+    }
+    // J-only gather tables: short lists in a sliced-ELL copy, long lists in chunks
+    {
+        int32_t *hist = nullptr, *lflag = nullptr, *nch = nullptr, *gw = nullptr;
+        int64_t *lpos = nullptr, *cpos = nullptr, *stmp = nullptr;
+        RCK(dalloc(g, &hist, 128));
+        RCK(dalloc(g, &lflag, nvox));
+        RCK(dalloc(g, &nch, nvox));
+        RCK(dalloc(g, &gw, (nvox + 31) / 32 + 1));
+        RCK(dalloc(g, &lpos, nvox + 1));
+        RCK(dalloc(g, &cpos, nvox + 1));
+        RCK(dalloc(g, &stmp, scan_tmp_elems(nvox + 1)));
+        g->jt.assign(g->nblk, GatherJTables());
+        int64_t max_chunks = 1;
+        for (int b = 0; b < g->nblk; ++b) {
+            const int w0 = g->blk_w0[b];
+            const int64_t lo = g->h_ang_seg_off[w0];
+            const int32_t *off = g->d_csr_off + (size_t)b * (nvox + 1);
+            GatherJTables &t = g->jt[b];
+            CK(gatherJ_classify(nvox, off, hist, lflag, nch, g->st));
+            std::vector<int32_t> hh(65);
+            CK(cudaMemcpyAsync(hh.data(), hist, sizeof(int32_t) * 65, cudaMemcpyDeviceToHost, g->st));
+            RCK(sync(g));
+            int64_t nshort = 0;
+            for (int q = 0; q < 65; ++q) nshort += hh[q];
+            t.nshort = nshort;
+            int32_t *jorder = nullptr, *jsell = nullptr;
+            int64_t *jgbase = nullptr;
+            const int64_t ng = (nshort + 31) / 32;
+            RCK(dalloc(g, &jorder, std::max<int64_t>(1, nshort)));
+            RCK(dalloc(g, &jgbase, ng + 1));
+            CK(gatherJ_short(nvox, off, hist, jorder, nshort, gw, g->st));
+            CK(scan_i32(gw, jgbase, ng, stmp, g->st));
+            int64_t nsell = 0;
+            CK(cudaMemcpyAsync(&nsell, jgbase + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, g->st));
+            RCK(sync(g));
+            RCK(dalloc(g, &jsell, std::max<int64_t>(1, nsell)));
+            CK(gatherJ_sell(nshort, off, jorder, g->d_perm + lo, jgbase, jsell, g->st));
+            t.jorder = jorder;
+            t.jgbase = jgbase;
+            t.jsell = jsell;
+            // long lists
+            CK(scan_i32(lflag, lpos, nvox, stmp, g->st));
+            CK(scan_i32(nch, cpos, nvox, stmp, g->st));
+            int64_t tots[2] = {0, 0};
+            CK(cudaMemcpyAsync(&tots[0], lpos + nvox, sizeof(int64_t), cudaMemcpyDeviceToHost, g->st));
+            CK(cudaMemcpyAsync(&tots[1], cpos + nvox, sizeof(int64_t), cudaMemcpyDeviceToHost, g->st));
+            RCK(sync(g));
+            t.nlong = (int)tots[0];
+            t.nchunks = tots[1];
+            int32_t *lrows = nullptr, *lfirst = nullptr, *crow = nullptr, *cbeg = nullptr, *clr = nullptr;
+            int *cnt = nullptr;
+            RCK(dalloc(g, &lrows, std::max<int64_t>(1, tots[0])));
+            RCK(dalloc(g, &lfirst, std::max<int64_t>(1, tots[0])));
+            RCK(dalloc(g, &cnt, std::max<int64_t>(1, tots[0])));
+            RCK(dalloc(g, &crow, std::max<int64_t>(1, tots[1])));
+            RCK(dalloc(g, &cbeg, std::max<int64_t>(1, tots[1])));
+            RCK(dalloc(g, &clr, std::max<int64_t>(1, tots[1])));
+            CK(cudaMemsetAsync(cnt, 0, sizeof(int) * std::max<int64_t>(1, tots[0]), g->st));
+            CK(gatherJ_long(nvox, off, lflag, lpos, cpos, lrows, lfirst, crow, cbeg, clr, g->st));
+            t.lfirst = lfirst;
+            t.crow = crow;
+            t.cbeg = cbeg;
+            t.clr = clr;
+            t.cnt = cnt;
+            max_chunks = std::max(max_chunks, tots[1]);
+        }
+        RCK(dalloc(g, &g->d_partJ, max_chunks));
+        RCK(sync(g));
+        dfree(g, hist);
+        dfree(g, lflag);
+        dfree(g, nch);
+        dfree(g, gw);
+        dfree(g, lpos);
+        dfree(g, cpos);
+        dfree(g, stmp);
+    }
     dfree(g, cnt);
     dfree(g, cursor);
     dfree(g, ctmp);
@@ -411,6 +555,7 @@ int alloc_fields(rt_grid *g)
     CK(fill_const(n, g->d_J, 0.0, g->st));
     CK(fill_const(n, g->d_L, 0.0, g->st));
     CK(fill_const(3 * n, g->d_F, 0.0, g->st));
+    CK(mark_parabola(g->d_vox, g->d_len64, g->d_chi, g->n_seg, g->interp == RT_PARABOLIC, g->st));
     return RT_OK;
 }
 
@@ -435,10 +580,12 @@ int run_fs(rt_grid *g, int prec, int homog, const double *S_src, double *J, doub
                                             g->I_outer, homog, para, buf, g->march_chunk, g->st));
             tstop(g, t0, 0, ns);
             t1 = tstart(g);
-            CK(gather_block<double2>(n, off, g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->d_wt,
-                                     g->d_dirs, g->d_urow + g->h_ubase[b], g->d_ubeg + g->h_ubase[b],
-                                     g->d_ufirst + (size_t)b * (n + 1), g->h_nunits[b], g->d_part, J, L, Fc, b == 0,
-                                     g->st));
+            CK(gather_block<double2>(n, off, g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->d_wL32,
+                                     g->d_wt, g->d_dirs, g->d_urow + g->h_ubase[b], g->d_ubeg + g->h_ubase[b],
+                                     g->d_ufirst + (size_t)b * (n + 1), g->h_nunits[b], g->d_multi + g->h_mbase[b],
+                                     (int)(g->h_mbase[b + 1] - g->h_mbase[b]), g->d_order + g->h_ubase[b],
+                                     g->d_ulen + g->h_ubase[b], g->d_gbase + g->h_goff[b], g->d_sell + g->h_soff[b],
+                                     g->d_part, J, L, Fc, b == 0, g->st));
             tstop(g, t1, 1, ns);
         } else {
             float2 *buf = (float2 *)g->d_segbuf;
@@ -447,10 +594,12 @@ int run_fs(rt_grid *g, int prec, int homog, const double *S_src, double *J, doub
                                           (float)g->I_outer, homog, para, buf, g->march_chunk, g->st));
             tstop(g, t0, 0, ns);
             t1 = tstart(g);
-            CK(gather_block<float2>(n, off, g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->d_wt,
-                                     g->d_dirs, g->d_urow + g->h_ubase[b], g->d_ubeg + g->h_ubase[b],
-                                     g->d_ufirst + (size_t)b * (n + 1), g->h_nunits[b], g->d_part, J, L, Fc, b == 0,
-                                     g->st));
+            CK(gather_block<float2>(n, off, g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->d_wL32,
+                                    g->d_wt, g->d_dirs, g->d_urow + g->h_ubase[b], g->d_ubeg + g->h_ubase[b],
+                                     g->d_ufirst + (size_t)b * (n + 1), g->h_nunits[b], g->d_multi + g->h_mbase[b],
+                                     (int)(g->h_mbase[b + 1] - g->h_mbase[b]), g->d_order + g->h_ubase[b],
+                                     g->d_ulen + g->h_ubase[b], g->d_gbase + g->h_goff[b], g->d_sell + g->h_soff[b],
+                                     g->d_part, J, L, Fc, b == 0, g->st));
             tstop(g, t1, 1, ns);
         }
         g->launches += 3;
@@ -459,6 +608,57 @@ int run_fs(rt_grid *g, int prec, int homog, const double *S_src, double *J, doub
         CK(flux_local(g->G, Fc, F, g->st));
         g->launches++;
     }
+    return RT_OK;
+}
+
+// J-only formal solution (the ALI iteration reuses Lambda*, which depends on
+// chi and the lengths but not on S).
+int run_fs_J(rt_grid *g, int prec, int homog, const double *S_src, double *J)
+{
+    const int n = g->nvox;
+    if (prec == RT_FP64) CK(pack_chiS64(n, g->d_chi, S_src, g->d_cs64, g->st));
+    else CK(pack_chiS32(n, g->d_chi, S_src, g->d_B, g->d_cs32, g->d_B32, g->st));
+    g->launches++;
+    for (int b = 0; b < g->nblk; ++b) {
+        int w0 = g->blk_w0[b], nw = g->blk_nw[b];
+        int64_t r_lo = g->h_ang_ray_off[w0], r_hi = g->h_ang_ray_off[w0 + nw];
+        int64_t lo = g->h_ang_seg_off[w0], ns = g->h_ang_seg_off[w0 + nw] - lo;
+        const int32_t *off = g->d_csr_off + (size_t)b * (n + 1);
+        int t0, t1;
+        if (prec == RT_FP64) {
+            double *buf = (double *)g->d_segbuf;
+            t0 = tstart(g);
+            CK(march_block_J<double, double2>(g->d_vox, g->d_len64, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs64, g->d_B,
+                                              g->I_outer, homog, buf, g->march_chunk, g->st));
+            tstop(g, t0, 0, ns);
+            t1 = tstart(g);
+            CK(gather_J<double>(n, off, g->jt[b], g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_wL32,
+                                g->d_invL, g->d_wt, g->d_partJ, J, b == 0, g->st));
+            tstop(g, t1, 1, ns);
+        } else {
+            float *buf = (float *)g->d_segbuf;
+            t0 = tstart(g);
+            CK(march_block_J<float, float2>(g->d_vox, g->d_len32, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs32,
+                                            g->d_B32, (float)g->I_outer, homog, buf, g->march_chunk, g->st));
+            tstop(g, t0, 0, ns);
+            t1 = tstart(g);
+            CK(gather_J<float>(n, off, g->jt[b], g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_wL32,
+                               g->d_invL, g->d_wt, g->d_partJ, J, b == 0, g->st));
+            tstop(g, t1, 1, ns);
+        }
+        g->launches += 2;
+    }
+    return RT_OK;
+}
+
+// J of S for an ALI iteration: a full FS (J, Lambda*, flux) when Lambda* is not
+// yet known for this chi at this precision, else the J-only FS.
+int fs_iteration(rt_grid *g, int prec, const double *S_src, double *J)
+{
+    const bool lstar_ok = g->lstar_prec == RT_FP64 || (g->lstar_prec == RT_MIXED && prec == RT_MIXED);
+    if (!g->use_lstar || lstar_ok) return run_fs_J(g, prec, 0, S_src, J);
+    RCK(run_fs(g, prec, 0, S_src, J, g->d_L, g->d_Fc, g->d_F));
+    g->lstar_prec = prec;
     return RT_OK;
 }
 
@@ -507,7 +707,7 @@ int ng_maybe(rt_grid *g, double *out, const double *wref)
 
 int ali_step_impl(rt_grid *g, int prec, double *rel_out)
 {
-    RCK(run_fs(g, prec, 0, g->d_S, g->d_J, g->d_L, g->d_Fc, g->d_F));
+    RCK(fs_iteration(g, prec, g->d_S, g->d_J));
     CK(cudaMemsetAsync(g->d_maxrel, 0, sizeof(unsigned long long), g->st));
     double *slot = g->ng ? ng_append_slot(g) : nullptr;
     CK(ali_update(g->nvox, g->d_S, g->d_J, g->d_L, g->d_eps, g->d_B, g->use_lstar, slot, g->d_maxrel, g->st));
@@ -633,6 +833,9 @@ int rt_set_opacity(rt_grid *g, const double *chi, const double *eps, const doubl
     CK(cudaMemcpyAsync(g->d_eps, eps, sizeof(double) * n, kind, g->st));
     CK(cudaMemcpyAsync(g->d_B, B, sizeof(double) * n, kind, g->st));
     CK(cudaMemcpyAsync(g->d_S, g->d_B, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->st));
+    CK(mark_parabola(g->d_vox, g->d_len64, g->d_chi, g->n_seg, g->interp == RT_PARABOLIC, g->st));
+    g->launches++;
+    g->lstar_prec = -1;
     if (where == RT_HOST) RCK(sync(g));
     reset_ng(g);
     g->history.clear();
@@ -680,6 +883,7 @@ int rt_formal_solution_ex(rt_grid *g, int precision, int homog)
     CK(cudaSetDevice(g->device));
     RCK(run_fs(g, precision, homog ? 1 : 0, g->d_S, g->d_J, g->d_L, g->d_Fc, g->d_F));
     CK(cudaGetLastError());
+    g->lstar_prec = precision;
     return RT_OK;
 }
 
@@ -724,7 +928,7 @@ int rt_solve(rt_grid *g, double tol, int max_iter, int *iters)
     const int n = g->nvox;
     int total = 0;
     while (total < max_iter) {
-        RCK(run_fs(g, RT_FP64, 0, g->d_S, g->d_J, g->d_L, g->d_Fc, g->d_F));
+        RCK(fs_iteration(g, RT_FP64, g->d_S, g->d_J));
         total++;
         CK(cudaMemsetAsync(g->d_maxrel, 0, sizeof(unsigned long long), g->st));
         CK(residual(n, g->d_S, g->d_J, g->d_L, g->d_eps, g->d_B, g->use_lstar, g->d_r, g->d_maxrel, g->st));
@@ -742,7 +946,7 @@ int rt_solve(rt_grid *g, double tol, int max_iter, int *iters)
         // converges slowly (thick media, small eps)
         const double inner_tol = 0.01 * tol;
         for (int k = 0; k < g->refine_every && total < max_iter; ++k) {
-            RCK(run_fs(g, RT_MIXED, 1, g->d_delta, g->d_Jd, g->d_Ld, g->d_Fcd, nullptr));
+            RCK(run_fs_J(g, RT_MIXED, 1, g->d_delta, g->d_Jd));
             total++;
             CK(cudaMemsetAsync(g->d_maxrel, 0, sizeof(unsigned long long), g->st));
             double *slot = g->ng ? ng_append_slot(g) : nullptr;

@@ -7,11 +7,12 @@
 
 #include "rt.h"
 
-// Segment word: voxel id in the low 29 bits plus three flags.
+// Segment word: voxel id in the low 28 bits plus four flags.
 #define RTK_RAYSTART 0x80000000u  // first segment of a characteristic
 #define RTK_CORE 0x40000000u      // the characteristic starts on the core (I_in = B of this voxel)
 #define RTK_RESTART 0x20000000u   // first segment after a transparent hole (I carries over)
-#define RTK_VOXMASK 0x1FFFFFFFu
+#define RTK_PARA 0x10000000u      // parabolic weights for this segment (decided in FP64 from chi)
+#define RTK_VOXMASK 0x0FFFFFFFu
 
 #define RTK_END_EXIT 1
 #define RTK_END_CORE 2
@@ -61,19 +62,59 @@ cudaError_t csr_build(int nvox, const uint32_t *vox_blk, int64_t nseg_blk, int32
                       int32_t *cursor, int32_t *perm_blk, int64_t *tmp, cudaStream_t st);
 cudaError_t csr_invL(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const double *len64_blk,
                      const int64_t *ang_seg_off, int w0, int nw, int64_t seg_lo, double *invL, cudaStream_t st);
-// Work units of one block's ownership lists (pieces of at most 512 entries):
+// Work units of one block's ownership lists (pieces of at most 32 entries):
 // nu[v] units per voxel, ufirst = exclusive scan (nvox + 1), then per unit its voxel and first entry.
 cudaError_t gather_units_build(int nvox, const int32_t *csr_off, int32_t *nu, int64_t *ufirst, int64_t *tmp,
                                cudaStream_t st);
 cudaError_t gather_units_fill(int nvox, const int32_t *csr_off, const int64_t *ufirst, int32_t *urow, int32_t *ubeg,
                               cudaStream_t st);
+// FP32 gather weights wt_w / L_wv per (solid angle, voxel).
+cudaError_t make_wL32(int n_ang, int nvox, const double *invL, const double *wt, float *wL, cudaStream_t st);
 // J, Lambda*, flux (Cartesian) of one block from the per-segment (l I, l lambda); first = 1 overwrites.
 template <typename P>
 cudaError_t gather_block(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const P *buf,
                          const int64_t *ang_seg_off, int w0, int nw, int64_t seg_lo, const double *invL,
-                         const double *wt, const double *dirs, const int32_t *urow, const int32_t *ubeg,
-                         const int64_t *ufirst, int64_t nunits, double *part, double *J, double *Lst, double *Fc,
-                         int first, cudaStream_t st);
+                         const float *wL32, const double *wt, const double *dirs, const int32_t *urow,
+                         const int32_t *ubeg, const int64_t *ufirst, int64_t nunits, const int32_t *multi,
+                         int nmulti, const int32_t *order, const int32_t *ulen, const int64_t *gbase,
+                         const int32_t *sell, double *part, double *J, double *Lst, double *Fc, int first,
+                         cudaStream_t st);
+// Sliced-ELL layout of one block's work units: unit lengths, order (longest
+// first), per-group width 32*max length (gw, to be scanned into gbase), fill.
+cudaError_t sell_order(int64_t nunits, const int32_t *urow, const int32_t *ubeg, const int32_t *csr_off, int32_t *ulen,
+                       int32_t *hist, int32_t *order, int32_t *gw, cudaStream_t st);
+cudaError_t sell_fill(int64_t nunits, const int32_t *order, const int32_t *ulen, const int32_t *ubeg,
+                      const int32_t *perm_blk, const int64_t *gbase, int32_t *sell, cudaStream_t st);
+// Voxels of a block whose ownership list spans more than one unit: pos[nvox+1] = scan of the flags.
+cudaError_t gather_multi_rows(int nvox, const int64_t *ufirst, int32_t *flag, int64_t *pos, int64_t *tmp,
+                              int32_t *multi, cudaStream_t st);
+// J-only gather tables of one block (see gather.cu): short lists in a
+// sliced-ELL copy, long lists cut into chunks finished by their last warp.
+struct GatherJTables {
+    int64_t nshort = 0;            // voxels with short lists
+    const int32_t *jorder = nullptr;  // short voxels, longest list first
+    const int64_t *jgbase = nullptr;  // sliced-ELL group offsets (ceil(nshort/32)+1)
+    const int32_t *jsell = nullptr;   // interleaved list entries
+    int64_t nchunks = 0;
+    const int32_t *crow = nullptr, *cbeg = nullptr, *clr = nullptr;  // per chunk: voxel, first entry, long-voxel index
+    int nlong = 0;
+    const int32_t *lfirst = nullptr;  // per long voxel: first chunk
+    int *cnt = nullptr;               // per long voxel: chunks finished (returns to 0)
+};
+cudaError_t gatherJ_classify(int nvox, const int32_t *csr_off, int32_t *hist, int32_t *longflag, int32_t *nch,
+                             cudaStream_t st);
+cudaError_t gatherJ_short(int nvox, const int32_t *csr_off, int32_t *hist, int32_t *jorder, int64_t nshort, int32_t *gw,
+                          cudaStream_t st);
+cudaError_t gatherJ_sell(int64_t nshort, const int32_t *csr_off, const int32_t *jorder, const int32_t *perm_blk,
+                         const int64_t *gbase, int32_t *sell, cudaStream_t st);
+cudaError_t gatherJ_long(int nvox, const int32_t *csr_off, const int32_t *longflag, const int64_t *lpos,
+                         const int64_t *cpos, int32_t *lrows, int32_t *lfirst, int32_t *crow, int32_t *cbeg,
+                         int32_t *clr, cudaStream_t st);
+template <typename T>
+cudaError_t gather_J(int nvox, const int32_t *csr_off, const GatherJTables &t, const int32_t *perm_blk, const T *buf,
+                     const int64_t *ang_seg_off, int w0, int nw, int64_t seg_lo, const float *wL32,
+                     const double *invL, const double *wt, double *part, double *J, int first, cudaStream_t st);
+
 // Ibar, Lbar of one solid angle whose segments are [s_lo, s_hi) of the block.
 cudaError_t gather_angle_range(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const void *buf, int fp32,
                                int64_t s_lo, int64_t s_hi, const double *invL_w, double *Ibar, double *Lbar,
@@ -81,6 +122,17 @@ cudaError_t gather_angle_range(int nvox, const int32_t *csr_off, const int32_t *
 cudaError_t flux_local(const GeomDev &G, const double *Fc, double *F, cudaStream_t st);
 
 // ---- ray march (march.cu) ----
+// The same march writing only l I_k per segment (J without Lambda*: the ALI
+// iteration reuses Lambda*, which depends on chi but not on S).
+template <typename T, typename P>
+cudaError_t march_block_J(const uint32_t *vox, const T *len, const int64_t *ray_off, int64_t r_lo, int64_t r_hi,
+                          int64_t seg_lo, int64_t nseg, const P *chiS, const T *B, T I_outer, int homog, T *out,
+                          int chunk, cudaStream_t st);
+// Parabola-guard decision per segment, taken once in FP64 from chi and the FP64
+// lengths (dtau_{k+1} >= dtau_k / 2 and not the last node of a run), stored in
+// the RTK_PARA bit so the FP32 and FP64 marches use identical interpolants.
+cudaError_t mark_parabola(uint32_t *vox, const double *len64, const double *chi, int64_t nseg, int parabolic,
+                          cudaStream_t st);
 // One warp per bundle of whole characteristics holding about `chunk` segments.
 template <typename T, typename P>
 cudaError_t march_block(const uint32_t *vox, const T *len, const int64_t *ray_off, int64_t r_lo, int64_t r_hi,

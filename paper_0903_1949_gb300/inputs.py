@@ -117,6 +117,9 @@ PROBLEMS = {
     # the paper's spherical grid 65x33x65, 32x32 angles, tau 1e2, eps 1e-4, 20% lognormal noise
     "sph65": dict(coord=SPHERICAL, n=(65, 33, 65), n_mu=32, n_phi=32, fields="r2", tau=1e2, eps=1e-4,
                   noise=0.2, inner_bc=CORE_B),
+    # the same spherical grid with 8x8 solid angles (small case for profiling)
+    "sph65a64": dict(coord=SPHERICAL, n=(65, 33, 65), n_mu=8, n_phi=8, fields="r2", tau=1e2, eps=1e-4,
+                     noise=0.2, inner_bc=CORE_B),
     # cylindrical disc 65^3, R 0.1..10, |z| <= 2, 64x64 angles, midplane tau 1e3, eps 1e-6
     "cyl65": dict(coord=CYLINDRICAL, n=(65, 65, 65), n_mu=64, n_phi=64, fields="disc", tau=1e3, eps=1e-6,
                   inner_bc=TRANSPARENT),

@@ -247,3 +247,15 @@ def test_full_size_sph65_J_is_weighted_angle_sum(sph65):
         Ib, _ = g.fs_angles(ws[c:c + 128], rt.RT_FP64)
         acc += (p["weights"][ws[c:c + 128], None] * Ib).sum(0)
     assert relerr(J, acc) < 1e-12
+
+
+def test_full_size_sph65_fp32_formal_solution_within_1e5(sph65):
+    """The FP32 march over all 1024 solid angles stays within 1e-5 of the FP64 one."""
+    p, g = sph65
+    rng = np.random.default_rng(8)
+    g.set_S(p["B"] * rng.uniform(0.8, 1.2, p["B"].size))
+    g.formal_solution(rt.RT_FP64)
+    J64, L64 = g.J(), g.Lstar()
+    g.formal_solution(rt.RT_MIXED)
+    assert relerr(g.J(), J64) < TOL32
+    assert relerr(g.Lstar(), L64) < TOL32
