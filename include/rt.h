@@ -210,6 +210,43 @@ int rt_fs_angles(rt_grid *g, const int32_t *omegas, int n, int precision, double
  * first); calls whose GPU work overlaps (other streams, other threads) race. */
 int rt_fs_angle_noalloc(rt_grid *g, int omega, int precision, double *Ibar, double *Lbar);
 
+/* ---- batches: many opacity fields solved together ----------------------
+ * A batch holds n_members problems (wavelengths of a line profile or
+ * separate models, cf. the paper's wavelength "clusters", Sect. 3.2.2), each
+ * on one of n_grids existing grids of possibly different sizes (member_grid[m]
+ * gives its grid).  Members share their grid's characteristics but have their
+ * own chi, eps, B, S, J and Lambda*.  One batch iteration applies, to every
+ * member at once, the diagonal-Lambda* ALI update after an FP32 J-only formal
+ * solution (no Ng); it runs as a single CUDA graph of persistent march and
+ * gather launches that mix all members and grids.  The batch uses `stream` (or
+ * a stream of its own when NULL); its grids must not be used on other streams
+ * while the batch works, and must outlive it. */
+typedef struct rt_batch rt_batch;
+
+int rt_batch_create(rt_batch **out, rt_grid *const *grids, int n_grids, int n_members, const int32_t *member_grid,
+                    void *stream);
+int rt_batch_destroy(rt_batch *b);
+
+/* Opacity of member m (n_vox of its grid each; validated like rt_set_opacity);
+ * sets its S to B and computes its parabola choices and Lambda* (one full FP32
+ * formal solution).  Every member must be set before the first iteration. */
+int rt_batch_set_member(rt_batch *b, int m, const double *chi, const double *eps, const double *B, int where);
+
+/* One iteration of every member; max_rel_dS (may be NULL) gets n_members values. */
+int rt_batch_ali_step(rt_batch *b, double *max_rel_dS);
+
+/* Iterate until every member's max rel dS < tol; iters (may be NULL) gets, per
+ * member, the iteration at which it first met tol (0 if never). */
+int rt_batch_solve(rt_batch *b, double tol, int max_iter, int32_t *iters);
+
+/* Member m's S (what = 0), J (1) or Lambda* (2). */
+int rt_batch_get(const rt_batch *b, int m, int what, double *out, int where);
+
+/* Times one batch iteration for several bundle sizes (rays per warp) and
+ * persistent grid sizes, keeps the fastest and reports it (any output may be
+ * NULL).  Member S is restored afterwards. */
+int rt_batch_autotune(rt_batch *b, int32_t *chunk_out, int32_t *grid_out, double *ms_out);
+
 /* Device timing of the hot kernels.  rt_set_timing(g, 1) resets the counters
  * and brackets every ray-march and gather launch of later calls with CUDA
  * events on the grid's stream; rt_set_timing(g, 0) stops recording (counters

@@ -1,0 +1,531 @@
+// batch.cu -- many opacity fields (wavelengths of a line profile, or models)
+// solved together on one or more grids of uneven size (the paper distributes
+// wavelengths over MPI "clusters", Sect. 3.2.2; here they share one GPU).
+//
+// Every member m has its own chi, eps, B, S, J and Lambda* and its own
+// parabola choices (a bit per crossing segment, from its chi in FP64); the
+// crossing lists and ownership lists are those of the member's grid.  One
+// ALI iteration of all members is: pack (chi, S) in FP32, then for each wave
+// k (angle block k of every member that has one) a persistent FP32 J-only
+// march over the bundles of all the wave's items and a persistent J gather
+// over their lists, then the FP64 ALI update of every member.  Each member
+// appears at most once per wave, so its J accumulates over its angle blocks
+// in a fixed order.  The whole iteration is captured once as a CUDA graph and
+// replayed; rt_batch_autotune picks the bundle size and the persistent grid.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "grid.h"
+#include "rt_internal.h"
+
+using namespace rtk;
+
+namespace {
+
+int bfail(int code, const std::string &m)
+{
+    set_last_error(m.c_str());
+    return code;
+}
+
+#define BCK(...)                                                                                         \
+    do {                                                                                                 \
+        cudaError_t e_ = (__VA_ARGS__);                                                                  \
+        if (e_ != cudaSuccess) return bfail(RT_ECUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define BRCK(call)                  \
+    do {                            \
+        int r_ = (call);            \
+        if (r_ != RT_OK) return r_; \
+    } while (0)
+
+__global__ void k_bpack(int64_t n, const double *chi, const double *S, const double *B, float2 *cs, float *B32)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        cs[i] = make_float2((float)chi[i], (float)S[i]);
+        B32[i] = (float)B[i];
+    }
+}
+
+// ALI update of every member's voxels; per-member max |dS| / |S_new|.
+__global__ void k_bali(int64_t n, const int64_t *voff, int nm, double *S, const double *J, const double *L,
+                       const double *eps, const double *B, unsigned long long *maxrel)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nm;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (voff[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        const double e = eps[i], s = S[i];
+        const double sn = s + ((1.0 - e) * J[i] + e * B[i] - s) / (1.0 - (1.0 - e) * L[i]);
+        const double rel = fabs(sn - s) / fabs(sn);
+        S[i] = sn;
+        atomicMax(maxrel + lo, (unsigned long long)__double_as_longlong(rel));
+    }
+}
+
+struct Wave {
+    int n = 0;            // items
+    int64_t mi0 = 0;      // first item in the concatenated item arrays
+    int64_t pf0 = 0;      // first prefix entry (n + 1 per wave)
+    int64_t bundles = 0;  // total march bundles
+    int64_t work = 0;     // total gather work units
+};
+
+}  // namespace
+
+struct rt_batch {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::vector<rt_grid *> grids;
+    std::vector<int> mgrid;
+    std::vector<int64_t> voff;  // member voxel offsets (n_members + 1)
+    std::vector<char> ready;
+    int nm = 0;
+    int64_t ntot = 0;
+    std::vector<void *> allocs;
+    double *chi = nullptr, *eps = nullptr, *B = nullptr, *S = nullptr, *J = nullptr, *L = nullptr, *Fc = nullptr;
+    float2 *cs = nullptr;
+    float *B32 = nullptr;
+    int64_t *d_voff = nullptr;
+    std::vector<uint32_t *> pbits;
+    unsigned long long *maxrel = nullptr;
+    std::vector<unsigned long long> h_maxrel;
+    std::vector<Wave> waves;
+    std::vector<MarchItem> h_mi;
+    std::vector<GatherItem> h_gi;
+    MarchItem *d_mi = nullptr;
+    GatherItem *d_gi = nullptr;
+    int64_t *d_bpfx = nullptr, *d_wpfx = nullptr;
+    float *wbuf = nullptr;
+    double *wpart = nullptr;
+    int *wcnt = nullptr;
+    unsigned long long *counters = nullptr;
+    int chunk = 1024;
+    int grid_march = 152 * 5, grid_gather = 152 * 5;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<double> history;  // max over members of max rel dS per iteration
+};
+
+namespace {
+
+template <typename T>
+int balloc(rt_batch *b, T **p, size_t count)
+{
+    void *q = nullptr;
+    size_t nbytes = sizeof(T) * (count > 0 ? count : 1);
+    cudaError_t e = cudaMalloc(&q, nbytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(RT_ENOMEM, "cudaMalloc of " + std::to_string(nbytes) + " bytes failed");
+    }
+    b->allocs.push_back(q);
+    *p = (T *)q;
+    return RT_OK;
+}
+
+void bfree_all(rt_batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    for (void *p : b->allocs) cudaFree(p);
+    b->allocs.clear();
+    if (b->own_stream && b->st) cudaStreamDestroy(b->st);
+    b->st = nullptr;
+}
+
+// Bundle and work-unit prefixes of every wave for the current bundle size.
+int build_prefixes(rt_batch *b)
+{
+    std::vector<int64_t> bp, wp;
+    for (Wave &w : b->waves) {
+        w.pf0 = (int64_t)bp.size();
+        int64_t acc_b = 0, acc_w = 0;
+        bp.push_back(0);
+        wp.push_back(0);
+        for (int i = 0; i < w.n; ++i) {
+            const MarchItem &m = b->h_mi[w.mi0 + i];
+            const GatherItem &g = b->h_gi[w.mi0 + i];
+            acc_b += (m.nseg + b->chunk - 1) / b->chunk;
+            acc_w += g.nbs + g.nbc;
+            bp.push_back(acc_b);
+            wp.push_back(acc_w);
+        }
+        w.bundles = acc_b;
+        w.work = acc_w;
+    }
+    if (!b->d_bpfx) {
+        BRCK(balloc(b, &b->d_bpfx, bp.size()));
+        BRCK(balloc(b, &b->d_wpfx, wp.size()));
+    }
+    BCK(cudaMemcpyAsync(b->d_bpfx, bp.data(), sizeof(int64_t) * bp.size(), cudaMemcpyHostToDevice, b->st));
+    BCK(cudaMemcpyAsync(b->d_wpfx, wp.data(), sizeof(int64_t) * wp.size(), cudaMemcpyHostToDevice, b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    return RT_OK;
+}
+
+// The kernels of one ALI iteration of all members (captured into the graph).
+int enqueue_iteration(rt_batch *b)
+{
+    k_bpack<<<152 * 8, 256, 0, b->st>>>(b->ntot, b->chi, b->S, b->B, b->cs, b->B32);
+    BCK(cudaGetLastError());
+    for (const Wave &w : b->waves) {
+        BCK(cudaMemsetAsync(b->counters, 0, 2 * sizeof(unsigned long long), b->st));
+        BCK(march_batch(b->d_mi + w.mi0, b->d_bpfx + w.pf0, w.n, w.bundles, b->chunk, 0, b->counters, b->grid_march,
+                        b->st));
+        BCK(gather_J_batch(b->d_gi + w.mi0, b->d_wpfx + w.pf0, w.n, w.work, b->counters + 1, b->grid_gather, b->st));
+    }
+    BCK(cudaMemsetAsync(b->maxrel, 0, sizeof(unsigned long long) * b->nm, b->st));
+    k_bali<<<152 * 8, 256, 0, b->st>>>(b->ntot, b->d_voff, b->nm, b->S, b->J, b->L, b->eps, b->B, b->maxrel);
+    BCK(cudaGetLastError());
+    return RT_OK;
+}
+
+int capture(rt_batch *b)
+{
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    cudaGraph_t gr = nullptr;
+    BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_iteration(b);
+    cudaError_t e = cudaStreamEndCapture(b->st, &gr);
+    if (rc != RT_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return rc;
+    }
+    if (e != cudaSuccess) return bfail(RT_ECUDA, std::string("stream capture failed: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->graph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return bfail(RT_ECUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(e));
+    return RT_OK;
+}
+
+int step(rt_batch *b, double *rel_out)
+{
+    for (int m = 0; m < b->nm; ++m)
+        if (!b->ready[m]) return bfail(RT_EINVAL, "member " + std::to_string(m) + " has no opacity yet");
+    if (!b->graph) BRCK(capture(b));
+    BCK(cudaGraphLaunch(b->graph, b->st));
+    BCK(cudaMemcpyAsync(b->h_maxrel.data(), b->maxrel, sizeof(unsigned long long) * b->nm, cudaMemcpyDeviceToHost,
+                        b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    double mx = 0.0;
+    for (int m = 0; m < b->nm; ++m) {
+        double r;
+        std::memcpy(&r, &b->h_maxrel[m], sizeof(r));
+        if (rel_out) rel_out[m] = r;
+        mx = std::max(mx, r);
+    }
+    b->history.push_back(mx);
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rt_batch_create(rt_batch **out, rt_grid *const *grids, int n_grids, int n_members, const int32_t *member_grid,
+                    void *stream)
+{
+    if (!out || !grids || n_grids < 1 || n_members < 1 || !member_grid) return bfail(RT_EINVAL, "bad arguments");
+    for (int q = 0; q < n_grids; ++q)
+        if (!grids[q]) return bfail(RT_EINVAL, "grid " + std::to_string(q) + " is NULL");
+    for (int m = 0; m < n_members; ++m)
+        if (member_grid[m] < 0 || member_grid[m] >= n_grids) return bfail(RT_EINVAL, "member_grid out of range");
+    for (int q = 0; q < n_grids; ++q) {
+        if (grids[q]->device != grids[0]->device) return bfail(RT_EINVAL, "all grids must live on one device");
+        if (grids[q]->lost) return bfail(RT_EDEVICE, "a grid has characteristics that could not be tracked");
+        for (int k = 0; k < grids[q]->nblk; ++k)
+            if (grids[q]->h_ang_seg_off[grids[q]->blk_w0[k] + grids[q]->blk_nw[k]] - grids[q]->h_ang_seg_off[grids[q]->blk_w0[k]] >= (1ll << 31))
+                return bfail(RT_EINVAL, "angle block too large");
+    }
+    if (cudaSetDevice(grids[0]->device) != cudaSuccess) return bfail(RT_ECUDA, "cudaSetDevice failed");
+    rt_batch *b = new rt_batch();
+    b->device = grids[0]->device;
+    b->grids.assign(grids, grids + n_grids);
+    b->mgrid.assign(member_grid, member_grid + n_members);
+    b->nm = n_members;
+    b->ready.assign(n_members, 0);
+    b->h_maxrel.assign(n_members, 0ull);
+    auto fail_and_free = [&](int rc) {
+        std::string keep = rt_last_error();
+        if (b->st) cudaStreamSynchronize(b->st);
+        bfree_all(b);
+        delete b;
+        set_last_error(keep.c_str());
+        return rc;
+    };
+    if (stream) {
+        b->st = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess)
+            return fail_and_free(bfail(RT_ECUDA, "stream creation failed"));
+        b->own_stream = true;
+    }
+    b->voff.assign(n_members + 1, 0);
+    int max_vox = 0;
+    for (int m = 0; m < n_members; ++m) {
+        b->voff[m + 1] = b->voff[m] + grids[member_grid[m]]->nvox;
+        max_vox = std::max(max_vox, grids[member_grid[m]]->nvox);
+    }
+    b->ntot = b->voff[n_members];
+    int rc = RT_OK;
+#define TRY(x)                          \
+    do {                                \
+        if ((rc = (x)) != RT_OK) return fail_and_free(rc); \
+    } while (0)
+    TRY(balloc(b, &b->chi, b->ntot));
+    TRY(balloc(b, &b->eps, b->ntot));
+    TRY(balloc(b, &b->B, b->ntot));
+    TRY(balloc(b, &b->S, b->ntot));
+    TRY(balloc(b, &b->J, b->ntot));
+    TRY(balloc(b, &b->L, b->ntot));
+    TRY(balloc(b, &b->Fc, 3 * (size_t)max_vox));
+    TRY(balloc(b, &b->cs, b->ntot));
+    TRY(balloc(b, &b->B32, b->ntot));
+    TRY(balloc(b, &b->d_voff, n_members + 1));
+    TRY(balloc(b, &b->maxrel, n_members));
+    TRY(balloc(b, &b->counters, 2));
+    if (cudaMemcpyAsync(b->d_voff, b->voff.data(), sizeof(int64_t) * (n_members + 1), cudaMemcpyHostToDevice, b->st) !=
+        cudaSuccess)
+        return fail_and_free(bfail(RT_ECUDA, "copy failed"));
+    b->pbits.assign(n_members, nullptr);
+    for (int m = 0; m < n_members; ++m)
+        TRY(balloc(b, &b->pbits[m], (grids[member_grid[m]]->n_seg + 31) / 32));
+    // waves: wave k holds angle block k of every member whose grid has one
+    int maxblk = 0;
+    for (rt_grid *g : b->grids) maxblk = std::max(maxblk, g->nblk);
+    int64_t max_buf = 0, max_part = 0, max_cnt = 0;
+    for (int k = 0; k < maxblk; ++k) {
+        Wave w;
+        w.mi0 = (int64_t)b->h_mi.size();
+        int64_t buf = 0, part = 0, cnt = 0;
+        for (int m = 0; m < n_members; ++m) {
+            rt_grid *g = b->grids[b->mgrid[m]];
+            if (k >= g->nblk) continue;
+            const int w0 = g->blk_w0[k], nw = g->blk_nw[k];
+            const int64_t lo = g->h_ang_seg_off[w0], ns = g->h_ang_seg_off[w0 + nw] - lo;
+            MarchItem mi;
+            mi.vox = g->d_vox;
+            mi.len = g->d_len32;
+            mi.ray_off = g->d_ray_off;
+            mi.r_lo = g->h_ang_ray_off[w0];
+            mi.r_hi = g->h_ang_ray_off[w0 + nw];
+            mi.seg_lo = lo;
+            mi.nseg = ns;
+            mi.cs = b->cs + b->voff[m];
+            mi.B = b->B32 + b->voff[m];
+            mi.pbits = b->pbits[m];
+            mi.I_outer = (float)g->I_outer;
+            mi.out = (float *)(intptr_t)buf;  // offset for now
+            GatherItem gi;
+            gi.t = g->jt[k];
+            gi.t.cnt = (int *)(intptr_t)cnt;
+            gi.off = g->d_csr_off + (size_t)k * (g->nvox + 1);
+            gi.perm = g->d_perm + lo;
+            gi.buf = (const float *)(intptr_t)buf;
+            gi.ang_seg_off = g->d_ang_seg_off;
+            gi.wL = g->d_wL32;
+            gi.invL = g->d_invL;
+            gi.wt = g->d_wt;
+            gi.part = (double *)(intptr_t)part;
+            gi.J = b->J + b->voff[m];
+            gi.seg_lo = lo;
+            gi.w0 = w0;
+            gi.nw = nw;
+            gi.nvox = g->nvox;
+            gi.first = (k == 0);
+            gi.nbs = (gi.t.nshort + 255) / 256;
+            gi.nbc = (gi.t.nchunks * 32 + 255) / 256;
+            b->h_mi.push_back(mi);
+            b->h_gi.push_back(gi);
+            buf += ns;
+            part += std::max<int64_t>(1, gi.t.nchunks);
+            cnt += std::max(1, gi.t.nlong);
+            w.n++;
+        }
+        b->waves.push_back(w);
+        max_buf = std::max(max_buf, buf);
+        max_part = std::max(max_part, part);
+        max_cnt = std::max(max_cnt, cnt);
+    }
+    TRY(balloc(b, &b->wbuf, max_buf));
+    TRY(balloc(b, &b->wpart, max_part));
+    TRY(balloc(b, &b->wcnt, max_cnt));
+    if (cudaMemsetAsync(b->wcnt, 0, sizeof(int) * max_cnt, b->st) != cudaSuccess)
+        return fail_and_free(bfail(RT_ECUDA, "memset failed"));
+    for (size_t i = 0; i < b->h_mi.size(); ++i) {  // turn offsets into pointers
+        b->h_mi[i].out = b->wbuf + (intptr_t)b->h_mi[i].out;
+        b->h_gi[i].buf = b->wbuf + (intptr_t)b->h_gi[i].buf;
+        b->h_gi[i].part = b->wpart + (intptr_t)b->h_gi[i].part;
+        b->h_gi[i].t.cnt = b->wcnt + (intptr_t)b->h_gi[i].t.cnt;
+    }
+    TRY(balloc(b, &b->d_mi, b->h_mi.size()));
+    TRY(balloc(b, &b->d_gi, b->h_gi.size()));
+    if (cudaMemcpyAsync(b->d_mi, b->h_mi.data(), sizeof(MarchItem) * b->h_mi.size(), cudaMemcpyHostToDevice, b->st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(b->d_gi, b->h_gi.data(), sizeof(GatherItem) * b->h_gi.size(), cudaMemcpyHostToDevice, b->st) !=
+            cudaSuccess)
+        return fail_and_free(bfail(RT_ECUDA, "copy failed"));
+    TRY(build_prefixes(b));
+#undef TRY
+    *out = b;
+    return RT_OK;
+}
+
+int rt_batch_destroy(rt_batch *b)
+{
+    if (!b) return RT_OK;
+    cudaSetDevice(b->device);
+    if (b->st) cudaStreamSynchronize(b->st);
+    bfree_all(b);
+    delete b;
+    return RT_OK;
+}
+
+int rt_batch_set_member(rt_batch *b, int m, const double *chi, const double *eps, const double *B, int where)
+{
+    if (!b || !chi || !eps || !B) return bfail(RT_EINVAL, "NULL argument");
+    if (m < 0 || m >= b->nm) return bfail(RT_EINVAL, "member out of range");
+    if (where != RT_HOST && where != RT_DEVICE) return bfail(RT_EINVAL, "where must be RT_HOST or RT_DEVICE");
+    BCK(cudaSetDevice(b->device));
+    rt_grid *g = b->grids[b->mgrid[m]];
+    const int64_t n = g->nvox, o = b->voff[m];
+    if (where == RT_HOST) {
+        for (int64_t v = 0; v < n; ++v) {
+            if (!(chi[v] > 0.0) || !std::isfinite(chi[v])) return bfail(RT_EINVAL, "chi must be > 0 and finite");
+            if (!(eps[v] > 0.0 && eps[v] <= 1.0)) return bfail(RT_EINVAL, "eps must be in (0, 1]");
+            if (!(B[v] >= 0.0) || !std::isfinite(B[v])) return bfail(RT_EINVAL, "B must be >= 0 and finite");
+        }
+    }
+    const cudaMemcpyKind kind = where == RT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    BCK(cudaMemcpyAsync(b->chi + o, chi, sizeof(double) * n, kind, b->st));
+    BCK(cudaMemcpyAsync(b->eps + o, eps, sizeof(double) * n, kind, b->st));
+    BCK(cudaMemcpyAsync(b->B + o, B, sizeof(double) * n, kind, b->st));
+    BCK(cudaMemcpyAsync(b->S + o, b->B + o, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->st));
+    BCK(para_bits(g->d_vox, g->d_len64, b->chi + o, g->n_seg, g->interp == RT_PARABOLIC, b->pbits[m], b->st));
+    // this member's Lambda* (depends on its chi only): one full FP32 formal solution
+    k_bpack<<<152 * 4, 256, 0, b->st>>>(n, b->chi + o, b->S + o, b->B + o, b->cs + o, b->B32 + o);
+    BCK(cudaGetLastError());
+    BCK(cudaStreamSynchronize(b->st));
+    BCK(cudaStreamSynchronize(g->st));
+    BRCK(rt_grid_member_fs(g, b->cs + o, b->B32 + o, b->pbits[m], b->J + o, b->L + o, b->Fc, b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    b->ready[m] = 1;
+    b->history.clear();
+    return RT_OK;
+}
+
+int rt_batch_ali_step(rt_batch *b, double *max_rel_dS)
+{
+    if (!b) return bfail(RT_EINVAL, "batch is NULL");
+    BCK(cudaSetDevice(b->device));
+    return step(b, max_rel_dS);
+}
+
+int rt_batch_solve(rt_batch *b, double tol, int max_iter, int32_t *iters)
+{
+    if (!b) return bfail(RT_EINVAL, "batch is NULL");
+    if (!(tol > 0.0) || max_iter < 1) return bfail(RT_EINVAL, "need tol > 0 and max_iter >= 1");
+    BCK(cudaSetDevice(b->device));
+    std::vector<double> rel(b->nm);
+    std::vector<int32_t> done(b->nm, 0);
+    b->history.clear();
+    for (int it = 1; it <= max_iter; ++it) {
+        BRCK(step(b, rel.data()));
+        bool all = true;
+        for (int m = 0; m < b->nm; ++m) {
+            if (!done[m] && rel[m] < tol) done[m] = it;
+            all = all && done[m];
+        }
+        if (all) {
+            if (iters) std::copy(done.begin(), done.end(), iters);
+            return RT_OK;
+        }
+    }
+    if (iters) std::copy(done.begin(), done.end(), iters);
+    return bfail(RT_ENOTCONVERGED, "not every member converged in " + std::to_string(max_iter) + " iterations");
+}
+
+int rt_batch_get(const rt_batch *b, int m, int what, double *out, int where)
+{
+    if (!b || !out) return bfail(RT_EINVAL, "NULL argument");
+    if (m < 0 || m >= b->nm) return bfail(RT_EINVAL, "member out of range");
+    if (where != RT_HOST && where != RT_DEVICE) return bfail(RT_EINVAL, "where must be RT_HOST or RT_DEVICE");
+    const double *src = what == 0 ? b->S : what == 1 ? b->J : what == 2 ? b->L : nullptr;
+    if (!src) return bfail(RT_EINVAL, "what must be 0 (S), 1 (J) or 2 (Lambda*)");
+    BCK(cudaSetDevice(b->device));
+    const int64_t n = b->voff[m + 1] - b->voff[m];
+    BCK(cudaMemcpyAsync(out, src + b->voff[m], sizeof(double) * n,
+                        where == RT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    return RT_OK;
+}
+
+int rt_batch_autotune(rt_batch *b, int32_t *chunk_out, int32_t *grid_out, double *ms_out)
+{
+    if (!b) return bfail(RT_EINVAL, "batch is NULL");
+    BCK(cudaSetDevice(b->device));
+    for (int m = 0; m < b->nm; ++m)
+        if (!b->ready[m]) return bfail(RT_EINVAL, "set every member before autotuning");
+    double *saveS = nullptr;
+    BRCK(balloc(b, &saveS, b->ntot));
+    BCK(cudaMemcpyAsync(saveS, b->S, sizeof(double) * b->ntot, cudaMemcpyDeviceToDevice, b->st));
+    const int chunks[3] = {512, 1024, 2048};
+    const int grids[2] = {152 * 4, 152 * 8};
+    double best = 1e300;
+    int bc = b->chunk, bg = b->grid_march;
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    for (int c : chunks)
+        for (int gsz : grids) {
+            b->chunk = c;
+            b->grid_march = b->grid_gather = gsz;
+            BRCK(build_prefixes(b));
+            BRCK(capture(b));
+            BCK(cudaGraphLaunch(b->graph, b->st));
+            BCK(cudaEventRecord(e0, b->st));
+            BCK(cudaGraphLaunch(b->graph, b->st));
+            BCK(cudaGraphLaunch(b->graph, b->st));
+            BCK(cudaEventRecord(e1, b->st));
+            BCK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BCK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms / 2 < best) {
+                best = ms / 2;
+                bc = c;
+                bg = gsz;
+            }
+            BCK(cudaMemcpyAsync(b->S, saveS, sizeof(double) * b->ntot, cudaMemcpyDeviceToDevice, b->st));
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->chunk = bc;
+    b->grid_march = b->grid_gather = bg;
+    BRCK(build_prefixes(b));
+    BRCK(capture(b));
+    BCK(cudaStreamSynchronize(b->st));
+    auto it = std::find(b->allocs.begin(), b->allocs.end(), (void *)saveS);
+    if (it != b->allocs.end()) b->allocs.erase(it);
+    cudaFree(saveS);
+    b->history.clear();
+    if (chunk_out) *chunk_out = bc;
+    if (grid_out) *grid_out = bg;
+    if (ms_out) *ms_out = best;
+    return RT_OK;
+}
+
+}  // extern "C"

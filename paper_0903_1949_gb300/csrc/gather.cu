@@ -542,6 +542,81 @@ __device__ __forceinline__ int angle_of(const int32_t *soff, int nw, int s)
     return lo;
 }
 
+// One short list (thread i of the sliced-ELL order) into J.
+template <typename T>
+__device__ __forceinline__ void gj_short(int64_t i, int nvox, const int32_t *__restrict__ off,
+                                         const int32_t *__restrict__ jorder, const int64_t *__restrict__ jgbase,
+                                         const int32_t *__restrict__ jsell, const T *__restrict__ buf,
+                                         const int32_t *soff, const double *swt, int w0, int nw,
+                                         const float *__restrict__ wL, const double *__restrict__ invL, double *J,
+                                         int first)
+{
+    const int v = jorder[i];
+    const int L = off[v + 1] - off[v];
+    const int32_t *lst = jsell + jgbase[i >> 5] + (i & 31);
+    JAcc<T> acc;
+    if (L > 0) {
+        int q = angle_of(soff, nw, lst[0]);
+        T f = JW<T>::weight(wL, swt, invL, w0 + q, q, nvox, v);
+        for (int k = 0; k < L; k += 4) {
+            int ss[4];
+            T val[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) ss[j] = (k + j < L) ? lst[32 * (k + j)] : -1;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (ss[j] >= 0) val[j] = buf[ss[j]];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (ss[j] < 0) continue;
+                while (ss[j] >= soff[q + 1]) {
+                    ++q;
+                    f = JW<T>::weight(wL, swt, invL, w0 + q, q, nvox, v);
+                }
+                acc.add(f * val[j]);
+            }
+        }
+    }
+    const double r = acc.value();
+    J[v] = first ? r : J[v] + r;
+}
+
+// One chunk of a long list (one warp); the warp that completes a voxel's last
+// chunk adds all its chunk sums in chunk order.
+template <typename T>
+__device__ __forceinline__ void gj_chunk(int64_t c, int lane, int nvox, const int32_t *__restrict__ off,
+                                         const int32_t *__restrict__ perm, int64_t nchunks,
+                                         const int32_t *__restrict__ crow, const int32_t *__restrict__ cbeg,
+                                         const int32_t *__restrict__ clr, const int32_t *__restrict__ lfirst, int nlong,
+                                         int *cnt, double *part, const T *__restrict__ buf, const int32_t *soff,
+                                         const double *swt, int w0, int nw, const float *__restrict__ wL,
+                                         const double *__restrict__ invL, double *J, int first)
+{
+    const int v = crow[c];
+    const int e0 = cbeg[c];
+    const int e1 = min(e0 + CHUNK_LEN, off[v + 1]);
+    JAcc<T> acc;
+    for (int e = e0 + lane; e < e1; e += 32) {
+        const int s = perm[e];
+        const int q = angle_of(soff, nw, s);
+        acc.add(JW<T>::weight(wL, swt, invL, w0 + q, q, nvox, v) * buf[s]);
+    }
+    acc.warp_reduce();
+    if (lane == 0) {
+        const int lr = clr[c];
+        __stcg(part + c, acc.value());
+        __threadfence();
+        const int c0 = lfirst[lr], c1 = (lr + 1 < nlong) ? lfirst[lr + 1] : (int)nchunks;
+        if (atomicAdd(cnt + lr, 1) == c1 - c0 - 1) {
+            __threadfence();
+            double r = 0.0;
+            for (int cc = c0; cc < c1; ++cc) r += __ldcg(part + cc);
+            J[v] = first ? r : J[v] + r;
+            cnt[lr] = 0;
+        }
+    }
+}
+
 // Blocks [0, nbs) sum short lists (thread per voxel); the rest are warps over chunks of long lists.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gatherJ(int nvox, int64_t nshort, int nbs, const int32_t *__restrict__ off,
@@ -562,63 +637,62 @@ __global__ void __launch_bounds__(256) k_gatherJ(int nvox, int64_t nshort, int n
     __syncthreads();
     if ((int)blockIdx.x < nbs) {
         const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-        if (i >= nshort) return;
-        const int v = jorder[i];
-        const int L = off[v + 1] - off[v];
-        const int32_t *lst = jsell + jgbase[i >> 5] + (i & 31);
-        JAcc<T> acc;
-        if (L > 0) {
-            int q = angle_of(soff, nw, lst[0]);
-            T f = JW<T>::weight(wL, swt, invL, w0 + q, q, nvox, v);
-            for (int k = 0; k < L; k += 4) {
-                int ss[4];
-                T val[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) ss[j] = (k + j < L) ? lst[32 * (k + j)] : -1;
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (ss[j] >= 0) val[j] = buf[ss[j]];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (ss[j] < 0) continue;
-                    while (ss[j] >= soff[q + 1]) {
-                        ++q;
-                        f = JW<T>::weight(wL, swt, invL, w0 + q, q, nvox, v);
-                    }
-                    acc.add(f * val[j]);
-                }
-            }
-        }
-        const double r = acc.value();
-        J[v] = first ? r : J[v] + r;
+        if (i < nshort) gj_short<T>(i, nvox, off, jorder, jgbase, jsell, buf, soff, swt, w0, nw, wL, invL, J, first);
         return;
     }
-    const int lane = threadIdx.x & 31;
     const int64_t c = ((int64_t)(blockIdx.x - nbs) * blockDim.x + threadIdx.x) >> 5;
-    if (c >= nchunks) return;
-    const int v = crow[c];
-    const int e0 = cbeg[c];
-    const int e1 = min(e0 + CHUNK_LEN, off[v + 1]);
-    JAcc<T> acc;
-    for (int e = e0 + lane; e < e1; e += 32) {
-        const int s = perm[e];
-        const int q = angle_of(soff, nw, s);
-        acc.add(JW<T>::weight(wL, swt, invL, w0 + q, q, nvox, v) * buf[s]);
-    }
-    acc.warp_reduce();
-    if (lane == 0) {
-        const int lr = clr[c];
-        __stcg(part + c, acc.value());
-        __threadfence();
-        const int c0 = lfirst[lr], c1 = (lr + 1 < nlong) ? lfirst[lr + 1] : (int)nchunks;
-        if (atomicAdd(cnt + lr, 1) == c1 - c0 - 1) {
-            // last chunk of this voxel: add all chunk sums in chunk order
-            __threadfence();
-            double r = 0.0;
-            for (int cc = c0; cc < c1; ++cc) r += __ldcg(part + cc);
-            J[v] = first ? r : J[v] + r;
-            cnt[lr] = 0;
+    if (c < nchunks)
+        gj_chunk<T>(c, threadIdx.x & 31, nvox, off, perm, nchunks, crow, cbeg, clr, lfirst, nlong, cnt, part, buf, soff,
+                    swt, w0, nw, wL, invL, J, first);
+}
+
+// Persistent batched J gather (FP32): every CTA takes work units (one block
+// worth of short lists or chunks of one member's angle block) from a device
+// counter; wpfx[i] = first work unit of item i.
+__global__ void __launch_bounds__(256) k_gatherJ_batch(const GatherItem *__restrict__ items,
+                                                       const int64_t *__restrict__ wpfx, int n_items, int64_t total,
+                                                       unsigned long long *counter)
+{
+    __shared__ int32_t soff[MAX_BLOCK_ANGLES + 1];
+    __shared__ double swt[MAX_BLOCK_ANGLES];
+    __shared__ long long s_unit;
+    __shared__ int s_item;
+    for (int guard = 0; guard < (1 << 30); ++guard) {
+        if (threadIdx.x == 0) {
+            unsigned long long u = atomicAdd(counter, 1ull);
+            int lo = 0, hi = n_items;
+            if ((int64_t)u < total) {
+                while (hi - lo > 1) {
+                    int mid = (lo + hi) >> 1;
+                    if (wpfx[mid] <= (int64_t)u) lo = mid;
+                    else hi = mid;
+                }
+            }
+            s_unit = (long long)u;
+            s_item = lo;
         }
+        __syncthreads();
+        const int64_t u = s_unit;
+        if (u >= total) return;
+        const GatherItem &it = items[s_item];
+        for (int q = threadIdx.x; q <= it.nw; q += blockDim.x)
+            soff[q] = (int32_t)(it.ang_seg_off[it.w0 + q] - it.seg_lo);
+        for (int q = threadIdx.x; q < it.nw; q += blockDim.x) swt[q] = it.wt[it.w0 + q];
+        __syncthreads();
+        const int64_t bi = u - wpfx[s_item];
+        if (bi < it.nbs) {
+            const int64_t i = bi * blockDim.x + threadIdx.x;
+            if (i < it.t.nshort)
+                gj_short<float>(i, it.nvox, it.off, it.t.jorder, it.t.jgbase, it.t.jsell, it.buf, soff, swt, it.w0,
+                                it.nw, it.wL, it.invL, it.J, it.first);
+        } else {
+            const int64_t c = ((bi - it.nbs) * blockDim.x + threadIdx.x) >> 5;
+            if (c < it.t.nchunks)
+                gj_chunk<float>(c, threadIdx.x & 31, it.nvox, it.off, it.perm, it.t.nchunks, it.t.crow, it.t.cbeg,
+                                it.t.clr, it.t.lfirst, it.t.nlong, it.t.cnt, it.part, it.buf, soff, swt, it.w0, it.nw,
+                                it.wL, it.invL, it.J, it.first);
+        }
+        __syncthreads();
     }
 }
 
@@ -803,6 +877,14 @@ cudaError_t gather_J(int nvox, const int32_t *csr_off, const GatherJTables &t, c
     k_gatherJ<T><<<(unsigned)grid, 256, 0, st>>>(nvox, t.nshort, nbs, csr_off, t.jorder, t.jgbase, t.jsell, t.nchunks,
                                                  t.crow, t.cbeg, t.clr, t.lfirst, t.nlong, t.cnt, part, perm_blk, buf,
                                                  ang_seg_off, w0, nw, seg_lo, wL32, invL, wt, J, first);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_J_batch(const GatherItem *items, const int64_t *wpfx, int n_items, int64_t total,
+                           unsigned long long *counter, int grid_blocks, cudaStream_t st)
+{
+    if (total <= 0) return cudaSuccess;
+    k_gatherJ_batch<<<grid_blocks, 256, 0, st>>>(items, wpfx, n_items, total, counter);
     return cudaGetLastError();
 }
 

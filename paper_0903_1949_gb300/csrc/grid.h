@@ -71,3 +71,9 @@ struct rt_grid {
     int64_t launches = 0;
     int march_chunk = 512;  // segments per warp bundle (RT_TUNE_MARCH_CHUNK)
 };
+
+// FP32 formal solution of another opacity field on this grid's geometry (a
+// batch member): (chi, S) packed in cs, B in B32, parabola choices in pbits.
+// Writes J, Lambda* and the Cartesian flux sums Fc; returns an RT_ status.
+int rt_grid_member_fs(rt_grid *g, const float2 *cs, const float *B32, const uint32_t *pbits, double *J, double *L,
+                      double *Fc, cudaStream_t st);

@@ -148,17 +148,18 @@ __device__ __forceinline__ int64_t lower_bound64(const int64_t *a, int64_t lo, i
 // the scan, shuffle and index work per segment is divided by K.  The next
 // tile's segment words and lengths are fetched before the current tile is
 // processed.
-template <typename T, typename P, int K, bool LAM>
-__global__ void __launch_bounds__(256) k_march4(const uint32_t *__restrict__ vox, const T *__restrict__ len,
-                                                const int64_t *__restrict__ ray_off, int64_t r_lo, int64_t r_hi,
-                                                int64_t seg_lo, int64_t nseg, const P *__restrict__ cs,
-                                                const T *__restrict__ Bv, T I_outer, int homog,
-                                                void *__restrict__ outv, int chunk)
+// Bundle wg of one angle block.  BITS: the parabola choice of segment s comes
+// from bit s of pbits (per-member choices of a batch) instead of RTK_PARA.
+template <typename T, typename P, int K, bool LAM, bool BITS>
+__device__ __forceinline__ void march_bundle(const uint32_t *__restrict__ vox, const T *__restrict__ len,
+                                             const int64_t *__restrict__ ray_off, int64_t r_lo, int64_t r_hi,
+                                             int64_t seg_lo, int64_t nseg, int64_t wg, const P *__restrict__ cs,
+                                             const T *__restrict__ Bv, T I_outer, int homog, void *__restrict__ outv,
+                                             int chunk, const uint32_t *__restrict__ pbits)
 {
     using C = typename Traits<T>::C;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t c_lo = wg * chunk;
     if (c_lo >= nseg) return;
     const int64_t c_hi = (c_lo + chunk < nseg) ? c_lo + chunk : nseg;
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(256) k_march4(const uint32_t *__restrict__ vox
         T A[K], b[K], lam[K];
         T gam_prev_lane;  // gamma of the previous lane's last segment, filled after the coefficients
         T E[K], al[K], be[K], ga[K];
-        bool run0[K];
+        bool run0[K], paraj[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             const int s = s0 + j;
@@ -238,7 +239,12 @@ __global__ void __launch_bounds__(256) k_march4(const uint32_t *__restrict__ vox
             run0[j] = (w[j] & (RTK_RAYSTART | RTK_RESTART)) != 0u;
             const T x = valid ? chi[j] * l[j] : (T)1;
             const T pp = last ? (T)0 : chn * lnn;
-            const bool para = (w[j] & RTK_PARA) != 0u;
+            bool para = (w[j] & RTK_PARA) != 0u;
+            if (BITS) {
+                const int64_t gs = seg_lo + s;
+                para = valid && ((pbits[gs >> 5] >> (gs & 31)) & 1u);
+            }
+            paraj[j] = para;
             C::eval(x, pp, para, E[j], al[j], be[j], ga[j]);
         }
         gam_prev_lane = __shfl_up_sync(FULL, ga[K - 1], 1);
@@ -250,7 +256,7 @@ __global__ void __launch_bounds__(256) k_march4(const uint32_t *__restrict__ vox
             const T Sm = (j == 0) ? Sp : S[j - 1];
             const T gm = (j == 0) ? gam_prev_lane : ga[j - 1];
             const T Sn = (j + 1 < K) ? S[j + 1] : Snx;
-            const bool para = (w[j] & RTK_PARA) != 0u;
+            const bool para = paraj[j];
             const T Skm = run0[j] ? S[j] : Sm;
             const T src = al[j] * Skm + be[j] * S[j] + (para ? ga[j] * Sn : (T)0);
             if (LAM) lam[j] = be[j] + (run0[j] ? al[j] : gm * E[j]);
@@ -315,6 +321,83 @@ __global__ void __launch_bounds__(256) k_march4(const uint32_t *__restrict__ vox
     }
 }
 
+template <typename T, typename P, int K, bool LAM>
+__global__ void __launch_bounds__(256) k_march4(const uint32_t *__restrict__ vox, const T *__restrict__ len,
+                                                const int64_t *__restrict__ ray_off, int64_t r_lo, int64_t r_hi,
+                                                int64_t seg_lo, int64_t nseg, const P *__restrict__ cs,
+                                                const T *__restrict__ Bv, T I_outer, int homog,
+                                                void *__restrict__ outv, int chunk)
+{
+    const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    march_bundle<T, P, K, LAM, false>(vox, len, ray_off, r_lo, r_hi, seg_lo, nseg, wg, cs, Bv, I_outer, homog, outv,
+                                      chunk, nullptr);
+}
+
+// Full march (l I and l lambda) with the parabola choices of a bitmask.
+__global__ void __launch_bounds__(256) k_march_bits(const uint32_t *__restrict__ vox, const float *__restrict__ len,
+                                                    const int64_t *__restrict__ ray_off, int64_t r_lo, int64_t r_hi,
+                                                    int64_t seg_lo, int64_t nseg, const float2 *__restrict__ cs,
+                                                    const float *__restrict__ Bv, float I_outer,
+                                                    void *__restrict__ outv, int chunk,
+                                                    const uint32_t *__restrict__ pbits)
+{
+    const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    march_bundle<float, float2, 2, true, true>(vox, len, ray_off, r_lo, r_hi, seg_lo, nseg, wg, cs, Bv, I_outer, 0,
+                                               outv, chunk, pbits);
+}
+
+// Persistent batched march (FP32, J only): the warps of a grid sized to the
+// GPU take bundles of all work items (member x angle block, uneven grids
+// mixed) from a device counter until none is left.
+__global__ void __launch_bounds__(256) k_march_batch(const MarchItem *__restrict__ items,
+                                                     const int64_t *__restrict__ bpfx, int n_items, int64_t total,
+                                                     int chunk, int homog, unsigned long long *counter)
+{
+    const int lane = threadIdx.x & 31;
+    for (int guard = 0; guard < (1 << 30); ++guard) {
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(counter, 1ull);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if ((int64_t)b >= total) return;
+        int lo = 0, hi = n_items;  // item: bpfx[item] <= b < bpfx[item+1]
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (bpfx[mid] <= (int64_t)b) lo = mid;
+            else hi = mid;
+        }
+        const MarchItem &it = items[lo];
+        march_bundle<float, float2, 2, false, true>(it.vox, it.len, it.ray_off, it.r_lo, it.r_hi, it.seg_lo, it.nseg,
+                                                    (int64_t)b - bpfx[lo], it.cs, it.B, it.I_outer, homog, it.out,
+                                                    chunk, it.pbits);
+    }
+}
+
+// Per-member parabola choices as a bitmask (bit s of segment s), from that
+// member's chi in FP64 (same rule as k_mark_parabola).
+__global__ void k_para_bits(const uint32_t *vox, const double *len64, const double *chi, int64_t nseg, int parabolic,
+                            uint32_t *bits)
+{
+    const int64_t nwords = (nseg + 31) / 32;
+    for (int64_t wi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; wi < nwords; wi += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t word = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int64_t s = wi * 32 + b;
+            if (s >= nseg) break;
+            bool para = false;
+            if (parabolic && s + 1 < nseg) {
+                const uint32_t w = vox[s], wn = vox[s + 1];
+                if (!(wn & (RTK_RAYSTART | RTK_RESTART))) {
+                    double x = chi[w & RTK_VOXMASK] * len64[s];
+                    double p = chi[wn & RTK_VOXMASK] * len64[s + 1];
+                    para = p >= 0.5 * x;
+                }
+            }
+            if (para) word |= 1u << b;
+        }
+        bits[wi] = word;
+    }
+}
+
 __global__ void k_mark_parabola(uint32_t *vox, const double *len64, const double *chi, int64_t nseg, int parabolic)
 {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nseg; s += (int64_t)gridDim.x * blockDim.x) {
@@ -376,6 +459,37 @@ cudaError_t march_block_J(const uint32_t *vox, const T *len, const int64_t *ray_
     else
         k_march4<T, P, 1, false><<<(unsigned)blocks, 256, 0, st>>>(vox, len, ray_off, r_lo, r_hi, seg_lo, nseg, chiS, B,
                                                                    I_outer, homog, out, chunk);
+    return cudaGetLastError();
+}
+
+cudaError_t march_batch(const MarchItem *items, const int64_t *bpfx, int n_items, int64_t total, int chunk, int homog,
+                        unsigned long long *counter, int grid_blocks, cudaStream_t st)
+{
+    if (total <= 0) return cudaSuccess;
+    k_march_batch<<<grid_blocks, 256, 0, st>>>(items, bpfx, n_items, total, chunk, homog, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t march_block_bits(const uint32_t *vox, const float *len, const int64_t *ray_off, int64_t r_lo, int64_t r_hi,
+                             int64_t seg_lo, int64_t nseg, const float2 *chiS, const float *B, float I_outer,
+                             float2 *out, int chunk, const uint32_t *pbits, cudaStream_t st)
+{
+    if (nseg <= 0) return cudaSuccess;
+    int64_t warps = (nseg + chunk - 1) / chunk;
+    int64_t blocks = (warps + 7) / 8;
+    k_march_bits<<<(unsigned)blocks, 256, 0, st>>>(vox, len, ray_off, r_lo, r_hi, seg_lo, nseg, chiS, B, I_outer, out,
+                                                   chunk, pbits);
+    return cudaGetLastError();
+}
+
+cudaError_t para_bits(const uint32_t *vox, const double *len64, const double *chi, int64_t nseg, int parabolic,
+                      uint32_t *bits, cudaStream_t st)
+{
+    if (nseg <= 0) return cudaSuccess;
+    int64_t words = (nseg + 31) / 32;
+    int64_t blocks = (words + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_para_bits<<<(unsigned)blocks, 256, 0, st>>>(vox, len64, chi, nseg, parabolic, bits);
     return cudaGetLastError();
 }
 

@@ -737,6 +737,28 @@ int check_lost(rt_grid *g)
 
 }  // namespace
 
+int rt_grid_member_fs(rt_grid *g, const float2 *cs, const float *B32, const uint32_t *pbits, double *J, double *L,
+                      double *Fc, cudaStream_t st)
+{
+    const int n = g->nvox;
+    for (int b = 0; b < g->nblk; ++b) {
+        int w0 = g->blk_w0[b], nw = g->blk_nw[b];
+        int64_t r_lo = g->h_ang_ray_off[w0], r_hi = g->h_ang_ray_off[w0 + nw];
+        int64_t lo = g->h_ang_seg_off[w0], ns = g->h_ang_seg_off[w0 + nw] - lo;
+        const int32_t *off = g->d_csr_off + (size_t)b * (n + 1);
+        float2 *buf = (float2 *)g->d_segbuf;
+        CK(march_block_bits(g->d_vox, g->d_len32, g->d_ray_off, r_lo, r_hi, lo, ns, cs, B32, (float)g->I_outer, buf,
+                            g->march_chunk, pbits, st));
+        CK(gather_block<float2>(n, off, g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->d_wL32,
+                                g->d_wt, g->d_dirs, g->d_urow + g->h_ubase[b], g->d_ubeg + g->h_ubase[b],
+                                g->d_ufirst + (size_t)b * (n + 1), g->h_nunits[b], g->d_multi + g->h_mbase[b],
+                                (int)(g->h_mbase[b + 1] - g->h_mbase[b]), g->d_order + g->h_ubase[b],
+                                g->d_ulen + g->h_ubase[b], g->d_gbase + g->h_goff[b], g->d_sell + g->h_soff[b],
+                                g->d_part, J, L, Fc, b == 0, st));
+    }
+    return RT_OK;
+}
+
 extern "C" {
 
 const char *rt_last_error(void) { return g_err.c_str(); }

@@ -115,6 +115,24 @@ cudaError_t gather_J(int nvox, const int32_t *csr_off, const GatherJTables &t, c
                      const int64_t *ang_seg_off, int w0, int nw, int64_t seg_lo, const float *wL32,
                      const double *invL, const double *wt, double *part, double *J, int first, cudaStream_t st);
 
+// One batched J-gather work item: an angle block of one member (FP32 buffer).
+// nbs = blocks of short lists, nbc = blocks of long-list chunks (8 chunks each).
+struct GatherItem {
+    GatherJTables t;        // tables of the grid's block, with this member's cnt slice
+    const int32_t *off, *perm;
+    const float *buf;
+    const int64_t *ang_seg_off;
+    const float *wL;
+    const double *invL, *wt;
+    double *part;           // this member's chunk sums
+    double *J;              // this member's J
+    int64_t seg_lo;
+    int w0, nw, nvox, first;
+    int64_t nbs, nbc;
+};
+cudaError_t gather_J_batch(const GatherItem *items, const int64_t *wpfx, int n_items, int64_t total,
+                           unsigned long long *counter, int grid_blocks, cudaStream_t st);
+
 // Ibar, Lbar of one solid angle whose segments are [s_lo, s_hi) of the block.
 cudaError_t gather_angle_range(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const void *buf, int fp32,
                                int64_t s_lo, int64_t s_hi, const double *invL_w, double *Ibar, double *Lbar,
@@ -128,6 +146,26 @@ template <typename T, typename P>
 cudaError_t march_block_J(const uint32_t *vox, const T *len, const int64_t *ray_off, int64_t r_lo, int64_t r_hi,
                           int64_t seg_lo, int64_t nseg, const P *chiS, const T *B, T I_outer, int homog, T *out,
                           int chunk, cudaStream_t st);
+// One batched march work item: an angle block of one member (FP32, J only).
+struct MarchItem {
+    const uint32_t *vox;
+    const float *len;
+    const int64_t *ray_off;
+    int64_t r_lo, r_hi, seg_lo, nseg;
+    const float2 *cs;      // member (chi, S) per voxel
+    const float *B;        // member B (FP32) for characteristics leaving the core
+    const uint32_t *pbits; // member parabola choices, bit per segment of the grid
+    float I_outer;
+    float *out;            // l I per segment of the block (wave scratch)
+};
+// bpfx[i] = first bundle of item i (n_items + 1 entries); counter starts at 0.
+cudaError_t march_batch(const MarchItem *items, const int64_t *bpfx, int n_items, int64_t total, int chunk, int homog,
+                        unsigned long long *counter, int grid_blocks, cudaStream_t st);
+cudaError_t march_block_bits(const uint32_t *vox, const float *len, const int64_t *ray_off, int64_t r_lo, int64_t r_hi,
+                             int64_t seg_lo, int64_t nseg, const float2 *chiS, const float *B, float I_outer,
+                             float2 *out, int chunk, const uint32_t *pbits, cudaStream_t st);
+cudaError_t para_bits(const uint32_t *vox, const double *len64, const double *chi, int64_t nseg, int parabolic,
+                      uint32_t *bits, cudaStream_t st);
 // Parabola-guard decision per segment, taken once in FP64 from chi and the FP64
 // lengths (dtau_{k+1} >= dtau_k / 2 and not the last node of a run), stored in
 // the RTK_PARA bit so the FP32 and FP64 marches use identical interpolants.

@@ -91,6 +91,14 @@ def load():
         "rt_set_precision": [_P, _I],
         "rt_tune": [_P, _I, _I],
         "rt_fs_angle_noalloc": [_P, _I, _I, _P, _P],
+        "rt_batch_create": [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _I, _P, _P],
+        "rt_batch_destroy": [_P],
+        "rt_batch_set_member": [_P, _I, _P, _P, _P, _I],
+        "rt_batch_ali_step": [_P, _P],
+        "rt_batch_solve": [_P, ctypes.c_double, _I, _P],
+        "rt_batch_get": [_P, _I, _I, _P, _I],
+        "rt_batch_autotune": [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                              ctypes.POINTER(ctypes.c_double)],
         "rt_get_timing": [_P, ctypes.POINTER(rt_timing)],
     }
     for name, args in sig.items():
@@ -272,6 +280,96 @@ def rt_get_timing(h):
     t = rt_timing()
     _check(load().rt_get_timing(h, ctypes.byref(t)))
     return {k: getattr(t, k) for k, _ in rt_timing._fields_}
+
+
+def rt_batch_create(grid_handles, member_grid, stream=None):
+    L = load()
+    arr = (ctypes.c_void_p * len(grid_handles))(*[h.value if hasattr(h, "value") else h for h in grid_handles])
+    mg = np.ascontiguousarray(member_grid, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(L.rt_batch_create(ctypes.byref(h), ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), len(grid_handles),
+                             len(mg), ctypes.c_void_p(mg.ctypes.data), stream if stream else None))
+    return h
+
+
+def rt_batch_destroy(h):
+    return _check(load().rt_batch_destroy(h))
+
+
+def rt_batch_set_member(h, m, chi, eps, B):
+    pc, wc, k1 = _ptr(chi)
+    pe, we, k2 = _ptr(eps)
+    pb, wb, k3 = _ptr(B)
+    if not (wc == we == wb):
+        raise TypeError("chi, eps and B must live in the same memory space")
+    return _check(load().rt_batch_set_member(h, int(m), pc, pe, pb, wc))
+
+
+def rt_batch_ali_step(h, n_members):
+    rel = np.empty(n_members)
+    _check(load().rt_batch_ali_step(h, ctypes.c_void_p(rel.ctypes.data)))
+    return rel
+
+
+def rt_batch_solve(h, tol, max_iter, n_members):
+    it = np.zeros(n_members, np.int32)
+    rc = load().rt_batch_solve(h, float(tol), int(max_iter), ctypes.c_void_p(it.ctypes.data))
+    if rc not in (RT_OK, RT_ENOTCONVERGED):
+        _check(rc)
+    return it, rc == RT_OK
+
+
+def rt_batch_get(h, m, what, n_vox, out=None):
+    return _get(lambda hh, p, w: load().rt_batch_get(hh, int(m), int(what), p, w), h, n_vox, out)
+
+
+def rt_batch_autotune(h):
+    c, g, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(load().rt_batch_autotune(h, ctypes.byref(c), ctypes.byref(g), ctypes.byref(ms)))
+    return c.value, g.value, ms.value
+
+
+class Batch:
+    """Many opacity fields on a few grids, iterated together (see rt_batch_* in rt.h)."""
+
+    def __init__(self, grids, member_grid, stream=None):
+        self.grids = list(grids)  # kept alive: the batch uses their geometry
+        self.member_grid = list(member_grid)
+        self.h = None
+        self.h = rt_batch_create([g.h for g in self.grids], member_grid, stream)
+        self.nvox = [self.grids[q].nvox for q in self.member_grid]
+
+    def close(self):
+        if self.h:
+            rt_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_member(self, m, chi, eps, B):
+        rt_batch_set_member(self.h, m, chi, eps, B)
+
+    def ali_step(self):
+        return rt_batch_ali_step(self.h, len(self.member_grid))
+
+    def solve(self, tol, max_iter):
+        return rt_batch_solve(self.h, tol, max_iter, len(self.member_grid))
+
+    def S(self, m):
+        return rt_batch_get(self.h, m, 0, self.nvox[m])
+
+    def J(self, m):
+        return rt_batch_get(self.h, m, 1, self.nvox[m])
+
+    def Lstar(self, m):
+        return rt_batch_get(self.h, m, 2, self.nvox[m])
+
+    def autotune(self):
+        return rt_batch_autotune(self.h)
 
 
 class Grid:
