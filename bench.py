@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-equal-error", action="store_true", help="skip the equal-J-error solver comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-angles", type=int, default=48, help="solid angles in the CPU oracle sample")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-wavelength batch measurement")
     return ap.parse_args()
 
 
@@ -308,6 +309,13 @@ def main():
     if not args.no_equal_error and rank == 0:
         equal = equal_error(g, p, rt, torch)
 
+    batch = None
+    if not args.no_batch and rank == 0:
+        g.close()
+        g = None
+        torch.cuda.empty_cache()
+        batch = batch_measure(rt, I, torch, max(3, args.steps // 3))
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 march + f32 (compensated) gather, f64 ALI/Ng",
@@ -337,18 +345,56 @@ def main():
             "clocks": ck}
     if equal is not None:
         line["equal_error"] = equal
+    if batch is not None:
+        line["batch"] = batch
     if rank == 0 and not args.no_cpu:
         try:
             line["cpu_baseline"] = cpu_oracle_sample(p, args.cpu_angles)
         except Exception as exc:  # the oracle is a baseline, never the product path
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": "failed: %s" % exc}
-    g.close()
+    if g is not None:
+        g.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def batch_measure(rt, I, torch, steps):
+    """256 wavelengths on three spherical grids of uneven size, one CUDA-graph iteration each step."""
+    t0 = time.perf_counter()
+    grids_in, member_grid, members = I.make_batch_problem()
+    grids = [rt.Grid(q["coord"], q["edges"], q["dirs"], q["weights"], inner_bc=q["inner_bc"], precision=rt.RT_MIXED,
+                     ng=False) for q in grids_in]
+    t_geom = time.perf_counter() - t0
+    b = rt.Batch(grids, member_grid)
+    t1 = time.perf_counter()
+    for m, f in enumerate(members):
+        b.set_member(m, *f)
+    t_members = time.perf_counter() - t1
+    chunk, gsz, tune_ms = b.autotune()
+    b.ali_step()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    for _ in range(steps):
+        rel = b.ali_step()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t2) * 1e3 / steps
+    units = sum(grids[q].nvox * grids[q].n_ang for q in member_grid)
+    segs = sum(grids[q].info()["n_segments"] for q in member_grid)
+    out = {"workload": "256 wavelengths round-robin on spherical 33x17x33, 65x33x65, 97x49x97 voxels, 16x16 solid "
+                       "angles; chi scale log-U(1e-2, 1e2), eps log-U(1e-6, 1e-2); FP32 march + FP64 ALI, "
+                       "one CUDA graph per iteration",
+           "value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "voxel_angles_per_step": units, "segments_per_step": segs, "autotuned_chunk": chunk,
+           "autotuned_grid": gsz, "autotune_ms_per_step": tune_ms, "geometry_s": t_geom,
+           "member_setup_s": t_members, "max_rel_dS_last": float(np.max(rel))}
+    b.close()
+    for q in grids:
+        q.close()
+    return out
 
 
 def equal_error(g, p, rt, torch, target=1e-5, n_iter=24):

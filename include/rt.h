@@ -176,6 +176,34 @@ int rt_get_flux(const rt_grid *g, double *out3, int where);
  * values of max rel dS, *n receives the count stored. */
 int rt_get_history(const rt_grid *g, double *hist, int max, int *n);
 
+/* Gradients of a loss L(S, J, F) evaluated at the converged source function,
+ * with respect to the per-voxel chi, eps and B that rt_set_opacity set.  The
+ * fixed point S = (1 - eps) J(S; chi, B) + eps B of the ALI iteration (Sect.
+ * 3.2.1, with J from the formal solution of Sect. 2) is differentiated
+ * implicitly: the adjoint source function lam solves
+ *   lam = gS + Lambda^T gJ + Lambda_F^T gF + Lambda^T ((1 - eps) lam)
+ * by the same diagonal-Lambda* preconditioned iteration as the forward ALI
+ * (run to max|d lam| <= tol max|lam|, at most max_iter sweeps), where
+ * Lambda^T is the ray march run backwards along every characteristic; then
+ *   dL/dchi = (dJ/dchi)^T (gJ + (1-eps) lam) + (dF/dchi)^T gF,
+ *   dL/dB   = eps lam + (dJ/dB)^T (gJ + (1-eps) lam) + (dF/dB)^T gF,
+ *   dL/deps = lam (B - J).
+ * The paper computes no gradients; this operation is an extension of it.
+ * Inputs: dL_dS, dL_dJ (n_vox doubles) and dL_dF (n_vox x 3, the local basis
+ * of rt_get_flux); any may be NULL (zero).  Outputs dchi, deps, dB: n_vox
+ * doubles each, caller-owned, all in the memory space `where`.  The
+ * derivatives hold at the grid's current S (call rt_solve first), in FP64
+ * whatever the grid's precision; the parabola-or-linear choice of every
+ * segment is held fixed.  Side effect: J, Lambda* and the flux of the grid
+ * are recomputed in FP64 from the current S.  *iters (may be NULL) receives
+ * the adjoint sweeps taken.  Returns RT_ENOTCONVERGED (outputs written from
+ * the last iterate) when max_iter is reached, RT_EINVAL for a NULL grid or
+ * output, bad `where`, tol <= 0, max_iter < 1 or use_lstar = 0, RT_ENOMEM when
+ * its work arrays (about 6 n_vox + 3 segments-per-block doubles) cannot be
+ * allocated. */
+int rt_adjoint(rt_grid *g, const double *dL_dS, const double *dL_dJ, const double *dL_dF, double tol, int max_iter,
+               double *dchi, double *deps, double *dB, int where, int *iters);
+
 /* Crossing lists of solid angle omega (host buffers).  Call with NULL arrays
  * to get *n_rays and *n_seg, then with buffers of those sizes:
  * ray_off[n_rays+1] (segment offsets), ray_origin[n_rays] (voxel whose centre

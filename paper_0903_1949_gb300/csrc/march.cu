@@ -18,115 +18,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "coef.cuh"
 #include "rt_internal.h"
 
 namespace rtk {
 namespace {
-
-// 1/n! for n = 0..20
-__device__ __forceinline__ double inv_fact(int n)
-{
-    const double f[21] = {1.0,
-                          1.0,
-                          1.0 / 2.0,
-                          1.0 / 6.0,
-                          1.0 / 24.0,
-                          1.0 / 120.0,
-                          1.0 / 720.0,
-                          1.0 / 5040.0,
-                          1.0 / 40320.0,
-                          1.0 / 362880.0,
-                          1.0 / 3628800.0,
-                          1.0 / 39916800.0,
-                          1.0 / 479001600.0,
-                          1.0 / 6227020800.0,
-                          1.0 / 87178291200.0,
-                          1.0 / 1307674368000.0,
-                          1.0 / 20922789888000.0,
-                          1.0 / 355687428096000.0,
-                          1.0 / 6402373705728000.0,
-                          1.0 / 121645100408832000.0,
-                          1.0 / 2432902008176640000.0};
-    return f[n];
-}
-
-// Weights of one segment of optical depth x followed by p.
-//   e0 = 1 - e^{-x},  f1 = (x - e0)/x,  f2 = (x(2 - e0) - 2 e0)/x
-//   parabolic: alpha = e0 - f1 - f2/(x+p), beta = f1 + f2/p, gamma = -x f2/(p (x+p))
-//   linear:    alpha = e0 - f1,           beta = f1,         gamma = 0
-// f1 and f2 are odd/even power series in x that cancel catastrophically when
-// evaluated from e0 at small x; below the threshold they are summed directly
-// (Horner), above it they come from expm1.
-struct Coef64 {
-    static constexpr int NS = 19;  // series terms for x < 0.5
-    __device__ __forceinline__ static void eval(double x, double p, bool para, double &E, double &al, double &be,
-                                                double &ga)
-    {
-        double e0, f1, f2;
-        if (x < 0.5) {
-            double h1 = 0.0, h2 = 0.0;
-#pragma unroll
-            for (int n = NS + 1; n >= 2; --n) h1 = inv_fact(n) - x * h1;        // sum (-x)^(n-2)/n!
-#pragma unroll
-            for (int m = NS + 1; m >= 3; --m) h2 = (double)(m - 2) * inv_fact(m) - x * h2;
-            f1 = x * h1;
-            f2 = (x * x) * h2;
-            e0 = x - x * f1;
-            E = 1.0 - e0;
-        } else {
-            double em = expm1(-x);
-            e0 = -em;
-            E = 1.0 + em;
-            f1 = (x - e0) / x;
-            f2 = (x * (2.0 - e0) - 2.0 * e0) / x;
-        }
-        if (para) {
-            double iD = 1.0 / (x + p), ip = 1.0 / p;
-            al = (e0 - f1) - f2 * iD;
-            be = f1 + f2 * ip;
-            ga = -(x * f2) * (ip * iD);
-        } else {
-            al = e0 - f1;
-            be = f1;
-            ga = 0.0;
-        }
-    }
-};
-
-struct Coef32 {
-    static constexpr int NS = 11;  // series terms for x < 1
-    __device__ __forceinline__ static void eval(float x, float p, bool para, float &E, float &al, float &be, float &ga)
-    {
-        float e0, f1, f2;
-        if (x < 1.0f) {
-            float h1 = 0.0f, h2 = 0.0f;
-#pragma unroll
-            for (int n = NS + 1; n >= 2; --n) h1 = (float)inv_fact(n) - x * h1;
-#pragma unroll
-            for (int m = NS + 2; m >= 3; --m) h2 = (float)((double)(m - 2) * inv_fact(m)) - x * h2;
-            f1 = x * h1;
-            f2 = (x * x) * h2;
-            e0 = x - x * f1;
-            E = 1.0f - e0;
-        } else {
-            E = __expf(-x);
-            e0 = 1.0f - E;
-            float ix = __frcp_rn(x);
-            f1 = (x - e0) * ix;
-            f2 = (x * (2.0f - e0) - 2.0f * e0) * ix;
-        }
-        if (para) {
-            float iD = __frcp_rn(x + p), ip = __frcp_rn(p);
-            al = (e0 - f1) - f2 * iD;
-            be = f1 + f2 * ip;
-            ga = -(x * f2) * (ip * iD);
-        } else {
-            al = e0 - f1;
-            be = f1;
-            ga = 0.0f;
-        }
-    }
-};
 
 template <typename T> struct Traits;
 template <> struct Traits<double> { using C = Coef64; };
@@ -150,7 +46,8 @@ __device__ __forceinline__ int64_t lower_bound64(const int64_t *a, int64_t lo, i
 // processed.
 // Bundle wg of one angle block.  BITS: the parabola choice of segment s comes
 // from bit s of pbits (per-member choices of a batch) instead of RTK_PARA.
-template <typename T, typename P, int K, bool LAM, bool BITS>
+// RAWI: store I_k itself (not l I_k) when LAM is false.
+template <typename T, typename P, int K, bool LAM, bool BITS, bool RAWI = false>
 __device__ __forceinline__ void march_bundle(const uint32_t *__restrict__ vox, const T *__restrict__ len,
                                              const int64_t *__restrict__ ray_off, int64_t r_lo, int64_t r_hi,
                                              int64_t seg_lo, int64_t nseg, int64_t wg, const P *__restrict__ cs,
@@ -306,7 +203,7 @@ __device__ __forceinline__ void march_bundle(const uint32_t *__restrict__ vox, c
                     o.y = l[j] * lam[j];
                     __stcg((P *)outv + s0 + j, o);
                 } else {
-                    __stcg((T *)outv + s0 + j, l[j] * I);
+                    __stcg((T *)outv + s0 + j, RAWI ? I : l[j] * I);
                 }
             }
         }
@@ -331,6 +228,18 @@ __global__ void __launch_bounds__(256) k_march4(const uint32_t *__restrict__ vox
     const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     march_bundle<T, P, K, LAM, false>(vox, len, ray_off, r_lo, r_hi, seg_lo, nseg, wg, cs, Bv, I_outer, homog, outv,
                                       chunk, nullptr);
+}
+
+// FP64 march writing I_k per segment (forward intensities for the adjoint).
+__global__ void __launch_bounds__(256) k_march_I(const uint32_t *__restrict__ vox, const double *__restrict__ len,
+                                                 const int64_t *__restrict__ ray_off, int64_t r_lo, int64_t r_hi,
+                                                 int64_t seg_lo, int64_t nseg, const double2 *__restrict__ cs,
+                                                 const double *__restrict__ Bv, double I_outer, int homog,
+                                                 double *__restrict__ out, int chunk)
+{
+    const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    march_bundle<double, double2, 1, false, false, true>(vox, len, ray_off, r_lo, r_hi, seg_lo, nseg, wg, cs, Bv,
+                                                         I_outer, homog, out, chunk, nullptr);
 }
 
 // Full march (l I and l lambda) with the parabola choices of a bitmask.
@@ -459,6 +368,18 @@ cudaError_t march_block_J(const uint32_t *vox, const T *len, const int64_t *ray_
     else
         k_march4<T, P, 1, false><<<(unsigned)blocks, 256, 0, st>>>(vox, len, ray_off, r_lo, r_hi, seg_lo, nseg, chiS, B,
                                                                    I_outer, homog, out, chunk);
+    return cudaGetLastError();
+}
+
+cudaError_t march_block_I(const uint32_t *vox, const double *len, const int64_t *ray_off, int64_t r_lo, int64_t r_hi,
+                          int64_t seg_lo, int64_t nseg, const double2 *chiS, const double *B, double I_outer, int homog,
+                          double *out, int chunk, cudaStream_t st)
+{
+    if (nseg <= 0) return cudaSuccess;
+    int64_t warps = (nseg + chunk - 1) / chunk;
+    int64_t blocks = (warps + 7) / 8;
+    k_march_I<<<(unsigned)blocks, 256, 0, st>>>(vox, len, ray_off, r_lo, r_hi, seg_lo, nseg, chiS, B, I_outer, homog,
+                                                out, chunk);
     return cudaGetLastError();
 }
 

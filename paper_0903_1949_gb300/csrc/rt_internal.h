@@ -146,6 +146,10 @@ template <typename T, typename P>
 cudaError_t march_block_J(const uint32_t *vox, const T *len, const int64_t *ray_off, int64_t r_lo, int64_t r_hi,
                           int64_t seg_lo, int64_t nseg, const P *chiS, const T *B, T I_outer, int homog, T *out,
                           int chunk, cudaStream_t st);
+// FP64 march writing I_k (not l I_k) per segment: forward intensities for the adjoint.
+cudaError_t march_block_I(const uint32_t *vox, const double *len, const int64_t *ray_off, int64_t r_lo, int64_t r_hi,
+                          int64_t seg_lo, int64_t nseg, const double2 *chiS, const double *B, double I_outer, int homog,
+                          double *out, int chunk, cudaStream_t st);
 // One batched march work item: an angle block of one member (FP32, J only).
 struct MarchItem {
     const uint32_t *vox;

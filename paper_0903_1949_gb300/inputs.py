@@ -129,6 +129,36 @@ PROBLEMS = {
 }
 
 
+def make_batch_problem(n_members=256, n_angle=16, shapes=((33, 17, 33), (65, 33, 65), (97, 49, 97)), seed=SEED + 2,
+                       tau=1.0):
+    """Many wavelengths on spherical grids of uneven size (round-robin by member index).
+
+    Each member m has chi = s_m chi0 r^-2 (radial tau of the base law `tau`), eps_m and
+    B = 1, with s_m log-uniform in [1e-2, 1e2] and eps_m log-uniform in [1e-6, 1e-2].
+    Returns (grids: list of dict(coord, edges, dirs, weights, inner_bc, n), member_grid,
+    members: list of (chi, eps, B)).
+    """
+    rng = np.random.default_rng(seed)
+    grids = []
+    dirs, wts = angle_set(n_angle, n_angle)
+    for n in shapes:
+        edges = sph_edges(*n)
+        grids.append(dict(coord=SPHERICAL, edges=edges, dirs=dirs, weights=wts, inner_bc=CORE_B, n=tuple(n)))
+    scale = 10.0 ** rng.uniform(-2.0, 2.0, n_members)
+    eps = 10.0 ** rng.uniform(-6.0, -2.0, n_members)
+    member_grid = [m % len(shapes) for m in range(n_members)]
+    base = []
+    for g in grids:
+        c1, _, _ = voxel_centres(SPHERICAL, g["edges"])
+        rmin, rmax = g["edges"][0][0], g["edges"][0][-1]
+        base.append(np.ascontiguousarray((tau / (1.0 / rmin - 1.0 / rmax) / (c1 * c1)).reshape(-1)))
+    members = []
+    for m in range(n_members):
+        chi = base[member_grid[m]] * scale[m]
+        members.append((chi, np.full(chi.size, eps[m]), np.ones(chi.size)))
+    return grids, member_grid, members
+
+
 def voxel_angle_count(n, n_ang):
     return int(np.prod(n)) * int(n_ang)
 

@@ -100,6 +100,7 @@ def load():
         "rt_batch_autotune": [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                               ctypes.POINTER(ctypes.c_double)],
         "rt_get_timing": [_P, ctypes.POINTER(rt_timing)],
+        "rt_adjoint": [_P, _P, _P, _P, ctypes.c_double, _I, _P, _P, _P, _I, ctypes.POINTER(_I)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -231,6 +232,36 @@ def rt_get_history(h):
     buf = np.empty(max(1, n.value))
     _check(load().rt_get_history(h, ctypes.c_void_p(buf.ctypes.data), n.value, ctypes.byref(n)))
     return buf[:n.value]
+
+
+def rt_adjoint(h, n_vox, dL_dS=None, dL_dJ=None, dL_dF=None, tol=1e-10, max_iter=10000, device=False):
+    """(dchi, deps, dB, iters, converged) of a loss with gradients dL_dS, dL_dJ (n_vox) and
+    dL_dF (n_vox x 3, local basis) at the grid's current S.  device=True: CUDA float64
+    tensors in and out (then every given gradient must be a CUDA tensor)."""
+    keep = []
+
+    def arg(x):
+        if x is None:
+            return None, None
+        p, w, k = _ptr(x)
+        keep.append(k)
+        return p, w
+    ins = [arg(x) for x in (dL_dS, dL_dJ, dL_dF)]
+    where = RT_DEVICE if device else RT_HOST
+    if any(w is not None and w != where for _, w in ins):
+        raise TypeError("gradients and outputs must live in the same memory space")
+    if device:
+        import torch
+        outs = [torch.empty(n_vox, dtype=torch.float64, device="cuda") for _ in range(3)]
+    else:
+        outs = [np.empty(n_vox) for _ in range(3)]
+    po = [_ptr(o)[0] for o in outs]
+    it = ctypes.c_int()
+    rc = load().rt_adjoint(h, ins[0][0], ins[1][0], ins[2][0], float(tol), int(max_iter), po[0], po[1], po[2], where,
+                           ctypes.byref(it))
+    if rc not in (RT_OK, RT_ENOTCONVERGED):
+        _check(rc)
+    return outs[0], outs[1], outs[2], it.value, rc == RT_OK
 
 
 def rt_get_crossings(h, omega):
@@ -451,3 +482,6 @@ class Grid:
 
     def timing(self):
         return rt_get_timing(self.h)
+
+    def adjoint(self, dL_dS=None, dL_dJ=None, dL_dF=None, tol=1e-10, max_iter=10000, device=False):
+        return rt_adjoint(self.h, self.nvox, dL_dS, dL_dJ, dL_dF, tol, max_iter, device)

@@ -79,6 +79,8 @@ def test_null_handles_rejected(lib):
     assert lib.rt_grid_destroy(None) == rt.RT_OK
     out = np.zeros(4)
     assert lib.rt_get_J(None, ctypes.c_void_p(out.ctypes.data), rt.RT_HOST) == rt.RT_EINVAL
+    p = ctypes.c_void_p(out.ctypes.data)
+    assert lib.rt_adjoint(None, None, None, None, 1e-8, 10, p, p, p, rt.RT_HOST, None) == rt.RT_EINVAL
 
 
 def test_struct_layout_matches_header(lib):
