@@ -22,6 +22,7 @@ an equal-J-error comparison of the mixed and FP64 solvers.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -45,7 +46,7 @@ MARCH_BYTES_PER_SEG = 8  # int32 voxel word + fp32 path length streamed per cros
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="sph65")
@@ -63,24 +64,34 @@ def dist_env():
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.marks = []
         self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
 
     def start(self):
+        """Start sampling every 50 ms and wait (up to 5 s) for the first sample."""
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
+
+    def mark(self):
+        """Wall-clock bounds of the timed region (call before and after it)."""
+        self.marks.append(time.time())
 
     def stop(self):
         if self.proc is None:
@@ -91,22 +102,32 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[5:9]):
+        lo, hi = (self.marks[0], self.marks[-1]) if len(self.marks) >= 2 else (-1e300, 1e300)
+        inside = [r for r in rows if lo <= r[0] <= hi]
+        if not inside and rows:  # region shorter than the sampling period: nearest sample after it starts
+            after = [r for r in rows if r[0] >= lo]
+            inside = after[:1] if after else rows[-1:]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in inside:
+            for nm, val in zip(names, r[3]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
+        sm = [r[1] for r in inside]
+        smax = [r[2] for r in inside]
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "region_s": (hi - lo) if len(self.marks) >= 2 else None}
 
 
 def hbm_peak():
@@ -256,7 +277,9 @@ def main():
     clocks = Clocks(local)
     g.set_timing(True)
     clocks.start()
+    clocks.mark()
     ms = timed(g.ali_step, args.steps)
+    clocks.mark()
     ck = clocks.stop()
     tm = g.timing()
     g.set_timing(False)

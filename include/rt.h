@@ -135,6 +135,19 @@ int rt_set_precision(rt_grid *g, int precision);
  * warp bundle in the ray march, 64..16384 (default 512); a bundle always holds
  * whole characteristics, so results do not depend on it beyond rounding. */
 #define RT_TUNE_MARCH_CHUNK 1
+/* RT_TUNE_STREAMED_WEIGHTS (default 1): the FP32 J-only march of the ALI
+ * iteration streams per-segment weights (E, alpha, beta, gamma) evaluated once
+ * per chi in FP64 and the gather weight w l / L (20 extra bytes per segment of
+ * device memory, allocated at the first use); 0, or when that memory is not
+ * available: the march evaluates the weights itself from chi and l.
+ * RT_TUNE_MARCH_COARSEN: segments per lane of the streamed-weight march, 1, 2
+ * (default) or 4.  RT_TUNE_OVERLAP (default 1): the J gather of angle block b
+ * runs on a second stream of the library while block b + 1 is marched (the
+ * grid's stream waits for it before the call returns its work); 0: both on
+ * the grid's stream.  None of these changes results beyond FP32 rounding. */
+#define RT_TUNE_STREAMED_WEIGHTS 2
+#define RT_TUNE_MARCH_COARSEN 3
+#define RT_TUNE_OVERLAP 4
 int rt_tune(rt_grid *g, int knob, int value);
 
 /* Formal solution from the current S with the grid's precision: J, the
@@ -286,6 +299,8 @@ typedef struct rt_timing {
     int64_t gather_launches;
     int64_t march_segments;   /* crossing segments processed by the timed march launches */
     int64_t kernel_launches;  /* every kernel this library launched on the grid since the reset */
+    int64_t march_bytes;      /* DRAM bytes the timed march launches stream by design (per segment:
+                                 8 FP32, 12 FP64, 24 streamed-weight FP32) */
 } rt_timing;
 
 int rt_set_timing(rt_grid *g, int enable);

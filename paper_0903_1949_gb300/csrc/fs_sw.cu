@@ -1,0 +1,341 @@
+// fs_sw.cu -- FP32 J-only formal solution of the ALI iteration with streamed
+// segment weights (the hot loop of the mixed-precision path).
+//
+// The weights of a segment in the recurrence I_k = I_{k-1} E_k + alpha_k
+// S_{k-1} + beta_k S_k + gamma_k S_{k+1} (scheme R6 of Papers I-II, Sect. 2)
+// depend on chi and the path length only, so for the duration of an ALI solve
+// they are loop invariants: k_coef_stream evaluates them once per chi in FP64
+// and stores (E, alpha, beta, gamma) as FP32, alpha folded into beta at the
+// start of a run (S_0 := S_1) and gamma = 0 where the linear weights apply.
+// k_seg_weight stores c = w_Omega l / L_{Omega v} per segment (geometry only),
+// so the march writes c_s I_s and J_v (Sect. 3.2.1) is a plain sum of those
+// values over v's ownership list, in list order.
+//
+// The march of angle block b (warps over bundles of whole characteristics,
+// bounds from a precomputed table) runs while J of block b - 1 is gathered
+// on a second stream from the other half of a double buffer, so the
+// latency-bound gather overlaps the march.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "coef.cuh"
+#include "rt_internal.h"
+
+namespace rtk {
+namespace {
+
+constexpr int CHUNK = RTK_JCHUNK;  // long-list chunk of the J tables (one warp each)
+
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+    // butterfly over the warp with an error-free combination of the partial sums
+    __device__ __forceinline__ void warp_reduce()
+    {
+        for (int o = 16; o > 0; o >>= 1) {
+            const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+            const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+            const float t = s + s2;
+            const float bb = t - s;
+            const float err = (s - (t - bb)) + (s2 - bb);
+            c = (c + c2) - err;
+            s = t;
+        }
+    }
+};
+
+__device__ __forceinline__ int64_t lb64(const int64_t *a, int64_t lo, int64_t hi, int64_t key)
+{
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (a[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Bundle bw of a block: the whole characteristics whose first segment lies in
+// [bw * chunk, (bw + 1) * chunk), as segment indices relative to the block.
+__global__ void k_bundles(const int64_t *ray_off, int64_t r_lo, int64_t r_hi, int64_t seg_lo, int64_t nseg, int chunk,
+                          int64_t nb, int2 *bnd)
+{
+    for (int64_t bw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; bw < nb; bw += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c_lo = bw * chunk;
+        const int64_t c_hi = (c_lo + chunk < nseg) ? c_lo + chunk : nseg;
+        const int64_t ra = lb64(ray_off, r_lo, r_hi, seg_lo + c_lo);
+        const int64_t rb = lb64(ray_off, r_lo, r_hi, seg_lo + c_hi);
+        bnd[bw] = make_int2((int)(ray_off[ra] - seg_lo), (int)(ray_off[rb] - seg_lo));
+    }
+}
+
+// One warp marches bundle wg: K consecutive segments per lane, the lane maps
+// I -> A I + b composed by an inclusive shuffle scan over the warp; the next
+// tile's words and weights are fetched before the current one is processed.
+template <int K>
+__device__ __forceinline__ void march_sw(const SwMarch &m, int64_t wg)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    if (wg >= m.nbundles) return;
+    const int2 be = m.bnd[wg];
+    const int s_begin = be.x, s_end = be.y;
+    if (s_begin >= s_end) return;
+    const uint32_t *vx = m.vox + m.seg_lo;
+    const float4 *cf = m.cw + m.seg_lo;
+    const float *gw = m.cg + m.seg_lo;
+    float *o = m.out;
+    float Icarry = 0.f, Sprev = 0.f;
+    uint32_t w[K];
+    float4 c[K];
+    float g[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int s = s_begin + K * lane + j;
+        const bool ok = s < s_end;
+        w[j] = ok ? __ldcs(vx + s) : 0u;
+        c[j] = ok ? __ldcs(cf + s) : make_float4(1.f, 0.f, 0.f, 0.f);
+        g[j] = ok ? __ldcs(gw + s) : 0.f;
+    }
+    for (int base = s_begin; base < s_end; base += 32 * K) {
+        const int s0 = base + K * lane;
+        uint32_t wN[K];
+        float4 cN[K];
+        float gN[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int s = base + 32 * K + K * lane + j;
+            const bool ok = s < s_end;
+            wN[j] = ok ? __ldcs(vx + s) : 0u;
+            cN[j] = ok ? __ldcs(cf + s) : make_float4(1.f, 0.f, 0.f, 0.f);
+            gN[j] = ok ? __ldcs(gw + s) : 0.f;
+        }
+        float S[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) S[j] = (s0 + j < s_end) ? m.cs[w[j] & RTK_VOXMASK].y : 0.f;
+        float Snx = __shfl_down_sync(FULL, S[0], 1);  // S after this lane's last segment
+        const uint32_t wn31 = __shfl_sync(FULL, wN[0], 0);
+        if (lane == 31) Snx = (base + 32 * K < s_end) ? m.cs[wn31 & RTK_VOXMASK].y : 0.f;
+        float Sp = __shfl_up_sync(FULL, S[K - 1], 1);  // S before this lane's first segment
+        if (lane == 0) Sp = Sprev;
+        float A[K], b[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const float Sm = (j == 0) ? Sp : S[j - 1];
+            const float Sn = (j + 1 < K) ? S[j + 1] : Snx;
+            const float src = fmaf(c[j].y, Sm, fmaf(c[j].z, S[j], c[j].w * Sn));
+            A[j] = c[j].x;
+            b[j] = src;
+            if (w[j] & RTK_RAYSTART) {
+                const float Iin = m.homog ? 0.f : ((w[j] & RTK_CORE) ? m.B32[w[j] & RTK_VOXMASK] : m.I_outer);
+                b[j] = fmaf(c[j].x, Iin, src);
+                A[j] = 0.f;
+            }
+            if (s0 + j >= s_end) {
+                A[j] = 1.f;
+                b[j] = 0.f;
+            }
+        }
+        float LA = A[0], LB = b[0];
+#pragma unroll
+        for (int j = 1; j < K; ++j) {
+            LB = fmaf(A[j], LB, b[j]);
+            LA = A[j] * LA;
+        }
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const float Ao = __shfl_up_sync(FULL, LA, off);
+            const float bo = __shfl_up_sync(FULL, LB, off);
+            if (lane >= off) {
+                LB = fmaf(LA, bo, LB);
+                LA = LA * Ao;
+            }
+        }
+        float PA = __shfl_up_sync(FULL, LA, 1);
+        float PB = __shfl_up_sync(FULL, LB, 1);
+        if (lane == 0) {
+            PA = 1.f;
+            PB = 0.f;
+        }
+        float I = fmaf(PA, Icarry, PB);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            I = fmaf(A[j], I, b[j]);
+            if (s0 + j < s_end) __stcg(o + s0 + j, g[j] * I);
+        }
+        Icarry = __shfl_sync(FULL, I, 31);
+        Sprev = __shfl_sync(FULL, S[K - 1], 31);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            w[j] = wN[j];
+            c[j] = cN[j];
+            g[j] = gN[j];
+        }
+    }
+}
+
+// J gather of one block from the values c_s I_s: CTAs [0, nbs) take 256 short
+// lists each (thread per voxel over the sliced-ELL entries, 8 loads in
+// flight); the other warps take one RTK_JCHUNK-entry chunk of a long list each
+// (32 entries per lane, 8 in flight), and the warp that completes a voxel's
+// last chunk adds the chunk sums in chunk order.
+__global__ void __launch_bounds__(256) k_gather_sw(SwGather t)
+{
+    const int64_t cta = blockIdx.x;
+    if (cta < t.nbs) {
+        const int64_t i = cta * 256 + threadIdx.x;
+        if (i >= t.nshort) return;
+        const int v = t.jorder[i];
+        const int L = t.off[v + 1] - t.off[v];
+        const int32_t *lst = t.jsell + t.jgbase[i >> 5] + (i & 31);
+        Kahan acc;
+        for (int k = 0; k < L; k += 8) {
+            int ss[8];
+            float val[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) ss[j] = (k + j < L) ? __ldcs(lst + 32 * (k + j)) : -1;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) val[j] = (ss[j] >= 0) ? __ldcg(t.buf + ss[j]) : 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (ss[j] >= 0) acc.add(val[j]);
+        }
+        const double r = acc.value();
+        t.J[v] = t.first ? r : t.J[v] + r;
+        return;
+    }
+    const int64_t c = ((cta - t.nbs) * 256 + threadIdx.x) >> 5;
+    if (c >= t.nchunks) return;
+    const int lane = threadIdx.x & 31;
+    const int v = t.crow[c];
+    const int e0 = t.cbeg[c];
+    const int e1 = min(e0 + CHUNK, t.off[v + 1]);
+    Kahan acc;
+    for (int k = e0 + lane; k < e1; k += 32 * 8) {
+        int ss[8];
+        float val[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ss[j] = (k + 32 * j < e1) ? __ldcs(t.perm + k + 32 * j) : -1;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) val[j] = (ss[j] >= 0) ? __ldcg(t.buf + ss[j]) : 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (ss[j] >= 0) acc.add(val[j]);
+    }
+    acc.warp_reduce();
+    if (lane == 0) {
+        const int lr = t.clr[c];
+        __stcg(t.part + c, acc.value());
+        __threadfence();
+        const int c0 = t.lfirst[lr], c1 = (lr + 1 < t.nlong) ? t.lfirst[lr + 1] : (int)t.nchunks;
+        if (atomicAdd(t.cnt + lr, 1) == c1 - c0 - 1) {
+            __threadfence();
+            double sum = 0.0;
+            for (int cc = c0; cc < c1; ++cc) sum += __ldcg(t.part + cc);
+            t.J[v] = t.first ? sum : t.J[v] + sum;
+            t.cnt[lr] = 0;
+        }
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_march_sw(SwMarch m)
+{
+    march_sw<K>(m, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+}
+
+// FP64 weights of every segment for the current chi, rounded to FP32.
+__global__ void k_coef_stream(const uint32_t *__restrict__ vox, const double *__restrict__ len64,
+                              const double *__restrict__ chi, int64_t nseg, float4 *__restrict__ cw)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nseg; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = vox[s];
+        const bool para = (w & RTK_PARA) != 0u;  // set only when segment s + 1 continues the run
+        const double x = chi[w & RTK_VOXMASK] * len64[s];
+        const double p = para ? chi[vox[s + 1] & RTK_VOXMASK] * len64[s + 1] : 0.0;
+        double E, al, be, ga;
+        Coef64::eval(x, p, para, E, al, be, ga);
+        if (w & (RTK_RAYSTART | RTK_RESTART)) {  // S_0 := S_1 at the start of a run
+            be += al;
+            al = 0.0;
+        }
+        cw[s] = make_float4((float)E, (float)al, (float)be, (float)ga);
+    }
+}
+
+// Gather weight times path length of every segment: w_Omega l_s / L_{Omega v_s}.
+__global__ void k_seg_weight(const uint32_t *__restrict__ vox, const double *__restrict__ len64,
+                             const int64_t *__restrict__ ang_seg_off, int n_ang, const double *__restrict__ wt,
+                             const double *__restrict__ invL, int nvox, int64_t nseg, float *__restrict__ cg)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nseg; s += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_ang;  // angle q: ang_seg_off[q] <= s < ang_seg_off[q + 1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (ang_seg_off[mid] <= s) lo = mid;
+            else hi = mid;
+        }
+        const int v = vox[s] & RTK_VOXMASK;
+        cg[s] = (float)(wt[lo] * len64[s] * invL[(int64_t)lo * nvox + v]);
+    }
+}
+
+unsigned grid_cap(int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    if (b > 152 * 32) b = 152 * 32;
+    return (unsigned)(b > 0 ? b : 1);
+}
+
+}  // namespace
+
+cudaError_t sw_bundles(const int64_t *ray_off, int64_t r_lo, int64_t r_hi, int64_t seg_lo, int64_t nseg, int chunk,
+                       int2 *bnd, cudaStream_t st)
+{
+    const int64_t nb = (nseg + chunk - 1) / chunk;
+    if (nb <= 0) return cudaSuccess;
+    k_bundles<<<grid_cap(nb), 256, 0, st>>>(ray_off, r_lo, r_hi, seg_lo, nseg, chunk, nb, bnd);
+    return cudaGetLastError();
+}
+
+cudaError_t march_sw_launch(const SwMarch &m, int coarsen, cudaStream_t st)
+{
+    const int64_t grid = (m.nbundles + 7) / 8;
+    if (grid <= 0) return cudaSuccess;
+    if (coarsen == 4) k_march_sw<4><<<(unsigned)grid, 256, 0, st>>>(m);
+    else if (coarsen == 1) k_march_sw<1><<<(unsigned)grid, 256, 0, st>>>(m);
+    else k_march_sw<2><<<(unsigned)grid, 256, 0, st>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_sw_launch(const SwGather &t, cudaStream_t st)
+{
+    const int64_t grid = t.nbs + (t.nchunks * 32 + 255) / 256;
+    if (grid <= 0) return cudaSuccess;
+    k_gather_sw<<<(unsigned)grid, 256, 0, st>>>(t);
+    return cudaGetLastError();
+}
+
+cudaError_t coef_stream(const uint32_t *vox, const double *len64, const double *chi, int64_t nseg, float4 *cw,
+                        cudaStream_t st)
+{
+    if (nseg <= 0) return cudaSuccess;
+    k_coef_stream<<<grid_cap(nseg), 256, 0, st>>>(vox, len64, chi, nseg, cw);
+    return cudaGetLastError();
+}
+
+cudaError_t seg_weight(const uint32_t *vox, const double *len64, const int64_t *ang_seg_off, int n_ang,
+                       const double *wt, const double *invL, int nvox, int64_t nseg, float *cg, cudaStream_t st)
+{
+    if (nseg <= 0) return cudaSuccess;
+    k_seg_weight<<<grid_cap(nseg), 256, 0, st>>>(vox, len64, ang_seg_off, n_ang, wt, invL, nvox, nseg, cg);
+    return cudaGetLastError();
+}
+
+}  // namespace rtk

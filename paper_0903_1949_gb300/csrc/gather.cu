@@ -9,6 +9,8 @@
 // quadrature weights (Sect. 3.2: J, flux vectors of voxels).  No float atomics
 // are used, so every result is bit-reproducible from run to run.
 #include <cuda_runtime.h>
+
+#include <utility>
 #include <stdint.h>
 
 #include "rt_internal.h"
@@ -32,30 +34,76 @@ __global__ void k_off32(const int64_t *off64, int32_t *off32, int n1)
     if (i < n1) off32[i] = (int32_t)off64[i];
 }
 
-__global__ void k_fill(const uint32_t *vox, int64_t n, int32_t *cursor, int32_t *perm)
+// Ownership lists by a stable LSD radix sort of the block's segment indices
+// keyed by voxel (8-bit digits): the input is in segment order, so every
+// voxel's list comes out sorted by segment index, which fixes the summation
+// order of the gather.  Tiles of RS_TILE segments per CTA.
+constexpr int RS_TILE = 4096;
+constexpr int RS_BUCKETS = 256;
+
+__global__ void k_rs_init(const uint32_t *vox, int64_t n, uint32_t *keys, int32_t *vals)
 {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
-        int v = vox[s] & RTK_VOXMASK;
-        int pos = atomicAdd(cursor + v, 1);
-        perm[pos] = (int32_t)s;
+        keys[s] = vox[s] & RTK_VOXMASK;
+        vals[s] = (int32_t)s;
     }
 }
 
-// The fill order above is arbitrary: sort every voxel's list so the
-// summation order is the segment order.
-__global__ void k_sort_lists(int nvox, const int32_t *off, int32_t *perm)
+// Digit counts of one tile, stored digit-major (hist[d * ntiles + t]) so that
+// one exclusive scan gives every (digit, tile) its first output position.
+__global__ void __launch_bounds__(256) k_rs_hist(const uint32_t *keys, int64_t n, int shift, int64_t ntiles,
+                                                 int32_t *hist)
 {
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nvox) return;
-    int lo = off[v], hi = off[v + 1];
-    for (int a = lo + 1; a < hi; ++a) {
-        int32_t x = perm[a];
-        int b = a - 1;
-        while (b >= lo && perm[b] > x) {
-            perm[b + 1] = perm[b];
-            --b;
+    __shared__ int32_t h[RS_BUCKETS];
+    for (int i = threadIdx.x; i < RS_BUCKETS; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int i = threadIdx.x; i < RS_TILE; i += blockDim.x) {
+        const int64_t e = base + i;
+        if (e < n) atomicAdd(&h[(keys[e] >> shift) & (RS_BUCKETS - 1)], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < RS_BUCKETS; i += blockDim.x) hist[(int64_t)i * ntiles + blockIdx.x] = h[i];
+}
+
+// Stable scatter of one tile: the tile is read in rounds of 256 elements in
+// order; an element's rank among equal digits is the count in earlier rounds
+// (run), in earlier warps of its round (wcnt) and in earlier lanes of its warp.
+__global__ void __launch_bounds__(256) k_rs_scatter(const uint32_t *__restrict__ keys, const int32_t *__restrict__ vals,
+                                                    int64_t n, int shift, int64_t ntiles, const int64_t *__restrict__ off,
+                                                    uint32_t *__restrict__ keys_out, int32_t *__restrict__ vals_out)
+{
+    __shared__ int32_t run[RS_BUCKETS];
+    __shared__ int32_t wcnt[8][RS_BUCKETS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < RS_BUCKETS; i += blockDim.x) run[i] = 0;
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int r = 0; r < RS_TILE / 256; ++r) {
+        for (int i = threadIdx.x; i < 8 * RS_BUCKETS; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        const int64_t e = base + r * 256 + threadIdx.x;
+        const bool ok = e < n;
+        const uint32_t k = ok ? keys[e] : 0u;
+        const int32_t val = ok ? vals[e] : 0;
+        const int d = ok ? (int)((k >> shift) & (RS_BUCKETS - 1)) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (ok && lane == __ffs(peers) - 1) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (ok) {
+            int before = 0;
+            for (int w2 = 0; w2 < warp; ++w2) before += wcnt[w2][d];
+            const int64_t pos = off[(int64_t)d * ntiles + blockIdx.x] + run[d] + before + rank;
+            keys_out[pos] = k;
+            vals_out[pos] = val;
         }
-        perm[b + 1] = x;
+        __syncthreads();
+        for (int i = threadIdx.x; i < RS_BUCKETS; i += blockDim.x) {
+            int t = 0;
+            for (int w2 = 0; w2 < 8; ++w2) t += wcnt[w2][i];
+            run[i] += t;
+        }
+        __syncthreads();
     }
 }
 
@@ -413,7 +461,7 @@ __global__ void k_sell_fill(int64_t nunits, const int32_t *order, const int32_t 
 // one warp per chunk reading the list coalesced, and the warp that finishes a
 // voxel's last chunk adds the chunk sums in chunk order.
 constexpr int SHORT_LEN = 64;
-constexpr int CHUNK_LEN = 1024;
+constexpr int CHUNK_LEN = RTK_JCHUNK;
 
 __global__ void k_jclass(int nvox, const int32_t *off, int32_t *hist, int32_t *longflag, int32_t *nch)
 {
@@ -705,21 +753,36 @@ int grid_for(int64_t n, int threads)
 
 }  // namespace
 
+int64_t radix_tiles(int64_t n) { return (n + RS_TILE - 1) / RS_TILE; }
+
 cudaError_t csr_build(int nvox, const uint32_t *vox_blk, int64_t nseg_blk, int32_t *counts, int32_t *csr_off,
-                      int32_t *cursor, int32_t *perm_blk, int64_t *tmp, cudaStream_t st)
+                      int32_t *perm_blk, int64_t *tmp, const RadixScratch &rs, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * nvox, st);
     if (e != cudaSuccess) return e;
+    if (nseg_blk > rs.cap) return cudaErrorInvalidValue;
     k_count_vox<<<grid_for(nseg_blk, 256), 256, 0, st>>>(vox_blk, nseg_blk, counts);
     // offsets in int64 scratch, then narrowed (a block holds < 2^31 segments)
     int64_t *off64 = tmp;
     int64_t *stmp = tmp + (nvox + 1);
     if ((e = scan_i32(counts, off64, nvox, stmp, st)) != cudaSuccess) return e;
     k_off32<<<(nvox + 256) / 256, 256, 0, st>>>(off64, csr_off, nvox + 1);
-    if ((e = cudaMemcpyAsync(cursor, csr_off, sizeof(int32_t) * nvox, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-        return e;
-    k_fill<<<grid_for(nseg_blk, 256), 256, 0, st>>>(vox_blk, nseg_blk, cursor, perm_blk);
-    k_sort_lists<<<(nvox + 127) / 128, 128, 0, st>>>(nvox, csr_off, perm_blk);
+    if (nseg_blk <= 0) return cudaGetLastError();
+    int bits = 0;
+    while (bits < 31 && ((int64_t)1 << bits) < (int64_t)nvox) ++bits;
+    const int passes = (bits + 7) / 8;
+    k_rs_init<<<grid_for(nseg_blk, 256), 256, 0, st>>>(vox_blk, nseg_blk, rs.kA, passes ? rs.vA : perm_blk);
+    const int64_t ntiles = radix_tiles(nseg_blk);
+    uint32_t *kin = rs.kA, *kout = rs.kB;
+    int32_t *vin = rs.vA, *vout = rs.vB;
+    for (int p = 0; p < passes; ++p) {
+        if (p == passes - 1) vout = perm_blk;
+        k_rs_hist<<<(unsigned)ntiles, 256, 0, st>>>(kin, nseg_blk, 8 * p, ntiles, rs.hist);
+        if ((e = scan_i32(rs.hist, rs.off, RS_BUCKETS * ntiles, rs.tmp, st)) != cudaSuccess) return e;
+        k_rs_scatter<<<(unsigned)ntiles, 256, 0, st>>>(kin, vin, nseg_blk, 8 * p, ntiles, rs.off, kout, vout);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
     return cudaGetLastError();
 }
 

@@ -70,6 +70,20 @@ struct rt_grid {
     std::vector<int64_t> ev_segs;
     int64_t launches = 0;
     int march_chunk = 512;  // segments per warp bundle (RT_TUNE_MARCH_CHUNK)
+    std::vector<int64_t> ev_bytes;  // streamed DRAM bytes of each timed march launch
+    // streamed-weight FP32 march (RT_TUNE_STREAMED_WEIGHTS)
+    float4 *d_cw4 = nullptr;  // (E, alpha, beta, gamma) per segment for the current chi
+    float *d_cg = nullptr;    // w_Omega l / L per segment
+    int sw_enabled = 1;
+    int sw_state = 0;         // 0 not allocated yet, 1 allocated, -1 allocation failed
+    bool cw_ok = false;       // d_cw4 matches the current chi
+    int sw_coarsen = 2;       // segments per lane (RT_TUNE_MARCH_COARSEN)
+    int sw_overlap = 1;       // gather of block b on st2 while block b + 1 is marched (RT_TUNE_OVERLAP)
+    cudaStream_t st2 = nullptr;  // second stream of the overlapped gather (created on first use)
+    cudaEvent_t sev[6] = {};     // fork, join, march done x2, gather done x2
+    int2 *d_bnd = nullptr;    // bundle bounds of every block for bnd_chunk
+    std::vector<int64_t> h_bnd_off;
+    int bnd_chunk = 0;
 };
 
 // FP32 formal solution of another opacity field on this grid's geometry (a

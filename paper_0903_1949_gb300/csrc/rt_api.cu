@@ -89,6 +89,10 @@ void release(rt_grid *g)
 {
     for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
     g->ev.clear();
+    for (cudaEvent_t &e : g->sev)
+        if (e) cudaEventDestroy(e), e = nullptr;
+    if (g->st2) cudaStreamDestroy(g->st2);
+    g->st2 = nullptr;
     for (void *p : g->allocs) cudaFree(p);
     g->allocs.clear();
     if (g->h_pin) cudaFreeHost(g->h_pin);
@@ -101,9 +105,11 @@ int sync(rt_grid *g)
     return RT_OK;
 }
 
-// Start event of a timed launch (returns its slot, or -1 when timing is off).
-int tstart(rt_grid *g)
+// Start event of a timed launch on stream st (default: the grid's stream);
+// returns its slot, or -1 when timing is off.
+int tstart(rt_grid *g, cudaStream_t st = nullptr)
 {
+    if (!st) st = g->st;
     if (!g->timing) return -1;
     if (g->ev_used + 2 > g->ev.size()) {
         for (int q = 0; q < 64; ++q) {
@@ -114,16 +120,17 @@ int tstart(rt_grid *g)
     }
     int slot = (int)g->ev_used;
     g->ev_used += 2;
-    cudaEventRecord(g->ev[slot], g->st);
+    cudaEventRecord(g->ev[slot], st);
     return slot;
 }
 
-void tstop(rt_grid *g, int slot, int kind, int64_t segs)
+void tstop(rt_grid *g, int slot, int kind, int64_t segs, int64_t bytes = 0, cudaStream_t st = nullptr)
 {
     if (slot < 0) return;
-    cudaEventRecord(g->ev[slot + 1], g->st);
+    cudaEventRecord(g->ev[slot + 1], st ? st : g->st);
     g->ev_kind.push_back(kind);
     g->ev_segs.push_back(segs);
+    g->ev_bytes.push_back(bytes);
 }
 
 int check_desc(const rt_grid_desc *d)
@@ -330,11 +337,40 @@ int build_geometry(rt_grid *g)
     RCK(dalloc(g, &g->d_csr_off, (size_t)g->nblk * (nvox + 1)));
     RCK(dalloc(g, &g->d_perm, g->n_seg));
     RCK(dalloc(g, &g->d_invL, (size_t)n_ang * nvox));
-    int32_t *cnt = nullptr, *cursor = nullptr;
+    int32_t *cnt = nullptr;
     int64_t *ctmp = nullptr;
     RCK(dalloc(g, &cnt, nvox));
-    RCK(dalloc(g, &cursor, nvox));
     RCK(dalloc(g, &ctmp, (nvox + 1) + scan_tmp_elems(nvox)));
+    // radix-sort scratch, freed once the lists are built
+    RadixScratch rs{};
+    rs.cap = std::max<int64_t>(1, g->max_blk_seg);
+    const int64_t nhist = 256 * radix_tiles(rs.cap);
+    std::vector<void *> rtmp;
+    auto talloc = [&](size_t bytes) -> void * {
+        void *q = nullptr;
+        if (cudaMalloc(&q, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        rtmp.push_back(q);
+        return q;
+    };
+    rs.kA = (uint32_t *)talloc(4 * (size_t)rs.cap);
+    rs.kB = (uint32_t *)talloc(4 * (size_t)rs.cap);
+    rs.vA = (int32_t *)talloc(4 * (size_t)rs.cap);
+    rs.vB = (int32_t *)talloc(4 * (size_t)rs.cap);
+    rs.hist = (int32_t *)talloc(4 * (size_t)nhist);
+    rs.off = (int64_t *)talloc(8 * (size_t)(nhist + 1));
+    rs.tmp = (int64_t *)talloc(8 * (size_t)scan_tmp_elems(nhist));
+    struct Free {
+        std::vector<void *> &v;
+        ~Free()
+        {
+            for (void *q : v) cudaFree(q);
+        }
+    } free_rtmp{rtmp};
+    if (!rs.kA || !rs.kB || !rs.vA || !rs.vB || !rs.hist || !rs.off || !rs.tmp)
+        return fail(RT_ENOMEM, "ownership-list sort scratch could not be allocated");
     RCK(dalloc(g, &g->d_ufirst, (size_t)g->nblk * (nvox + 1)));
     g->h_ubase.assign(g->nblk + 1, 0);
     g->h_nunits.assign(g->nblk, 0);
@@ -342,7 +378,7 @@ int build_geometry(rt_grid *g)
         int w0 = g->blk_w0[b], nw = g->blk_nw[b];
         int64_t lo = g->h_ang_seg_off[w0], ns = g->h_ang_seg_off[w0 + nw] - lo;
         int32_t *off = g->d_csr_off + (size_t)b * (nvox + 1);
-        CK(csr_build(nvox, g->d_vox + lo, ns, cnt, off, cursor, g->d_perm + lo, ctmp, g->st));
+        CK(csr_build(nvox, g->d_vox + lo, ns, cnt, off, g->d_perm + lo, ctmp, rs, g->st));
         CK(csr_invL(nvox, off, g->d_perm + lo, g->d_len64 + lo, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->st));
         int64_t *uf = g->d_ufirst + (size_t)b * (nvox + 1);
         CK(gather_units_build(nvox, off, cnt, uf, ctmp, g->st));
@@ -508,7 +544,6 @@ int build_geometry(rt_grid *g)
         dfree(g, stmp);
     }
     dfree(g, cnt);
-    dfree(g, cursor);
     dfree(g, ctmp);
     g->geom_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return RT_OK;
@@ -578,7 +613,7 @@ int run_fs(rt_grid *g, int prec, int homog, const double *S_src, double *J, doub
             t0 = tstart(g);
             CK(march_block<double, double2>(g->d_vox, g->d_len64, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs64, g->d_B,
                                             g->I_outer, homog, para, buf, g->march_chunk, g->st));
-            tstop(g, t0, 0, ns);
+            tstop(g, t0, 0, ns, 12 * ns);
             t1 = tstart(g);
             CK(gather_block<double2>(n, off, g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->d_wL32,
                                      g->d_wt, g->d_dirs, g->d_urow + g->h_ubase[b], g->d_ubeg + g->h_ubase[b],
@@ -592,7 +627,7 @@ int run_fs(rt_grid *g, int prec, int homog, const double *S_src, double *J, doub
             t0 = tstart(g);
             CK(march_block<float, float2>(g->d_vox, g->d_len32, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs32, g->d_B32,
                                           (float)g->I_outer, homog, para, buf, g->march_chunk, g->st));
-            tstop(g, t0, 0, ns);
+            tstop(g, t0, 0, ns, 8 * ns);
             t1 = tstart(g);
             CK(gather_block<float2>(n, off, g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->d_wL32,
                                     g->d_wt, g->d_dirs, g->d_urow + g->h_ubase[b], g->d_ubeg + g->h_ubase[b],
@@ -611,6 +646,168 @@ int run_fs(rt_grid *g, int prec, int homog, const double *S_src, double *J, doub
     return RT_OK;
 }
 
+// Streamed-weight march: allocate its per-segment arrays on first use (w l / L
+// computed then, from the geometry) and refresh (E, alpha, beta, gamma) after
+// chi changed.  Returns false when disabled or when the arrays do not fit; the
+// FP32 march then evaluates the weights itself.
+bool use_sw(rt_grid *g)
+{
+    if (!g->sw_enabled || g->sw_state < 0) return false;
+    if (g->sw_state == 0) {
+        void *a = nullptr, *b = nullptr;
+        if (cudaMalloc(&a, sizeof(float4) * (size_t)g->n_seg) != cudaSuccess ||
+            cudaMalloc(&b, sizeof(float) * (size_t)g->n_seg) != cudaSuccess) {
+            cudaGetLastError();
+            if (a) cudaFree(a);
+            g->sw_state = -1;
+            return false;
+        }
+        g->allocs.push_back(a);
+        g->allocs.push_back(b);
+        g->bytes += (int64_t)(20 * g->n_seg);
+        g->d_cw4 = (float4 *)a;
+        g->d_cg = (float *)b;
+        if (seg_weight(g->d_vox, g->d_len64, g->d_ang_seg_off, g->n_ang, g->d_wt, g->d_invL, g->nvox, g->n_seg, g->d_cg,
+                       g->st) != cudaSuccess) {
+            g->sw_state = -1;
+            return false;
+        }
+        g->launches++;
+        g->sw_state = 1;
+        g->cw_ok = false;
+    }
+    if (!g->cw_ok) {
+        if (coef_stream(g->d_vox, g->d_len64, g->d_chi, g->n_seg, g->d_cw4, g->st) != cudaSuccess) return false;
+        g->launches++;
+        g->cw_ok = true;
+    }
+    if (g->bnd_chunk != g->march_chunk) {  // bundle bounds for the current chunk
+        std::vector<int64_t> off(g->nblk + 1, 0);
+        for (int b = 0; b < g->nblk; ++b) {
+            const int w0 = g->blk_w0[b], nw = g->blk_nw[b];
+            const int64_t ns = g->h_ang_seg_off[w0 + nw] - g->h_ang_seg_off[w0];
+            off[b + 1] = off[b] + (ns + g->march_chunk - 1) / g->march_chunk;
+        }
+        if (g->d_bnd) {
+            cudaFree(g->d_bnd);
+            for (auto &q : g->allocs)
+                if (q == (void *)g->d_bnd) q = nullptr;
+            g->d_bnd = nullptr;
+        }
+        void *q = nullptr;
+        if (cudaMalloc(&q, sizeof(int2) * (size_t)std::max<int64_t>(1, off[g->nblk])) != cudaSuccess) {
+            cudaGetLastError();
+            g->sw_state = -1;
+            return false;
+        }
+        g->allocs.push_back(q);
+        g->d_bnd = (int2 *)q;
+        for (int b = 0; b < g->nblk; ++b) {
+            const int w0 = g->blk_w0[b], nw = g->blk_nw[b];
+            const int64_t lo = g->h_ang_seg_off[w0], ns = g->h_ang_seg_off[w0 + nw] - lo;
+            if (sw_bundles(g->d_ray_off, g->h_ang_ray_off[w0], g->h_ang_ray_off[w0 + nw], lo, ns, g->march_chunk,
+                           g->d_bnd + off[b], g->st) != cudaSuccess)
+                return false;
+            g->launches++;
+        }
+        g->h_bnd_off = off;
+        g->bnd_chunk = g->march_chunk;
+    }
+    return true;
+}
+
+SwMarch sw_march(rt_grid *g, int b, int homog, float *out)
+{
+    SwMarch m{};
+    if (b < 0 || b >= g->nblk) return m;  // nbundles = 0: no march part
+    const int w0 = g->blk_w0[b];
+    m.vox = g->d_vox;
+    m.cw = g->d_cw4;
+    m.cg = g->d_cg;
+    m.bnd = g->d_bnd + g->h_bnd_off[b];
+    m.seg_lo = g->h_ang_seg_off[w0];
+    m.nbundles = g->h_bnd_off[b + 1] - g->h_bnd_off[b];
+    m.cs = g->d_cs32;
+    m.B32 = g->d_B32;
+    m.I_outer = (float)g->I_outer;
+    m.homog = homog;
+    m.out = out;
+    return m;
+}
+
+SwGather sw_gather(rt_grid *g, int b, const float *buf, double *J)
+{
+    SwGather t{};
+    if (b < 0 || b >= g->nblk) return t;  // nshort = nchunks = 0: no gather part
+    const GatherJTables &jt = g->jt[b];
+    t.off = g->d_csr_off + (size_t)b * (g->nvox + 1);
+    t.jorder = jt.jorder;
+    t.jsell = jt.jsell;
+    t.jgbase = jt.jgbase;
+    t.crow = jt.crow;
+    t.cbeg = jt.cbeg;
+    t.clr = jt.clr;
+    t.lfirst = jt.lfirst;
+    t.cnt = jt.cnt;
+    t.perm = g->d_perm + g->h_ang_seg_off[g->blk_w0[b]];
+    t.part = g->d_partJ;
+    t.buf = buf;
+    t.J = J;
+    t.nshort = jt.nshort;
+    t.nchunks = jt.nchunks;
+    t.nbs = (jt.nshort + 255) / 256;
+    t.nlong = jt.nlong;
+    t.first = b == 0;
+    return t;
+}
+
+// Streamed-weight J.  Overlapped: the march of block b (grid stream, into
+// buffer b % 2) waits only for the gather of block b - 2, which read that
+// buffer; the gathers run in block order on the second stream, each after its
+// march, so J accumulates in the same order as without overlap.
+int run_fs_J_sw(rt_grid *g, int homog, double *J)
+{
+    float *bufs[2] = {(float *)g->d_segbuf, (float *)g->d_segbuf + g->max_blk_seg};
+    auto segs = [&](int b) -> int64_t {
+        return g->h_ang_seg_off[g->blk_w0[b] + g->blk_nw[b]] - g->h_ang_seg_off[g->blk_w0[b]];
+    };
+    if (!g->sw_overlap) {
+        for (int b = 0; b < g->nblk; ++b) {
+            int t0 = tstart(g);
+            CK(march_sw_launch(sw_march(g, b, homog, bufs[0]), g->sw_coarsen, g->st));
+            tstop(g, t0, 0, segs(b), 24 * segs(b));
+            t0 = tstart(g);
+            CK(gather_sw_launch(sw_gather(g, b, bufs[0], J), g->st));
+            tstop(g, t0, 1, segs(b));
+            g->launches += 2;
+        }
+        return RT_OK;
+    }
+    if (!g->st2) {
+        CK(cudaStreamCreateWithFlags(&g->st2, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : g->sev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    cudaEvent_t fork = g->sev[0], join = g->sev[1], *mdone = g->sev + 2, *gdone = g->sev + 4;
+    CK(cudaEventRecord(fork, g->st));
+    CK(cudaStreamWaitEvent(g->st2, fork, 0));
+    for (int b = 0; b < g->nblk; ++b) {
+        if (b >= 2) CK(cudaStreamWaitEvent(g->st, gdone[b & 1], 0));
+        int t0 = tstart(g);
+        CK(march_sw_launch(sw_march(g, b, homog, bufs[b & 1]), g->sw_coarsen, g->st));
+        tstop(g, t0, 0, segs(b), 24 * segs(b));
+        CK(cudaEventRecord(mdone[b & 1], g->st));
+        CK(cudaStreamWaitEvent(g->st2, mdone[b & 1], 0));
+        t0 = tstart(g, g->st2);
+        CK(gather_sw_launch(sw_gather(g, b, bufs[b & 1], J), g->st2));
+        tstop(g, t0, 1, segs(b), 0, g->st2);
+        CK(cudaEventRecord(gdone[b & 1], g->st2));
+        g->launches += 2;
+    }
+    CK(cudaEventRecord(join, g->st2));
+    CK(cudaStreamWaitEvent(g->st, join, 0));
+    return RT_OK;
+}
+
 // J-only formal solution (the ALI iteration reuses Lambda*, which depends on
 // chi and the lengths but not on S).
 int run_fs_J(rt_grid *g, int prec, int homog, const double *S_src, double *J)
@@ -619,6 +816,8 @@ int run_fs_J(rt_grid *g, int prec, int homog, const double *S_src, double *J)
     if (prec == RT_FP64) CK(pack_chiS64(n, g->d_chi, S_src, g->d_cs64, g->st));
     else CK(pack_chiS32(n, g->d_chi, S_src, g->d_B, g->d_cs32, g->d_B32, g->st));
     g->launches++;
+    if (prec == RT_MIXED && use_sw(g)) return run_fs_J_sw(g, homog, J);
+    CK(cudaGetLastError());
     for (int b = 0; b < g->nblk; ++b) {
         int w0 = g->blk_w0[b], nw = g->blk_nw[b];
         int64_t r_lo = g->h_ang_ray_off[w0], r_hi = g->h_ang_ray_off[w0 + nw];
@@ -630,7 +829,7 @@ int run_fs_J(rt_grid *g, int prec, int homog, const double *S_src, double *J)
             t0 = tstart(g);
             CK(march_block_J<double, double2>(g->d_vox, g->d_len64, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs64, g->d_B,
                                               g->I_outer, homog, buf, g->march_chunk, g->st));
-            tstop(g, t0, 0, ns);
+            tstop(g, t0, 0, ns, 12 * ns);
             t1 = tstart(g);
             CK(gather_J<double>(n, off, g->jt[b], g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_wL32,
                                 g->d_invL, g->d_wt, g->d_partJ, J, b == 0, g->st));
@@ -640,7 +839,7 @@ int run_fs_J(rt_grid *g, int prec, int homog, const double *S_src, double *J)
             t0 = tstart(g);
             CK(march_block_J<float, float2>(g->d_vox, g->d_len32, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs32,
                                             g->d_B32, (float)g->I_outer, homog, buf, g->march_chunk, g->st));
-            tstop(g, t0, 0, ns);
+            tstop(g, t0, 0, ns, 8 * ns);
             t1 = tstart(g);
             CK(gather_J<float>(n, off, g->jt[b], g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_wL32,
                                g->d_invL, g->d_wt, g->d_partJ, J, b == 0, g->st));
@@ -858,6 +1057,7 @@ int rt_set_opacity(rt_grid *g, const double *chi, const double *eps, const doubl
     CK(mark_parabola(g->d_vox, g->d_len64, g->d_chi, g->n_seg, g->interp == RT_PARABOLIC, g->st));
     g->launches++;
     g->lstar_prec = -1;
+    g->cw_ok = false;
     if (where == RT_HOST) RCK(sync(g));
     reset_ng(g);
     g->history.clear();
@@ -883,6 +1083,21 @@ int rt_tune(rt_grid *g, int knob, int value)
     if (knob == RT_TUNE_MARCH_CHUNK) {
         if (value < 64 || value > 16384) return fail(RT_EINVAL, "march chunk must be in [64, 16384]");
         g->march_chunk = value;
+        return RT_OK;
+    }
+    if (knob == RT_TUNE_STREAMED_WEIGHTS) {
+        if (value != 0 && value != 1) return fail(RT_EINVAL, "streamed weights: 0 or 1");
+        g->sw_enabled = value;
+        return RT_OK;
+    }
+    if (knob == RT_TUNE_OVERLAP) {
+        if (value != 0 && value != 1) return fail(RT_EINVAL, "overlap: 0 or 1");
+        g->sw_overlap = value;
+        return RT_OK;
+    }
+    if (knob == RT_TUNE_MARCH_COARSEN) {
+        if (value != 1 && value != 2 && value != 4) return fail(RT_EINVAL, "march coarsening must be 1, 2 or 4");
+        g->sw_coarsen = value;
         return RT_OK;
     }
     return fail(RT_EINVAL, "unknown tuning knob %d", knob);
@@ -1101,6 +1316,7 @@ int rt_set_timing(rt_grid *g, int enable)
         g->ev_used = 0;
         g->ev_kind.clear();
         g->ev_segs.clear();
+        g->ev_bytes.clear();
         g->launches = 0;
     }
     g->timing = enable != 0;
@@ -1120,6 +1336,7 @@ int rt_get_timing(rt_grid *g, rt_timing *t)
             t->march_ms += ms;
             t->march_launches++;
             t->march_segments += g->ev_segs[q];
+            t->march_bytes += g->ev_bytes[q];
         } else {
             t->gather_ms += ms;
             t->gather_launches++;

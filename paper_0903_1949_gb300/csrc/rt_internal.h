@@ -14,6 +14,9 @@
 #define RTK_PARA 0x10000000u      // parabolic weights for this segment (decided in FP64 from chi)
 #define RTK_VOXMASK 0x0FFFFFFFu
 
+// Long ownership lists are cut into chunks of this many entries (J-only gathers).
+#define RTK_JCHUNK 1024
+
 #define RTK_END_EXIT 1
 #define RTK_END_CORE 2
 #define RTK_END_LOST 3
@@ -58,8 +61,21 @@ cudaError_t scan_i32(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, c
 cudaError_t gather_i64(const int64_t *src, const int64_t *idx, int64_t *dst, int n, cudaStream_t st);
 
 // ---- ownership lists and gather (gather.cu) ----
+// Scratch of the stable radix sort that builds the ownership lists: keys and
+// values twice (cap entries each), digit histograms and their scan
+// (256 * radix_tiles(cap) entries, plus scan_tmp_elems of that for tmp).
+struct RadixScratch {
+    uint32_t *kA, *kB;
+    int32_t *vA, *vB;
+    int32_t *hist;
+    int64_t *off, *tmp;
+    int64_t cap;
+};
+int64_t radix_tiles(int64_t n);
+// Ownership (CSR) lists of one angle block: csr_off (nvox + 1) and perm_blk, every
+// voxel's segment indices in increasing order.
 cudaError_t csr_build(int nvox, const uint32_t *vox_blk, int64_t nseg_blk, int32_t *counts, int32_t *csr_off,
-                      int32_t *cursor, int32_t *perm_blk, int64_t *tmp, cudaStream_t st);
+                      int32_t *perm_blk, int64_t *tmp, const RadixScratch &rs, cudaStream_t st);
 cudaError_t csr_invL(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const double *len64_blk,
                      const int64_t *ang_seg_off, int w0, int nw, int64_t seg_lo, double *invL, cudaStream_t st);
 // Work units of one block's ownership lists (pieces of at most 32 entries):
@@ -150,6 +166,40 @@ cudaError_t march_block_J(const uint32_t *vox, const T *len, const int64_t *ray_
 cudaError_t march_block_I(const uint32_t *vox, const double *len, const int64_t *ray_off, int64_t r_lo, int64_t r_hi,
                           int64_t seg_lo, int64_t nseg, const double2 *chiS, const double *B, double I_outer, int homog,
                           double *out, int chunk, cudaStream_t st);
+// FP64 weights of every segment for the chi given, as FP32 (E, alpha, beta + [run start] alpha, gamma).
+cudaError_t coef_stream(const uint32_t *vox, const double *len64, const double *chi, int64_t nseg, float4 *cw,
+                        cudaStream_t st);
+// w_Omega l_s / L_{Omega v_s} of every segment (geometry only).
+cudaError_t seg_weight(const uint32_t *vox, const double *len64, const int64_t *ang_seg_off, int n_ang,
+                       const double *wt, const double *invL, int nvox, int64_t nseg, float *cg, cudaStream_t st);
+// Streamed-weight J-only formal solution (fs_sw.cu): march of one angle block,
+// J gather of one block.
+struct SwMarch {
+    const uint32_t *vox;
+    const float4 *cw;      // (E, alpha, beta, gamma) per segment (coef_stream)
+    const float *cg;       // w_Omega l / L per segment (seg_weight)
+    const int2 *bnd;       // bundle bounds of the block (sw_bundles), relative to seg_lo
+    int64_t seg_lo, nbundles;
+    const float2 *cs;      // (chi, S) per voxel, FP32
+    const float *B32;
+    float I_outer;
+    int homog;
+    float *out;            // c_s I_s per segment of the block
+};
+struct SwGather {
+    const int32_t *off, *jorder, *jsell, *crow, *cbeg, *clr, *lfirst, *perm;
+    const int64_t *jgbase;
+    int *cnt;
+    double *part;
+    const float *buf;      // c_s I_s of the block
+    double *J;
+    int64_t nshort, nchunks, nbs;
+    int nlong, first;
+};
+cudaError_t sw_bundles(const int64_t *ray_off, int64_t r_lo, int64_t r_hi, int64_t seg_lo, int64_t nseg, int chunk,
+                       int2 *bnd, cudaStream_t st);
+cudaError_t march_sw_launch(const SwMarch &m, int coarsen, cudaStream_t st);
+cudaError_t gather_sw_launch(const SwGather &t, cudaStream_t st);
 // One batched march work item: an angle block of one member (FP32, J only).
 struct MarchItem {
     const uint32_t *vox;

@@ -19,7 +19,7 @@ RT_CORE_B, RT_TRANSPARENT = 0, 1
 RT_FP64, RT_MIXED = 0, 1
 RT_PARABOLIC, RT_LINEAR = 0, 1
 RT_HOST, RT_DEVICE = 0, 1
-RT_TUNE_MARCH_CHUNK = 1
+RT_TUNE_MARCH_CHUNK, RT_TUNE_STREAMED_WEIGHTS, RT_TUNE_MARCH_COARSEN, RT_TUNE_OVERLAP = 1, 2, 3, 4
 
 _STATUS = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONVERGED", 5: "RT_ETIMEOUT",
            6: "RT_EDEVICE"}
@@ -50,7 +50,7 @@ class rt_info(ctypes.Structure):
 class rt_timing(ctypes.Structure):
     _fields_ = [("march_ms", ctypes.c_double), ("gather_ms", ctypes.c_double), ("march_launches", ctypes.c_int64),
                 ("gather_launches", ctypes.c_int64), ("march_segments", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("march_bytes", ctypes.c_int64)]
 
 
 _lib = None
