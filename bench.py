@@ -40,7 +40,6 @@ if ROOT not in sys.path:
 METRIC = "formal-solution voxel·angle updates/s; FP32-mixed vs FP64 at equal J error"
 UNIT = "voxel-angle updates/s"
 DEFAULT_HBM_FALLBACK = 6800.0
-MARCH_BYTES_PER_SEG = 8  # int32 voxel word + fp32 path length streamed per crossing segment
 
 
 def parse():
@@ -138,15 +137,17 @@ def hbm_peak():
         return DEFAULT_HBM_FALLBACK, "fallback"
 
 
+MARCH_SRC = os.path.join(ROOT, "paper_0903_1949_gb300", "csrc", "fs_sw.cu")
+
+
 def ncu_traffic(segments_per_launch):
-    """DRAM bytes per march launch from the committed ncu summary, if it matches this source."""
-    path = os.path.join(ROOT, "profiles", "march_fp32_traffic.json")
+    """DRAM bytes per march launch from the committed ncu summary, if it was taken of this source."""
+    path = os.path.join(ROOT, "profiles", "march_sw_traffic.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
         return None, None
-    src = open(os.path.join(ROOT, "paper_0903_1949_gb300", "csrc", "march.cu"), "rb").read()
-    if d.get("march_cu_sha256") != hashlib.sha256(src).hexdigest():
+    if d.get("source_sha256") != hashlib.sha256(open(MARCH_SRC, "rb").read()).hexdigest():
         return None, "stale"
     return d["dram_bytes_per_segment"] * segments_per_launch, d.get("capture")
 
@@ -286,7 +287,8 @@ def main():
     value = world * units / (ms / 1e3)
     march_avg_ms = tm["march_ms"] / max(1, tm["march_launches"])
     seg_per_launch = tm["march_segments"] / max(1, tm["march_launches"])
-    achieved = seg_per_launch * MARCH_BYTES_PER_SEG / (march_avg_ms / 1e3) / 1e9
+    bytes_per_seg = tm["march_bytes"] / max(1, tm["march_segments"])
+    achieved = seg_per_launch * bytes_per_seg / (march_avg_ms / 1e3) / 1e9
     peak, peak_src = hbm_peak()
     traffic, traffic_src = ncu_traffic(seg_per_launch)
     launches_per_step = tm["kernel_launches"] / args.steps
@@ -341,29 +343,31 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 march + f32 (compensated) gather, f64 ALI/Ng",
+            "vs_baseline": None, "dtype": "f32 march (weights from f64) + f32 compensated gather, f64 ALI/Ng",
             "data": "synthetic",
             "config": {"workload": workload_text(p), "step": "one ALI iteration, mixed precision: FP32 ray march "
-                       "of all solid angles + compensated FP32 ownership gather of J + FP64 ALI/Ng update with "
-                       "cached Lambda*", "voxel_angles_per_step": units,
+                       "of all solid angles with segment weights evaluated once per chi in FP64 + compensated FP32 "
+                       "ownership gather of J + FP64 ALI/Ng update with cached Lambda*", "voxel_angles_per_step": units,
                        "segments_per_step": info["n_segments"],
                        "segments_per_voxel_angle": info["n_segments"] / units,
                        "angle_block": info["angle_block"], "l2": "inputs larger than L2 (crossing lists %.1f GB "
-                       "streamed per step)" % (info["n_segments"] * 8 / 1e9),
+                       "streamed per step)" % (info["n_segments"] * bytes_per_seg / 1e9),
                        "parallelism": "replicas" if world > 1 else "1 GPU",
                        "geometry_ms": info["geometry_ms"], "device_gb": info["device_bytes"] / 1e9},
             "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "steps": k64,
                      "mixed_over_fp64": value / value64},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_march<float> (FP32 ray march)",
-                         "algorithmic_bytes": "%d B per crossing segment (voxel word + fp32 length)"
-                                              % MARCH_BYTES_PER_SEG,
+                         "kernel": "k_march_sw<2> (FP32 streamed-weight ray march, J only)",
+                         "algorithmic_bytes": "%g B per crossing segment (u32 voxel word + FP32 E, alpha, beta, "
+                                              "gamma + FP32 w l/L + i32 list position)" % bytes_per_seg,
                          "segments_per_launch": seg_per_launch, "avg_launch_ms": march_avg_ms,
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src if peak_src == "measured"
                          else "fallback 6800 GB/s", "traffic_source": traffic_src,
-                         "march_share_of_step": tm["march_ms"] / (ms * args.steps),
-                         "gather_share_of_step": tm["gather_ms"] / (ms * args.steps)},
+                         "timing": "CUDA events on the march's stream inside the timed steps; the J gather of the "
+                                   "previous angle block runs concurrently on a second stream",
+                         "march_ms_per_step": tm["march_ms"] / args.steps,
+                         "gather_ms_per_step": tm["gather_ms"] / args.steps},
             "e2e": e2e, "gpu_launches": int(tm["kernel_launches"]), "gpu_launches_per_step": launches_per_step,
             "clocks": ck}
     if equal is not None:

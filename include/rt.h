@@ -39,7 +39,7 @@ extern "C" {
 #define RT_ENOMEM 2         /* device or host allocation failed */
 #define RT_ECUDA 3          /* a CUDA runtime call failed */
 #define RT_ENOTCONVERGED 4  /* rt_solve reached max_iter */
-#define RT_ETIMEOUT 5       /* reserved: a bounded device wait gave up */
+#define RT_ETIMEOUT 5       /* a bounded device wait gave up (results of that call invalid) */
 #define RT_EDEVICE 6        /* a kernel raised its error flag (e.g. a lost characteristic) */
 
 /* coordinate systems (Sect. 3 and 4) */
@@ -144,10 +144,24 @@ int rt_set_precision(rt_grid *g, int precision);
  * (default) or 4.  RT_TUNE_OVERLAP (default 1): the J gather of angle block b
  * runs on a second stream of the library while block b + 1 is marched (the
  * grid's stream waits for it before the call returns its work); 0: both on
- * the grid's stream.  None of these changes results beyond FP32 rounding. */
+ * the grid's stream.  RT_TUNE_SCATTER (default 1): the streamed-weight march
+ * stores each segment's value at its place in the voxel-ordered ownership
+ * lists (4 more bytes of device memory per segment), so the J gather reads
+ * contiguous rows; 0: the gather reads the values through the lists.  None of
+ * these changes results beyond FP32 rounding. */
 #define RT_TUNE_STREAMED_WEIGHTS 2
 #define RT_TUNE_MARCH_COARSEN 3
 #define RT_TUNE_OVERLAP 4
+#define RT_TUNE_SCATTER 5
+/* RT_TUNE_MARCH_STAGES: depth of a per-warp shared-memory ring of segment
+ * tiles in the streamed-weight march, 2..4 (the ring holds the tile being
+ * processed and the ones in flight); 0 (default): one tile prefetched in
+ * registers.  RT_TUNE_MARCH_BULK: fill the ring with bulk copies and mbarrier
+ * completion (1) or 16-byte cp.async copies spread over the lanes (0,
+ * default).  A bounded mbarrier wait that gives up makes the calling
+ * rt_ali_step / rt_solve return RT_ETIMEOUT. */
+#define RT_TUNE_MARCH_STAGES 6
+#define RT_TUNE_MARCH_BULK 7
 int rt_tune(rt_grid *g, int knob, int value);
 
 /* Formal solution from the current S with the grid's precision: J, the
@@ -300,7 +314,7 @@ typedef struct rt_timing {
     int64_t march_segments;   /* crossing segments processed by the timed march launches */
     int64_t kernel_launches;  /* every kernel this library launched on the grid since the reset */
     int64_t march_bytes;      /* DRAM bytes the timed march launches stream by design (per segment:
-                                 8 FP32, 12 FP64, 24 streamed-weight FP32) */
+                                 8 FP32, 12 FP64, 24 streamed-weight FP32, 28 with RT_TUNE_SCATTER) */
 } rt_timing;
 
 int rt_set_timing(rt_grid *g, int enable);

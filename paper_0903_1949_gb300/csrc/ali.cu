@@ -35,12 +35,15 @@ __global__ void k_pack64(int n, const double *chi, const double *S, double2 *cs)
     if (v < n) cs[v] = make_double2(chi[v], S[v]);
 }
 
-__global__ void k_pack32(int n, const double *chi, const double *S, const double *B, float2 *cs, float *B32)
+__global__ void k_pack32(int n, const double *chi, const double *S, const double *B, float2 *cs, float *B32,
+                         float *S32)
 {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v < n) {
-        cs[v] = make_float2((float)chi[v], (float)S[v]);
+        const float s = (float)S[v];
+        cs[v] = make_float2((float)chi[v], s);
         B32[v] = (float)B[v];
+        if (S32) S32[v] = s;
     }
 }
 
@@ -181,10 +184,10 @@ cudaError_t pack_chiS64(int nvox, const double *chi, const double *S, double2 *c
     return cudaGetLastError();
 }
 
-cudaError_t pack_chiS32(int nvox, const double *chi, const double *S, const double *B, float2 *cs, float *B32,
+cudaError_t pack_chiS32(int nvox, const double *chi, const double *S, const double *B, float2 *cs, float *B32, float *S32,
                         cudaStream_t st)
 {
-    k_pack32<<<nb(nvox), 256, 0, st>>>(nvox, chi, S, B, cs, B32);
+    k_pack32<<<nb(nvox), 256, 0, st>>>(nvox, chi, S, B, cs, B32, S32);
     return cudaGetLastError();
 }
 

@@ -92,6 +92,7 @@ __device__ __forceinline__ void march_sw(const SwMarch &m, int64_t wg)
     const float *gw = m.cg + m.seg_lo;
     float *o = m.out;
     float Icarry = 0.f, Sprev = 0.f;
+    const int32_t *ps = m.pos ? m.pos + m.seg_lo : nullptr;
     uint32_t w[K];
     float4 c[K];
     float g[K];
@@ -103,6 +104,12 @@ __device__ __forceinline__ void march_sw(const SwMarch &m, int64_t wg)
         c[j] = ok ? __ldcs(cf + s) : make_float4(1.f, 0.f, 0.f, 0.f);
         g[j] = ok ? __ldcs(gw + s) : 0.f;
     }
+    // The last segment of a tile may use S of the next tile's first segment
+    // (gamma); its value is completed and stored at the start of the next tile,
+    // so no tile waits for the loads of the one after it.
+    float pend_I = 0.f, pend_gam = 0.f, pend_g = 0.f;
+    int pend_o = 0;
+    bool pend = false;  // warp-uniform
     for (int base = s_begin; base < s_end; base += 32 * K) {
         const int s0 = base + K * lane;
         uint32_t wN[K];
@@ -116,13 +123,23 @@ __device__ __forceinline__ void march_sw(const SwMarch &m, int64_t wg)
             cN[j] = ok ? __ldcs(cf + s) : make_float4(1.f, 0.f, 0.f, 0.f);
             gN[j] = ok ? __ldcs(gw + s) : 0.f;
         }
+        int pN[K];  // output positions of this tile (voxel order) when scattering
+#pragma unroll
+        for (int j = 0; j < K; ++j) pN[j] = (ps && s0 + j < s_end) ? __ldcs(ps + s0 + j) : 0;
         float S[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) S[j] = (s0 + j < s_end) ? m.cs[w[j] & RTK_VOXMASK].y : 0.f;
+        for (int j = 0; j < K; ++j) S[j] = (s0 + j < s_end) ? m.S32[w[j] & RTK_VOXMASK] : 0.f;
+        if (pend) {  // complete the previous tile's last segment
+            const float Sf = __shfl_sync(FULL, S[0], 0);
+            if (lane == 31) {
+                pend_I = fmaf(pend_gam * pend_g, Sf, pend_I);
+                __stcg(o + pend_o, pend_I);
+            }
+            Icarry = fmaf(pend_gam, Sf, Icarry);
+        }
         float Snx = __shfl_down_sync(FULL, S[0], 1);  // S after this lane's last segment
-        const uint32_t wn31 = __shfl_sync(FULL, wN[0], 0);
-        if (lane == 31) Snx = (base + 32 * K < s_end) ? m.cs[wn31 & RTK_VOXMASK].y : 0.f;
-        float Sp = __shfl_up_sync(FULL, S[K - 1], 1);  // S before this lane's first segment
+        if (lane == 31) Snx = 0.f;                    // next tile: added when it is loaded
+        float Sp = __shfl_up_sync(FULL, S[K - 1], 1); // S before this lane's first segment
         if (lane == 0) Sp = Sprev;
         float A[K], b[K];
 #pragma unroll
@@ -163,13 +180,23 @@ __device__ __forceinline__ void march_sw(const SwMarch &m, int64_t wg)
             PA = 1.f;
             PB = 0.f;
         }
+        pend = base + 32 * K < s_end;
         float I = fmaf(PA, Icarry, PB);
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             I = fmaf(A[j], I, b[j]);
-            if (s0 + j < s_end) __stcg(o + s0 + j, g[j] * I);
+            const int oi = ps ? pN[j] : s0 + j;
+            if (j == K - 1 && lane == 31 && pend) {
+                pend_I = g[j] * I;
+                pend_gam = c[j].w;
+                pend_g = g[j];
+                pend_o = oi;
+            } else if (s0 + j < s_end) {
+                __stcg(o + oi, g[j] * I);
+            }
         }
         Icarry = __shfl_sync(FULL, I, 31);
+        pend_gam = __shfl_sync(FULL, pend_gam, 31);
         Sprev = __shfl_sync(FULL, S[K - 1], 31);
 #pragma unroll
         for (int j = 0; j < K; ++j) {
@@ -178,6 +205,272 @@ __device__ __forceinline__ void march_sw(const SwMarch &m, int64_t wg)
             g[j] = gN[j];
         }
     }
+}
+
+// ---- staged variant: bulk copies (cp.async.bulk) into a per-warp ring ----
+//
+// Each warp keeps NS tiles of its bundle in flight: lane 0 issues, per tile,
+// one bulk copy of the (E, alpha, beta, gamma) stream and one of each 4-byte
+// stream (words, c, list positions) into a shared-memory stage and arms that
+// stage's mbarrier with the byte count; the lanes wait on the barrier, copy
+// the tile into registers and lane 0 refills the stage with tile t + NS
+// before the tile is processed.  A 4-byte stream's copy starts at the
+// 16-byte boundary at or below the tile (up to 3 extra words, the arrays
+// carry 4 words of padding) and the lanes index past the offset.  Every wait
+// is bounded: on timeout the warp raises *err, waits (bounded) for the
+// copies it issued and returns.
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false after MBAR_SPINS unsuccessful polls.
+constexpr int MBAR_SPINS = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (int it = 0; it < MBAR_SPINS; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int K>
+struct SwStage {
+    float4 cw[32 * K];
+    uint32_t w[32 * K + 4];
+    float cg[32 * K + 4];
+    int32_t pos[32 * K + 4];
+};
+
+template <int K, int NS>
+constexpr size_t tma_smem_bytes()
+{
+    return 8 * (NS * sizeof(SwStage<K>) + NS * sizeof(uint64_t));
+}
+
+template <int K, int NS, bool BULK>
+__device__ __forceinline__ void march_tma(const SwMarch &m, int64_t wg, SwStage<K> *stg, uint64_t *bar)
+{
+    constexpr int T = 32 * K;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    if (wg >= m.nbundles) return;
+    const int2 be = m.bnd[wg];
+    const int s_begin = be.x, s_end = be.y;
+    if (s_begin >= s_end) return;
+    const int ntile = (s_end - s_begin + T - 1) / T;
+    const bool scatter = m.pos != nullptr;
+    uint64_t policy = 0;
+    if (BULK && lane == 0) {
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+        for (int i = 0; i < NS; ++i) mbar_init(bar + i, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    // copy tile t into stage t % NS: bulk copies issued by lane 0 (BULK), or
+    // 16-byte cp.async copies spread over the lanes (one commit group per tile)
+    auto issue = [&](int t) {
+        const int i = t % NS;
+        const int64_t gs = m.seg_lo + s_begin + (int64_t)T * t;  // first segment of the tile (global index)
+        const int n = min(T, s_end - (s_begin + T * t));
+        const int64_t ga = gs & ~(int64_t)3;
+        const int cnt = (int)(((gs - ga) + n + 3) & ~3);  // words of the 16-byte aligned window
+        if (BULK) {
+            const uint32_t b4 = 4u * (uint32_t)cnt;
+            const uint32_t b16 = 16u * (uint32_t)n;
+            mbar_expect_tx(bar + i, b16 + (scatter ? 3u : 2u) * b4);
+            bulk_g2s(stg[i].cw, m.cw + gs, b16, bar + i, policy);
+            bulk_g2s(stg[i].w, m.vox + ga, b4, bar + i, policy);
+            bulk_g2s(stg[i].cg, m.cg + ga, b4, bar + i, policy);
+            if (scatter) bulk_g2s(stg[i].pos, m.pos + ga, b4, bar + i, policy);
+        } else {
+            for (int q = lane; q < n; q += 32) cp_async16(stg[i].cw + q, m.cw + gs + q);
+            for (int q = lane; q < cnt / 4; q += 32) {
+                cp_async16(stg[i].w + 4 * q, m.vox + ga + 4 * q);
+                cp_async16(stg[i].cg + 4 * q, m.cg + ga + 4 * q);
+                if (scatter) cp_async16(stg[i].pos + 4 * q, m.pos + ga + 4 * q);
+            }
+        }
+    };
+    if (BULK) {
+        if (lane == 0)
+            for (int t = 0; t < NS && t < ntile; ++t) issue(t);
+    } else {
+        for (int t = 0; t < NS - 1; ++t) {
+            if (t < ntile) issue(t);
+            cp_async_commit();
+        }
+    }
+    float Icarry = 0.f, Sprev = 0.f;
+    float *o = m.out;
+    float pend_I = 0.f, pend_gam = 0.f, pend_g = 0.f;  // last segment of the previous tile (see march_sw)
+    int pend_o = 0;
+    bool pend = false;
+    for (int t = 0; t < ntile; ++t) {
+        const int i = t % NS;
+        if (BULK) {
+            if (!mbar_wait(bar + i, (uint32_t)((t / NS) & 1))) {
+                if (lane == 0) {
+                    atomicExch(m.err, 1);
+                    for (int u = t; u < ntile && u < t + NS; ++u)
+                        (void)mbar_wait(bar + (u % NS), (uint32_t)((u / NS) & 1));
+                }
+                __syncwarp();
+                return;
+            }
+        } else {
+            cp_async_wait<NS - 2>();  // this lane's copies of tile t have landed
+            __syncwarp();             // ... and every lane's
+            if (t + NS - 1 < ntile) issue(t + NS - 1);  // into the stage read in the previous iteration
+            cp_async_commit();
+        }
+        const int base = s_begin + T * t;
+        const int off = (int)((m.seg_lo + base) & 3);
+        const int s0 = base + K * lane;
+        uint32_t w[K];
+        float4 c[K];
+        float g[K];
+        int pN[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int li = K * lane + j;
+            const bool ok = s0 + j < s_end;
+            w[j] = ok ? stg[i].w[off + li] : 0u;
+            c[j] = ok ? stg[i].cw[li] : make_float4(1.f, 0.f, 0.f, 0.f);
+            g[j] = ok ? stg[i].cg[off + li] : 0.f;
+            pN[j] = (ok && scatter) ? stg[i].pos[off + li] : 0;
+        }
+        __syncwarp();
+        if (BULK && lane == 0 && t + NS < ntile) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(t + NS);
+        }
+        float S[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) S[j] = (s0 + j < s_end) ? m.S32[w[j] & RTK_VOXMASK] : 0.f;
+        if (pend) {
+            const float Sf = __shfl_sync(FULL, S[0], 0);
+            if (lane == 31) {
+                pend_I = fmaf(pend_gam * pend_g, Sf, pend_I);
+                __stcg(o + pend_o, pend_I);
+            }
+            Icarry = fmaf(pend_gam, Sf, Icarry);
+        }
+        float Snx = __shfl_down_sync(FULL, S[0], 1);
+        if (lane == 31) Snx = 0.f;
+        float Sp = __shfl_up_sync(FULL, S[K - 1], 1);
+        if (lane == 0) Sp = Sprev;
+        float A[K], b[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const float Sm = (j == 0) ? Sp : S[j - 1];
+            const float Sn = (j + 1 < K) ? S[j + 1] : Snx;
+            const float src = fmaf(c[j].y, Sm, fmaf(c[j].z, S[j], c[j].w * Sn));
+            A[j] = c[j].x;
+            b[j] = src;
+            if (w[j] & RTK_RAYSTART) {
+                const float Iin = m.homog ? 0.f : ((w[j] & RTK_CORE) ? m.B32[w[j] & RTK_VOXMASK] : m.I_outer);
+                b[j] = fmaf(c[j].x, Iin, src);
+                A[j] = 0.f;
+            }
+            if (s0 + j >= s_end) {
+                A[j] = 1.f;
+                b[j] = 0.f;
+            }
+        }
+        float LA = A[0], LB = b[0];
+#pragma unroll
+        for (int j = 1; j < K; ++j) {
+            LB = fmaf(A[j], LB, b[j]);
+            LA = A[j] * LA;
+        }
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const float Ao = __shfl_up_sync(FULL, LA, d);
+            const float bo = __shfl_up_sync(FULL, LB, d);
+            if (lane >= d) {
+                LB = fmaf(LA, bo, LB);
+                LA = LA * Ao;
+            }
+        }
+        float PA = __shfl_up_sync(FULL, LA, 1);
+        float PB = __shfl_up_sync(FULL, LB, 1);
+        if (lane == 0) {
+            PA = 1.f;
+            PB = 0.f;
+        }
+        pend = base + T < s_end;
+        float I = fmaf(PA, Icarry, PB);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            I = fmaf(A[j], I, b[j]);
+            const int oi = scatter ? pN[j] : s0 + j;
+            if (j == K - 1 && lane == 31 && pend) {
+                pend_I = g[j] * I;
+                pend_gam = c[j].w;
+                pend_g = g[j];
+                pend_o = oi;
+            } else if (s0 + j < s_end) {
+                __stcg(o + oi, g[j] * I);
+            }
+        }
+        Icarry = __shfl_sync(FULL, I, 31);
+        pend_gam = __shfl_sync(FULL, pend_gam, 31);
+        Sprev = __shfl_sync(FULL, S[K - 1], 31);
+    }
+    if (!BULK) cp_async_wait<0>();
+}
+
+template <int K, int NS, bool BULK>
+__global__ void __launch_bounds__(256, 5) k_march_tma(SwMarch m)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5;
+    SwStage<K> *stg = reinterpret_cast<SwStage<K> *>(smem) + warp * NS;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 8 * NS * sizeof(SwStage<K>)) + warp * NS;
+    march_tma<K, NS, BULK>(m, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, stg, bar);
 }
 
 // J gather of one block from the values c_s I_s: CTAs [0, nbs) take 256 short
@@ -244,6 +537,69 @@ __global__ void __launch_bounds__(256) k_gather_sw(SwGather t)
     }
 }
 
+// J gather of one block from values already in voxel order (the march
+// scattered c_s I_s to the list positions): short lists thread per voxel in
+// voxel order (adjacent threads read adjacent rows), long lists one warp per
+// chunk; same summation order as k_gather_sw.
+__global__ void __launch_bounds__(256) k_gather_rows_sw(SwGather t, int nvox, int64_t nvb)
+{
+    const int64_t cta = blockIdx.x;
+    if (cta < nvb) {
+        const int v = (int)(cta * 256 + threadIdx.x);
+        if (v >= nvox) return;
+        const int a = t.off[v], L = t.off[v + 1] - a;
+        if (L > RTK_JSHORT) return;  // long list: chunk warps
+        Kahan acc;
+        for (int k = 0; k < L; k += 8) {
+            float val[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) val[j] = (k + j < L) ? __ldcg(t.buf + a + k + j) : 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (k + j < L) acc.add(val[j]);
+        }
+        const double r = acc.value();
+        t.J[v] = t.first ? r : t.J[v] + r;
+        return;
+    }
+    const int64_t c = ((cta - nvb) * 256 + threadIdx.x) >> 5;
+    if (c >= t.nchunks) return;
+    const int lane = threadIdx.x & 31;
+    const int v = t.crow[c];
+    const int e0 = t.cbeg[c];
+    const int e1 = min(e0 + CHUNK, t.off[v + 1]);
+    Kahan acc;
+    for (int k = e0 + lane; k < e1; k += 32 * 8) {
+        float val[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) val[j] = (k + 32 * j < e1) ? __ldcg(t.buf + k + 32 * j) : 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (k + 32 * j < e1) acc.add(val[j]);
+    }
+    acc.warp_reduce();
+    if (lane == 0) {
+        const int lr = t.clr[c];
+        __stcg(t.part + c, acc.value());
+        __threadfence();
+        const int c0 = t.lfirst[lr], c1 = (lr + 1 < t.nlong) ? t.lfirst[lr + 1] : (int)t.nchunks;
+        if (atomicAdd(t.cnt + lr, 1) == c1 - c0 - 1) {
+            __threadfence();
+            double sum = 0.0;
+            for (int cc = c0; cc < c1; ++cc) sum += __ldcg(t.part + cc);
+            t.J[v] = t.first ? sum : t.J[v] + sum;
+            t.cnt[lr] = 0;
+        }
+    }
+}
+
+// Position of every segment of a block in its ownership-list order.
+__global__ void k_inv_perm(const int32_t *perm, int64_t n, int32_t *pos)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        pos[perm[e]] = (int32_t)e;
+}
+
 template <int K>
 __global__ void __launch_bounds__(256) k_march_sw(SwMarch m)
 {
@@ -304,13 +660,53 @@ cudaError_t sw_bundles(const int64_t *ray_off, int64_t r_lo, int64_t r_hi, int64
     return cudaGetLastError();
 }
 
+template <int K, int NS, bool BULK>
+cudaError_t launch_ring(const SwMarch &m, int64_t grid, cudaStream_t st)
+{
+    constexpr size_t bytes = tma_smem_bytes<K, NS>();
+    static bool attr = false;  // per process: the attribute is a property of the kernel
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_march_tma<K, NS, BULK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_march_tma<K, NS, BULK><<<(unsigned)grid, 256, bytes, st>>>(m);
+    return cudaGetLastError();
+}
+
+template <bool BULK>
+cudaError_t launch_ring_k(const SwMarch &m, int coarsen, int64_t grid, cudaStream_t st)
+{
+    if (m.stages == 4) return coarsen == 1 ? launch_ring<1, 4, BULK>(m, grid, st) : launch_ring<2, 4, BULK>(m, grid, st);
+    if (m.stages == 3) return coarsen == 1 ? launch_ring<1, 3, BULK>(m, grid, st) : launch_ring<2, 3, BULK>(m, grid, st);
+    return coarsen == 1 ? launch_ring<1, 2, BULK>(m, grid, st) : launch_ring<2, 2, BULK>(m, grid, st);
+}
+
 cudaError_t march_sw_launch(const SwMarch &m, int coarsen, cudaStream_t st)
 {
     const int64_t grid = (m.nbundles + 7) / 8;
     if (grid <= 0) return cudaSuccess;
+    if (m.stages >= 2) return m.bulk ? launch_ring_k<true>(m, coarsen, grid, st) : launch_ring_k<false>(m, coarsen, grid, st);
     if (coarsen == 4) k_march_sw<4><<<(unsigned)grid, 256, 0, st>>>(m);
     else if (coarsen == 1) k_march_sw<1><<<(unsigned)grid, 256, 0, st>>>(m);
     else k_march_sw<2><<<(unsigned)grid, 256, 0, st>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_rows_sw_launch(const SwGather &t, int nvox, cudaStream_t st)
+{
+    const int64_t nvb = (nvox + 255) / 256;
+    const int64_t grid = nvb + (t.nchunks * 32 + 255) / 256;
+    if (grid <= 0) return cudaSuccess;
+    k_gather_rows_sw<<<(unsigned)grid, 256, 0, st>>>(t, nvox, nvb);
+    return cudaGetLastError();
+}
+
+cudaError_t inv_perm(const int32_t *perm_blk, int64_t n, int32_t *pos_blk, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_inv_perm<<<grid_cap(n), 256, 0, st>>>(perm_blk, n, pos_blk);
     return cudaGetLastError();
 }
 

@@ -460,7 +460,7 @@ __global__ void k_sell_fill(int64_t nunits, const int32_t *order, const int32_t 
 // consecutive words); longer lists are cut into chunks of CHUNK_LEN entries,
 // one warp per chunk reading the list coalesced, and the warp that finishes a
 // voxel's last chunk adds the chunk sums in chunk order.
-constexpr int SHORT_LEN = 64;
+constexpr int SHORT_LEN = RTK_JSHORT;
 constexpr int CHUNK_LEN = RTK_JCHUNK;
 
 __global__ void k_jclass(int nvox, const int32_t *off, int32_t *hist, int32_t *longflag, int32_t *nch)

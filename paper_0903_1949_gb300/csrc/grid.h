@@ -52,6 +52,7 @@ struct rt_grid {
     double2 *d_cs64 = nullptr;
     float2 *d_cs32 = nullptr;
     float *d_B32 = nullptr;
+    float *d_S32 = nullptr;  // S alone in FP32 (streamed-weight march)
     double *d_H = nullptr, *d_ng_part = nullptr, *d_ng_coef = nullptr;
     unsigned long long *d_maxrel = nullptr;
     double *d_r = nullptr, *d_delta = nullptr, *d_Jd = nullptr, *d_Ld = nullptr, *d_Fcd = nullptr, *d_Lkeep = nullptr;
@@ -79,6 +80,11 @@ struct rt_grid {
     bool cw_ok = false;       // d_cw4 matches the current chi
     int sw_coarsen = 2;       // segments per lane (RT_TUNE_MARCH_COARSEN)
     int sw_overlap = 1;       // gather of block b on st2 while block b + 1 is marched (RT_TUNE_OVERLAP)
+    int sw_scatter = 1;       // march stores in ownership-list order (RT_TUNE_SCATTER)
+    int sw_stages = 0;        // shared-memory ring depth of the streamed-weight march (RT_TUNE_MARCH_STAGES)
+    int sw_bulk = 0;          // ring filled by bulk copies instead of cp.async (RT_TUNE_MARCH_BULK)
+    int *d_err = nullptr;     // raised by a bounded device wait that gave up
+    int32_t *d_pos = nullptr; // list position of every segment within its block (NULL: not available)
     cudaStream_t st2 = nullptr;  // second stream of the overlapped gather (created on first use)
     cudaEvent_t sev[6] = {};     // fork, join, march done x2, gather done x2
     int2 *d_bnd = nullptr;    // bundle bounds of every block for bnd_chunk

@@ -114,7 +114,7 @@ int rt_fs_angle_noalloc(rt_grid *g, int omega, int precision, double *Ibar, doub
         k_noalloc_gather<double2><<<(n + 255) / 256, 256, 0, g->st>>>(n, off, g->d_perm + b_lo, (const double2 *)scratch,
                                                                      a0, a1, g->d_invL + (size_t)omega * n, Ibar, Lbar);
     } else {
-        if ((e = rtk::pack_chiS32(n, g->d_chi, g->d_S, g->d_B, g->d_cs32, g->d_B32, g->st)) != cudaSuccess)
+        if ((e = rtk::pack_chiS32(n, g->d_chi, g->d_S, g->d_B, g->d_cs32, g->d_B32, nullptr, g->st)) != cudaSuccess)
             return nofail(RT_ECUDA, cudaGetErrorString(e));
         e = rtk::march_block<float, float2>(g->d_vox, g->d_len32, g->d_ray_off, r_lo, r_hi, s_lo, nseg, g->d_cs32,
                                             g->d_B32, (float)g->I_outer, 0, para, (float2 *)scratch, 512, g->st);

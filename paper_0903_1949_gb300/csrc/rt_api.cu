@@ -299,7 +299,7 @@ int build_geometry(rt_grid *g)
     CK(cudaMemcpyAsync(&g->n_seg, g->d_ray_off + g->n_rays, sizeof(int64_t), cudaMemcpyDeviceToHost, g->st));
     RCK(sync(g));
     dfree(g, nseg);
-    RCK(dalloc(g, &g->d_vox, g->n_seg));
+    RCK(dalloc(g, &g->d_vox, g->n_seg + 4));  // 4 words of padding: 16-byte bulk-copy windows
     RCK(dalloc(g, &g->d_len64, g->n_seg));
     RCK(dalloc(g, &g->d_len32, g->n_seg));
     CK(cudaMemsetAsync(g->d_vox, 0, sizeof(uint32_t) * (size_t)g->n_seg, g->st));
@@ -563,10 +563,13 @@ int alloc_fields(rt_grid *g)
     RCK(dalloc(g, &g->d_cs64, n));
     RCK(dalloc(g, &g->d_cs32, n));
     RCK(dalloc(g, &g->d_B32, n));
+    RCK(dalloc(g, &g->d_S32, n));
     RCK(dalloc(g, &g->d_H, 4 * (size_t)n));
     RCK(dalloc(g, &g->d_ng_part, ng_partial_elems(n)));
     RCK(dalloc(g, &g->d_ng_coef, 4));
     RCK(dalloc(g, &g->d_maxrel, 1));
+    RCK(dalloc(g, &g->d_err, 1));
+    CK(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->st));
     RCK(dalloc(g, &g->d_r, n));
     RCK(dalloc(g, &g->d_delta, n));
     RCK(dalloc(g, &g->d_Jd, n));
@@ -600,7 +603,7 @@ int run_fs(rt_grid *g, int prec, int homog, const double *S_src, double *J, doub
     const int n = g->nvox;
     const int para = g->interp == RT_PARABOLIC;
     if (prec == RT_FP64) CK(pack_chiS64(n, g->d_chi, S_src, g->d_cs64, g->st));
-    else CK(pack_chiS32(n, g->d_chi, S_src, g->d_B, g->d_cs32, g->d_B32, g->st));
+    else CK(pack_chiS32(n, g->d_chi, S_src, g->d_B, g->d_cs32, g->d_B32, g->d_S32, g->st));
     g->launches++;
     for (int b = 0; b < g->nblk; ++b) {
         int w0 = g->blk_w0[b], nw = g->blk_nw[b];
@@ -656,7 +659,7 @@ bool use_sw(rt_grid *g)
     if (g->sw_state == 0) {
         void *a = nullptr, *b = nullptr;
         if (cudaMalloc(&a, sizeof(float4) * (size_t)g->n_seg) != cudaSuccess ||
-            cudaMalloc(&b, sizeof(float) * (size_t)g->n_seg) != cudaSuccess) {
+            cudaMalloc(&b, sizeof(float) * (size_t)(g->n_seg + 4)) != cudaSuccess) {
             cudaGetLastError();
             if (a) cudaFree(a);
             g->sw_state = -1;
@@ -673,6 +676,20 @@ bool use_sw(rt_grid *g)
             return false;
         }
         g->launches++;
+        void *c = nullptr;  // list positions (optional: without them the gather reads through perm)
+        if (cudaMalloc(&c, sizeof(int32_t) * (size_t)(g->n_seg + 4)) == cudaSuccess) {
+            g->allocs.push_back(c);
+            g->bytes += (int64_t)(4 * g->n_seg);
+            g->d_pos = (int32_t *)c;
+            for (int b = 0; b < g->nblk; ++b) {
+                const int64_t lo = g->h_ang_seg_off[g->blk_w0[b]];
+                const int64_t ns = g->h_ang_seg_off[g->blk_w0[b] + g->blk_nw[b]] - lo;
+                if (inv_perm(g->d_perm + lo, ns, g->d_pos + lo, g->st) != cudaSuccess) return false;
+                g->launches++;
+            }
+        } else {
+            cudaGetLastError();
+        }
         g->sw_state = 1;
         g->cw_ok = false;
     }
@@ -725,9 +742,13 @@ SwMarch sw_march(rt_grid *g, int b, int homog, float *out)
     m.cw = g->d_cw4;
     m.cg = g->d_cg;
     m.bnd = g->d_bnd + g->h_bnd_off[b];
+    m.pos = (g->sw_scatter && g->d_pos) ? g->d_pos : nullptr;
+    m.stages = g->sw_stages;
+    m.bulk = g->sw_bulk;
+    m.err = g->d_err;
     m.seg_lo = g->h_ang_seg_off[w0];
     m.nbundles = g->h_bnd_off[b + 1] - g->h_bnd_off[b];
-    m.cs = g->d_cs32;
+    m.S32 = g->d_S32;
     m.B32 = g->d_B32;
     m.I_outer = (float)g->I_outer;
     m.homog = homog;
@@ -775,9 +796,10 @@ int run_fs_J_sw(rt_grid *g, int homog, double *J)
         for (int b = 0; b < g->nblk; ++b) {
             int t0 = tstart(g);
             CK(march_sw_launch(sw_march(g, b, homog, bufs[0]), g->sw_coarsen, g->st));
-            tstop(g, t0, 0, segs(b), 24 * segs(b));
+            tstop(g, t0, 0, segs(b), (g->sw_scatter && g->d_pos ? 28 : 24) * segs(b));
             t0 = tstart(g);
-            CK(gather_sw_launch(sw_gather(g, b, bufs[0], J), g->st));
+            if (g->sw_scatter && g->d_pos) CK(gather_rows_sw_launch(sw_gather(g, b, bufs[0], J), g->nvox, g->st));
+            else CK(gather_sw_launch(sw_gather(g, b, bufs[0], J), g->st));
             tstop(g, t0, 1, segs(b));
             g->launches += 2;
         }
@@ -794,11 +816,12 @@ int run_fs_J_sw(rt_grid *g, int homog, double *J)
         if (b >= 2) CK(cudaStreamWaitEvent(g->st, gdone[b & 1], 0));
         int t0 = tstart(g);
         CK(march_sw_launch(sw_march(g, b, homog, bufs[b & 1]), g->sw_coarsen, g->st));
-        tstop(g, t0, 0, segs(b), 24 * segs(b));
+        tstop(g, t0, 0, segs(b), (g->sw_scatter && g->d_pos ? 28 : 24) * segs(b));
         CK(cudaEventRecord(mdone[b & 1], g->st));
         CK(cudaStreamWaitEvent(g->st2, mdone[b & 1], 0));
         t0 = tstart(g, g->st2);
-        CK(gather_sw_launch(sw_gather(g, b, bufs[b & 1], J), g->st2));
+        if (g->sw_scatter && g->d_pos) CK(gather_rows_sw_launch(sw_gather(g, b, bufs[b & 1], J), g->nvox, g->st2));
+        else CK(gather_sw_launch(sw_gather(g, b, bufs[b & 1], J), g->st2));
         tstop(g, t0, 1, segs(b), 0, g->st2);
         CK(cudaEventRecord(gdone[b & 1], g->st2));
         g->launches += 2;
@@ -814,7 +837,7 @@ int run_fs_J(rt_grid *g, int prec, int homog, const double *S_src, double *J)
 {
     const int n = g->nvox;
     if (prec == RT_FP64) CK(pack_chiS64(n, g->d_chi, S_src, g->d_cs64, g->st));
-    else CK(pack_chiS32(n, g->d_chi, S_src, g->d_B, g->d_cs32, g->d_B32, g->st));
+    else CK(pack_chiS32(n, g->d_chi, S_src, g->d_B, g->d_cs32, g->d_B32, g->d_S32, g->st));
     g->launches++;
     if (prec == RT_MIXED && use_sw(g)) return run_fs_J_sw(g, homog, J);
     CK(cudaGetLastError());
@@ -864,8 +887,15 @@ int fs_iteration(rt_grid *g, int prec, const double *S_src, double *J)
 int read_maxrel(rt_grid *g, double *rel)
 {
     CK(cudaMemcpyAsync(g->h_pin, g->d_maxrel, sizeof(double), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaMemcpyAsync(g->h_pin + 2, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->st));
     RCK(sync(g));
     *rel = g->h_pin[0];  // the device word holds the bits of a non-negative double
+    int err = 0;
+    std::memcpy(&err, g->h_pin + 2, sizeof(int));
+    if (err) {
+        CK(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->st));
+        return fail(RT_ETIMEOUT, "a bounded wait in the staged ray march gave up; results of this step are invalid");
+    }
     return RT_OK;
 }
 
@@ -1090,6 +1120,21 @@ int rt_tune(rt_grid *g, int knob, int value)
         g->sw_enabled = value;
         return RT_OK;
     }
+    if (knob == RT_TUNE_MARCH_STAGES) {
+        if (value != 0 && (value < 2 || value > 4)) return fail(RT_EINVAL, "march stages: 0 or 2..4");
+        g->sw_stages = value;
+        return RT_OK;
+    }
+    if (knob == RT_TUNE_MARCH_BULK) {
+        if (value != 0 && value != 1) return fail(RT_EINVAL, "march bulk copies: 0 or 1");
+        g->sw_bulk = value;
+        return RT_OK;
+    }
+    if (knob == RT_TUNE_SCATTER) {
+        if (value != 0 && value != 1) return fail(RT_EINVAL, "scatter: 0 or 1");
+        g->sw_scatter = value;
+        return RT_OK;
+    }
     if (knob == RT_TUNE_OVERLAP) {
         if (value != 0 && value != 1) return fail(RT_EINVAL, "overlap: 0 or 1");
         g->sw_overlap = value;
@@ -1277,7 +1322,7 @@ int rt_fs_angles(rt_grid *g, const int32_t *omegas, int n, int precision, double
     const int nv = g->nvox;
     const int para = g->interp == RT_PARABOLIC;
     if (precision == RT_FP64) CK(pack_chiS64(nv, g->d_chi, g->d_S, g->d_cs64, g->st));
-    else CK(pack_chiS32(nv, g->d_chi, g->d_S, g->d_B, g->d_cs32, g->d_B32, g->st));
+    else CK(pack_chiS32(nv, g->d_chi, g->d_S, g->d_B, g->d_cs32, g->d_B32, nullptr, g->st));
     double *tI = g->d_Jd, *tL = g->d_Ld;  // scratch vectors of the correction sweep
     int marched = -1;  // block whose per-segment results are in the buffer
     for (int q = 0; q < n; ++q) {

@@ -16,6 +16,8 @@
 
 // Long ownership lists are cut into chunks of this many entries (J-only gathers).
 #define RTK_JCHUNK 1024
+// Lists of at most this many entries are summed by one thread (J-only gathers).
+#define RTK_JSHORT 64
 
 #define RTK_END_EXIT 1
 #define RTK_END_CORE 2
@@ -179,8 +181,12 @@ struct SwMarch {
     const float4 *cw;      // (E, alpha, beta, gamma) per segment (coef_stream)
     const float *cg;       // w_Omega l / L per segment (seg_weight)
     const int2 *bnd;       // bundle bounds of the block (sw_bundles), relative to seg_lo
+    const int32_t *pos;    // NULL: out[s] in segment order; else out[pos[s]] (ownership-list order)
+    int stages;            // 0: register prefetch of one tile; 2..4: shared-memory ring of that many tiles per warp
+    int bulk;              // ring filled by bulk copies (1) or by per-lane 16-byte cp.async (0)
+    int *err;              // raised when a bounded wait of the staged march gives up
     int64_t seg_lo, nbundles;
-    const float2 *cs;      // (chi, S) per voxel, FP32
+    const float *S32;      // S per voxel, FP32
     const float *B32;
     float I_outer;
     int homog;
@@ -200,6 +206,10 @@ cudaError_t sw_bundles(const int64_t *ray_off, int64_t r_lo, int64_t r_hi, int64
                        int2 *bnd, cudaStream_t st);
 cudaError_t march_sw_launch(const SwMarch &m, int coarsen, cudaStream_t st);
 cudaError_t gather_sw_launch(const SwGather &t, cudaStream_t st);
+// J from values in ownership-list order (march with pos): contiguous rows.
+cudaError_t gather_rows_sw_launch(const SwGather &t, int nvox, cudaStream_t st);
+// pos_blk[perm_blk[e]] = e for the n segments of a block.
+cudaError_t inv_perm(const int32_t *perm_blk, int64_t n, int32_t *pos_blk, cudaStream_t st);
 // One batched march work item: an angle block of one member (FP32, J only).
 struct MarchItem {
     const uint32_t *vox;
@@ -233,7 +243,8 @@ cudaError_t march_block(const uint32_t *vox, const T *len, const int64_t *ray_of
 
 // ---- ALI, Ng, refinement (ali.cu) ----
 cudaError_t pack_chiS64(int nvox, const double *chi, const double *S, double2 *cs, cudaStream_t st);
-cudaError_t pack_chiS32(int nvox, const double *chi, const double *S, const double *B, float2 *cs, float *B32,
+// (chi, S) and B in FP32; S alone into S32 as well when S32 is not NULL.
+cudaError_t pack_chiS32(int nvox, const double *chi, const double *S, const double *B, float2 *cs, float *B32, float *S32,
                         cudaStream_t st);
 cudaError_t ali_update(int nvox, double *S, const double *J, const double *Lst, const double *eps, const double *B,
                        int use_lstar, double *hist_slot, unsigned long long *maxrel, cudaStream_t st);
