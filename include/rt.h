@@ -304,8 +304,11 @@ int rt_batch_autotune(rt_batch *b, int32_t *chunk_out, int32_t *grid_out, double
 
 /* Device timing of the hot kernels.  rt_set_timing(g, 1) resets the counters
  * and brackets every ray-march and gather launch of later calls with CUDA
- * events on the grid's stream; rt_set_timing(g, 0) stops recording (counters
- * are kept).  rt_get_timing synchronises the stream and returns the sums. */
+ * events on the stream each runs on; rt_set_timing(g, N) with N > 1 brackets
+ * only every N-th ray-march launch (less event overhead; the march sums then
+ * cover that sample, the gather sums stay 0); rt_set_timing(g, 0) stops
+ * recording (counters are kept).  N < 0 is RT_EINVAL.  rt_get_timing
+ * synchronises the stream and returns the sums. */
 typedef struct rt_timing {
     double march_ms;          /* summed event time of ray-march launches */
     double gather_ms;         /* summed event time of ownership-gather launches */

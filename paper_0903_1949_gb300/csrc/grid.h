@@ -65,6 +65,8 @@ struct rt_grid {
     std::vector<double> history;
     // kernel timing (rt_set_timing) and launch accounting
     bool timing = false;
+    int timing_every = 1;             // 1: every march and gather launch; N > 1: every N-th march launch
+    int64_t timing_count = 0;
     std::vector<cudaEvent_t> ev;      // event pool, two per timed launch
     size_t ev_used = 0;
     std::vector<int> ev_kind;         // 0 march, 1 gather

@@ -105,12 +105,17 @@ int sync(rt_grid *g)
     return RT_OK;
 }
 
-// Start event of a timed launch on stream st (default: the grid's stream);
-// returns its slot, or -1 when timing is off.
-int tstart(rt_grid *g, cudaStream_t st = nullptr)
+// Start event of a timed launch of `kind` (0 march, 1 gather) on stream st
+// (default: the grid's stream); returns its slot, or -1 when this launch is not
+// timed (timing off, or sampling every timing_every-th march launch only).
+int tstart(rt_grid *g, int kind, cudaStream_t st = nullptr)
 {
     if (!st) st = g->st;
     if (!g->timing) return -1;
+    if (g->timing_every > 1) {
+        if (kind != 0) return -1;
+        if (g->timing_count++ % g->timing_every != 0) return -1;
+    }
     if (g->ev_used + 2 > g->ev.size()) {
         for (int q = 0; q < 64; ++q) {
             cudaEvent_t e;
@@ -613,11 +618,11 @@ int run_fs(rt_grid *g, int prec, int homog, const double *S_src, double *J, doub
         int t0, t1;
         if (prec == RT_FP64) {
             double2 *buf = (double2 *)g->d_segbuf;
-            t0 = tstart(g);
+            t0 = tstart(g, 0);
             CK(march_block<double, double2>(g->d_vox, g->d_len64, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs64, g->d_B,
                                             g->I_outer, homog, para, buf, g->march_chunk, g->st));
             tstop(g, t0, 0, ns, 12 * ns);
-            t1 = tstart(g);
+            t1 = tstart(g, 1);
             CK(gather_block<double2>(n, off, g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->d_wL32,
                                      g->d_wt, g->d_dirs, g->d_urow + g->h_ubase[b], g->d_ubeg + g->h_ubase[b],
                                      g->d_ufirst + (size_t)b * (n + 1), g->h_nunits[b], g->d_multi + g->h_mbase[b],
@@ -627,11 +632,11 @@ int run_fs(rt_grid *g, int prec, int homog, const double *S_src, double *J, doub
             tstop(g, t1, 1, ns);
         } else {
             float2 *buf = (float2 *)g->d_segbuf;
-            t0 = tstart(g);
+            t0 = tstart(g, 0);
             CK(march_block<float, float2>(g->d_vox, g->d_len32, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs32, g->d_B32,
                                           (float)g->I_outer, homog, para, buf, g->march_chunk, g->st));
             tstop(g, t0, 0, ns, 8 * ns);
-            t1 = tstart(g);
+            t1 = tstart(g, 1);
             CK(gather_block<float2>(n, off, g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_invL, g->d_wL32,
                                     g->d_wt, g->d_dirs, g->d_urow + g->h_ubase[b], g->d_ubeg + g->h_ubase[b],
                                      g->d_ufirst + (size_t)b * (n + 1), g->h_nunits[b], g->d_multi + g->h_mbase[b],
@@ -794,10 +799,10 @@ int run_fs_J_sw(rt_grid *g, int homog, double *J)
     };
     if (!g->sw_overlap) {
         for (int b = 0; b < g->nblk; ++b) {
-            int t0 = tstart(g);
+            int t0 = tstart(g, 0);
             CK(march_sw_launch(sw_march(g, b, homog, bufs[0]), g->sw_coarsen, g->st));
             tstop(g, t0, 0, segs(b), (g->sw_scatter && g->d_pos ? 28 : 24) * segs(b));
-            t0 = tstart(g);
+            t0 = tstart(g, 1);
             if (g->sw_scatter && g->d_pos) CK(gather_rows_sw_launch(sw_gather(g, b, bufs[0], J), g->nvox, g->st));
             else CK(gather_sw_launch(sw_gather(g, b, bufs[0], J), g->st));
             tstop(g, t0, 1, segs(b));
@@ -814,12 +819,12 @@ int run_fs_J_sw(rt_grid *g, int homog, double *J)
     CK(cudaStreamWaitEvent(g->st2, fork, 0));
     for (int b = 0; b < g->nblk; ++b) {
         if (b >= 2) CK(cudaStreamWaitEvent(g->st, gdone[b & 1], 0));
-        int t0 = tstart(g);
+        int t0 = tstart(g, 0);
         CK(march_sw_launch(sw_march(g, b, homog, bufs[b & 1]), g->sw_coarsen, g->st));
         tstop(g, t0, 0, segs(b), (g->sw_scatter && g->d_pos ? 28 : 24) * segs(b));
         CK(cudaEventRecord(mdone[b & 1], g->st));
         CK(cudaStreamWaitEvent(g->st2, mdone[b & 1], 0));
-        t0 = tstart(g, g->st2);
+        t0 = tstart(g, 1, g->st2);
         if (g->sw_scatter && g->d_pos) CK(gather_rows_sw_launch(sw_gather(g, b, bufs[b & 1], J), g->nvox, g->st2));
         else CK(gather_sw_launch(sw_gather(g, b, bufs[b & 1], J), g->st2));
         tstop(g, t0, 1, segs(b), 0, g->st2);
@@ -849,21 +854,21 @@ int run_fs_J(rt_grid *g, int prec, int homog, const double *S_src, double *J)
         int t0, t1;
         if (prec == RT_FP64) {
             double *buf = (double *)g->d_segbuf;
-            t0 = tstart(g);
+            t0 = tstart(g, 0);
             CK(march_block_J<double, double2>(g->d_vox, g->d_len64, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs64, g->d_B,
                                               g->I_outer, homog, buf, g->march_chunk, g->st));
             tstop(g, t0, 0, ns, 12 * ns);
-            t1 = tstart(g);
+            t1 = tstart(g, 1);
             CK(gather_J<double>(n, off, g->jt[b], g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_wL32,
                                 g->d_invL, g->d_wt, g->d_partJ, J, b == 0, g->st));
             tstop(g, t1, 1, ns);
         } else {
             float *buf = (float *)g->d_segbuf;
-            t0 = tstart(g);
+            t0 = tstart(g, 0);
             CK(march_block_J<float, float2>(g->d_vox, g->d_len32, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs32,
                                             g->d_B32, (float)g->I_outer, homog, buf, g->march_chunk, g->st));
             tstop(g, t0, 0, ns, 8 * ns);
-            t1 = tstart(g);
+            t1 = tstart(g, 1);
             CK(gather_J<float>(n, off, g->jt[b], g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_wL32,
                                g->d_invL, g->d_wt, g->d_partJ, J, b == 0, g->st));
             tstop(g, t1, 1, ns);
@@ -1355,6 +1360,7 @@ int rt_fs_angles(rt_grid *g, const int32_t *omegas, int n, int precision, double
 int rt_set_timing(rt_grid *g, int enable)
 {
     if (!g) return fail(RT_EINVAL, "grid is NULL");
+    if (enable < 0) return fail(RT_EINVAL, "timing: 0 (off), 1 (every launch) or N > 1 (every N-th march launch)");
     CK(cudaSetDevice(g->device));
     if (enable) {
         RCK(sync(g));
@@ -1363,6 +1369,8 @@ int rt_set_timing(rt_grid *g, int enable)
         g->ev_segs.clear();
         g->ev_bytes.clear();
         g->launches = 0;
+        g->timing_count = 0;
+        g->timing_every = enable;
     }
     g->timing = enable != 0;
     return RT_OK;

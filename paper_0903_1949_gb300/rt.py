@@ -305,7 +305,9 @@ def rt_tune(h, knob, value):
 
 
 def rt_set_timing(h, enable=True):
-    return _check(load().rt_set_timing(h, 1 if enable else 0))
+    """enable: False/0 off, True/1 every march and gather launch, N > 1 every N-th march launch."""
+    v = int(enable) if not isinstance(enable, bool) else (1 if enable else 0)
+    return _check(load().rt_set_timing(h, v))
 
 
 def rt_get_timing(h):

@@ -1,6 +1,7 @@
-"""Adjoint checks at the paper's full spherical grid size (65 x 33 x 65 voxels,
-32 x 32 solid angles, chi ~ r^-2 with 20% noise; Sect. 3.1), through the
-public API only.
+"""Adjoint checks at full grid sizes, through the public API only: the paper's
+spherical grid (65 x 33 x 65 voxels, 32 x 32 solid angles, chi ~ r^-2 with 20%
+noise; Sect. 3.1) and the deep 129 x 65 x 129 grid (tau 1e4) with 16 x 16 solid
+angles (its 64 x 64 crossing lists would not fit one GPU).
 
 With eps = 1 the ALI fixed point is S = B whatever chi is, and J, F are
 linear in (S, B) jointly (boundary intensities B on the core, 0 outside), so
@@ -23,11 +24,13 @@ pytestmark = pytest.mark.gpu
 H_REL = 1e-6
 
 
-@pytest.fixture(scope="module")
-def full():
+@pytest.fixture(scope="module", params=[("sph65", {}), ("sph129", {"n_mu": 16, "n_phi": 16})],
+                ids=["sph65", "sph129_a256"])
+def full(request):
     Bd.build()
     rt.load()
-    p = I.make_problem("sph65")
+    name, over = request.param
+    p = I.make_problem(name, **over)
     g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=rt.RT_FP64,
                 ng=False)
     n = p["chi"].size

@@ -1,0 +1,96 @@
+"""The FP32 J-only march of the ALI iteration in all its launch configurations
+(rt_tune): streamed weights on/off, segments per lane, bundle size, list-order
+output (scatter), overlapped gather, shared-memory rings fed by cp.async or
+bulk copies.  Configurations that only move data differently give bit-identical
+iterates; the others agree to FP32 rounding; all stay within the mixed-precision
+bar of the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_0903_1949_gb300 import build as Bd
+from paper_0903_1949_gb300 import inputs as I
+from paper_0903_1949_gb300 import rt
+from tests.helpers import tiny_problem
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    Bd.build()
+    rt.load()
+
+
+def _problems():
+    p1 = I.make_problem("sph17")
+    p1["nvox"] = p1["chi"].size
+    p2 = tiny_problem(I.CYLINDRICAL, (9, 8, 7), 6, 6, I.TRANSPARENT, eps=0.05, seed=21)  # hole: restarts
+    p3 = tiny_problem(I.SPHERICAL, (11, 6, 10), 6, 6, I.CORE_B, eps=0.1, seed=22)
+    return {"sph17": (p1, rt.RT_PARABOLIC), "cyl_hole": (p2, rt.RT_PARABOLIC), "sph_linear": (p3, rt.RT_LINEAR)}
+
+
+def _iterate(p, interp, knobs):
+    g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], interp=interp,
+                precision=rt.RT_MIXED, ng=False)
+    for k, v in knobs.items():
+        g.tune(k, v)
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    for _ in range(STEPS):
+        g.ali_step()
+    S = g.S()
+    g.close()
+    return S
+
+
+T = rt
+BASE = {T.RT_TUNE_STREAMED_WEIGHTS: 1, T.RT_TUNE_MARCH_COARSEN: 2, T.RT_TUNE_MARCH_CHUNK: 512, T.RT_TUNE_SCATTER: 1,
+        T.RT_TUNE_OVERLAP: 1, T.RT_TUNE_MARCH_STAGES: 0, T.RT_TUNE_MARCH_BULK: 0}
+# same arithmetic in the same order, data moved differently: bit-identical
+SAME = [
+    {T.RT_TUNE_SCATTER: 0},
+    {T.RT_TUNE_OVERLAP: 0},
+    {T.RT_TUNE_SCATTER: 0, T.RT_TUNE_OVERLAP: 0},
+    {T.RT_TUNE_MARCH_STAGES: 2},
+    {T.RT_TUNE_MARCH_STAGES: 3},
+    {T.RT_TUNE_MARCH_STAGES: 4, T.RT_TUNE_SCATTER: 0},
+    {T.RT_TUNE_MARCH_STAGES: 3, T.RT_TUNE_MARCH_BULK: 1},
+    {T.RT_TUNE_MARCH_STAGES: 2, T.RT_TUNE_MARCH_BULK: 1, T.RT_TUNE_OVERLAP: 0},
+]
+# another association of the FP32 scan, or the on-the-fly weights: FP32 rounding
+CLOSE = [
+    {T.RT_TUNE_MARCH_COARSEN: 1},
+    {T.RT_TUNE_MARCH_COARSEN: 4},
+    {T.RT_TUNE_MARCH_CHUNK: 64},
+    {T.RT_TUNE_MARCH_CHUNK: 4096, T.RT_TUNE_MARCH_COARSEN: 1, T.RT_TUNE_MARCH_STAGES: 3},
+    {T.RT_TUNE_STREAMED_WEIGHTS: 0},
+]
+
+
+@pytest.mark.parametrize("name", ["sph17", "cyl_hole", "sph_linear"])
+def test_march_configurations(name):
+    p, interp = _problems()[name]
+    S0 = _iterate(p, interp, BASE)
+    for var in SAME:
+        S = _iterate(p, interp, {**BASE, **var})
+        assert np.array_equal(S, S0), (name, var, float(np.max(np.abs(S - S0) / np.abs(S0))))
+    for var in CLOSE:
+        S = _iterate(p, interp, {**BASE, **var})
+        assert np.max(np.abs(S - S0) / np.abs(S0)) < 2e-6, (name, var)
+    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"], interp=interp)
+    S_o, _, _ = o.solve(p["chi"], p["eps"], p["B"], tol=0.0, max_iter=STEPS, ng=False)
+    assert np.max(np.abs(S0 - S_o) / np.abs(S_o)) < 1e-5
+
+
+def test_tune_rejects_bad_values():
+    p, interp = _problems()["sph17"]
+    g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=rt.RT_MIXED)
+    for knob, bad in ((T.RT_TUNE_MARCH_CHUNK, 32), (T.RT_TUNE_MARCH_COARSEN, 3), (T.RT_TUNE_MARCH_STAGES, 1),
+                      (T.RT_TUNE_MARCH_STAGES, 5), (T.RT_TUNE_MARCH_BULK, 2), (T.RT_TUNE_SCATTER, -1),
+                      (T.RT_TUNE_OVERLAP, 7), (T.RT_TUNE_STREAMED_WEIGHTS, 3), (99, 1)):
+        with pytest.raises(rt.RtError) as ei:
+            g.tune(knob, bad)
+        assert ei.value.code == rt.RT_EINVAL
+    g.close()

@@ -165,6 +165,21 @@ def test_mixed_precision_solve_reaches_fp64_solution():
     g.close()
 
 
+def test_mixed_precision_solve_at_eps_1e8():
+    """eps = 1e-8 (the smallest destruction probability the mixed path must handle):
+    the FP32 corrections alone would leave the fixed point about (1 - rho)^-1 FP32
+    roundings away; the FP64 residual of the refinement brings it to the FP64 one."""
+    p = I.make_problem("sph17", eps=1e-8, tau=4.0)
+    o, g = pair(p, precision=rt.RT_MIXED, refine_every=16)
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    it, ok = g.solve(1e-10, 20000)
+    assert ok, g.history()[-5:]
+    S_o, it_o, _ = o.solve(p["chi"], p["eps"], p["B"], tol=1e-13, max_iter=20000)
+    assert it_o > 0
+    assert relerr(g.S(), S_o) < TOL32
+    g.close()
+
+
 def test_lambda_iteration_mode():
     p = GEOMS["sph_core"]()
     o, g = pair(p, use_lstar=False, ng=False)
