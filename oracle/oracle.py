@@ -68,6 +68,10 @@ def _lib():
         L.orc_ng.argtypes = [ctypes.c_int, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p]
         L.orc_solve.argtypes = [ctypes.c_void_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, ctypes.c_double,
                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_dbl_p]
+        L.orc_nn_lstar.argtypes = [ctypes.c_void_p, _c_dbl_p, _c_dbl_p]
+        L.orc_nn_ali_update.restype = ctypes.c_double
+        L.orc_nn_ali_update.argtypes = [ctypes.c_void_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p,
+                                        ctypes.c_double, ctypes.c_int, _c_int_p]
         L.orc_pz_intensity.restype = ctypes.c_double
         L.orc_pz_intensity.argtypes = [ctypes.c_int, _c_dbl_p, _c_dbl_p, _c_dbl_p, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -180,6 +184,27 @@ class OracleGrid:
                                    Ie.ctypes.data_as(_c_dbl_p))
         return Ib, Lb, Ie, miss
 
+    def nn_lstar(self, chi):
+        """Nearest-neighbour Lambda* (nvox, 27): column q is dJ_v/dS_u for the voxel u at offset
+        (q // 9 - 1, (q // 3) % 3 - 1, q % 3 - 1) of v in (i, j, k), phi periodic (see orc_nn_lstar)."""
+        c, pc = _d(chi)
+        out = np.empty((self.nvox, 27))
+        rc = _lib().orc_nn_lstar(self._h, pc, out.ctypes.data_as(_c_dbl_p))
+        if rc < 0:
+            raise RuntimeError("orc_nn_lstar failed (%d)" % rc)
+        return out
+
+    def nn_ali_update(self, S, J, L27, eps, B, jtol=1e-14, jmax=100000):
+        """One NN-Lambda* operator-splitting update; returns (S_new, max rel dS, Jacobi sweeps)."""
+        S, pS = _d(np.array(S, dtype=np.float64, copy=True))
+        J, pJ = _d(J)
+        L, pL = _d(L27)
+        e, pe = _d(eps)
+        Bb, pB = _d(B)
+        sw = ctypes.c_int()
+        rel = _lib().orc_nn_ali_update(self._h, pS, pJ, pL, pe, pB, float(jtol), int(jmax), ctypes.byref(sw))
+        return S, rel, sw.value
+
     def formal_solution(self, S, chi, B, homog=False):
         """(J, Lambda*, F[nvox,3] in the local basis, n missing (voxel, angle) pairs)."""
         S, pS = _d(S)
@@ -194,13 +219,16 @@ class OracleGrid:
         return J, L, F, miss
 
     def solve(self, chi, eps, B, tol=1e-8, max_iter=500, use_lstar=True, ng=True, S0=None):
-        """ALI (+Ng) to max rel dS < tol from S0 (default B); returns (S, iterations, history)."""
+        """ALI (+Ng) to max rel dS < tol from S0 (default B); returns (S, iterations, history).
+
+        use_lstar: False/0 Lambda iteration, True/1 diagonal Lambda*, 2 nearest-neighbour Lambda*."""
         c, pc = _d(chi)
         e, pe = _d(eps)
         Bb, pB = _d(B)
         S, pS = _d(np.array(B if S0 is None else S0, dtype=np.float64, copy=True))
         hist = np.zeros(max_iter)
-        it = _lib().orc_solve(self._h, pS, pc, pe, pB, float(tol), int(max_iter), 1 if use_lstar else 0,
+        mode = int(use_lstar) if not isinstance(use_lstar, bool) else (1 if use_lstar else 0)
+        it = _lib().orc_solve(self._h, pS, pc, pe, pB, float(tol), int(max_iter), mode,
                               1 if ng else 0, hist.ctypes.data_as(_c_dbl_p))
         n = abs(it)
         return S, it, hist[:n]

@@ -766,11 +766,179 @@ int orc_ng(int nvox, const double *y0, const double *y1, const double *y2, const
     return 1;
 }
 
+/* ------------------------------------------- nearest-neighbour Lambda* -- */
+
+/* Slot of voxel u in the 3x3x3 index neighbourhood of voxel v:
+ * (di+1)*9 + (dj+1)*3 + (dk+1) for the offset (di, dj, dk) in {-1,0,1}^3 that
+ * reaches u, the phi index (axis 3 spherical, axis 2 cylindrical) taken modulo
+ * n_phi; -1 when u is not a neighbour.  Needs n_phi >= 3 (one offset per
+ * neighbour); slot 13 is v itself. */
+static int nn_slot(const orc_grid *g, int v, int u)
+{
+    int i, j, k, a, b, c;
+    vox_ijk(g, v, &i, &j, &k);
+    vox_ijk(g, u, &a, &b, &c);
+    int d[3] = {a - i, b - j, c - k};
+    int per = (g->coord == ORC_SPH) ? 2 : 1, nper = (g->coord == ORC_SPH) ? g->n3 : g->n2;
+    if (d[per] == nper - 1) d[per] = -1;
+    else if (d[per] == 1 - nper) d[per] = 1;
+    for (int q = 0; q < 3; ++q)
+        if (d[q] < -1 || d[q] > 1) return -1;
+    return (d[0] + 1) * 9 + (d[1] + 1) * 3 + (d[2] + 1);
+}
+
+/* Voxel in slot q of v's neighbourhood, or -1 outside the grid. */
+static int nn_voxel(const orc_grid *g, int v, int q)
+{
+    int i, j, k;
+    vox_ijk(g, v, &i, &j, &k);
+    i += q / 9 - 1;
+    j += (q / 3) % 3 - 1;
+    k += q % 3 - 1;
+    if (g->coord == ORC_SPH) k = (k + g->n3) % g->n3;
+    else j = (j + g->n2) % g->n2;
+    if (i < 0 || i >= g->n1 || j < 0 || j >= g->n2 || k < 0 || k >= g->n3) return -1;
+    return vox_id(g, i, j, k);
+}
+
+/* Nearest-neighbour approximate Lambda operator, built exactly (Sect. 2: 3^3
+ * neighbour voxels, Paper I): L27[27 v + q] = dJ_v / dS_u for the voxel u in
+ * slot q of v's neighbourhood.  J_v = sum_w wt_w sum_{visits s of v} (l_s /
+ * L_wv) I_s and I_s = sum over the segments j <= s of its characteristic of
+ * (alpha_j S_prev(j) + beta_j S_{v_j} + gamma_j S_{v_{j+1}}) times the
+ * attenuation exp(-(tau_{j+1} + ... + tau_s)), where prev(j) is the previous
+ * node's voxel, or v_j at the start of a run; every upstream segment is
+ * visited for every s (brute force).  Returns 0, or < 0 on a geometry error
+ * (-2: n_phi < 3). */
+int orc_nn_lstar(orc_grid *g, const double *chi, double *L27)
+{
+    const int nvox = g->nvox;
+    if ((g->coord == ORC_SPH ? g->n3 : g->n2) < 3) return -2;
+    double *acc = (double *)calloc(27 * (size_t)nvox, sizeof(double));
+    double *sl = (double *)calloc(nvox, sizeof(double));
+    for (size_t q = 0; q < 27 * (size_t)nvox; ++q) L27[q] = 0.0;
+    int rc = 0;
+    for (int w = 0; w < g->n_ang && rc == 0; ++w) {
+        rc = orc_angle_geometry(g, w);
+        if (rc < 0) break;
+        angle_t *A = &g->ang[w];
+        memset(acc, 0, sizeof(double) * 27 * (size_t)nvox);
+        memset(sl, 0, sizeof(double) * nvox);
+        int nmax = 0;
+        for (int r = 0; r < A->n_rays; ++r)
+            if (A->ray_off[r + 1] - A->ray_off[r] > nmax) nmax = A->ray_off[r + 1] - A->ray_off[r];
+        double *E = (double *)malloc(sizeof(double) * (nmax + 1));
+        double *al = (double *)malloc(sizeof(double) * (nmax + 1));
+        double *be = (double *)malloc(sizeof(double) * (nmax + 1));
+        double *ga = (double *)malloc(sizeof(double) * (nmax + 1));
+        int *vm = (int *)malloc(sizeof(int) * (nmax + 1));
+        int *vp = (int *)malloc(sizeof(int) * (nmax + 1));
+        for (int r = 0; r < A->n_rays; ++r) {
+            const int s0 = A->ray_off[r], s1 = A->ray_off[r + 1];
+            int run_start = s0;
+            for (int s = s0; s < s1; ++s) { /* weights of every segment of the characteristic */
+                if (s > s0 && A->restart[s]) run_start = s;
+                const int last = (s + 1 == s1) || A->restart[s + 1];
+                const int v = A->vox[s];
+                const double dm = chi[v] * A->len[s];
+                const double dp = last ? 0.0 : chi[A->vox[s + 1]] * A->len[s + 1];
+                double a, b, c;
+                if (!last && use_parabola(g, dm, dp)) {
+                    orc_coeffs(dm, dp, 1, &a, &b, &c);
+                    vp[s - s0] = A->vox[s + 1];
+                } else {
+                    orc_coeffs(dm, 0.0, 0, &a, &b, &c);
+                    vp[s - s0] = -1;
+                }
+                E[s - s0] = exp(-dm);
+                al[s - s0] = a;
+                be[s - s0] = b;
+                ga[s - s0] = c;
+                vm[s - s0] = (s == run_start) ? v : A->vox[s - 1];
+            }
+            for (int s = s0; s < s1; ++s) {
+                const int v = A->vox[s];
+                double *row = acc + 27 * (size_t)v;
+                double P = A->len[s]; /* l_s times the attenuation from segment j to s */
+                for (int j = s; j >= s0; --j) {
+                    const int jj = j - s0;
+                    int q = nn_slot(g, v, A->vox[j]);
+                    if (q >= 0) row[q] += P * be[jj];
+                    q = nn_slot(g, v, vm[jj]);
+                    if (q >= 0) row[q] += P * al[jj];
+                    if (vp[jj] >= 0) {
+                        q = nn_slot(g, v, vp[jj]);
+                        if (q >= 0) row[q] += P * ga[jj];
+                    }
+                    P *= E[jj];
+                }
+                sl[v] += A->len[s];
+            }
+        }
+        free(E); free(al); free(be); free(ga); free(vm); free(vp);
+        const double wt = g->wt[w];
+        for (int v = 0; v < nvox; ++v)
+            if (sl[v] > 0.0)
+                for (int q = 0; q < 27; ++q) L27[27 * (size_t)v + q] += wt * acc[27 * (size_t)v + q] / sl[v];
+    }
+    free(acc);
+    free(sl);
+    return rc < 0 ? rc : 0;
+}
+
+/* Operator-splitting update with the nearest-neighbour Lambda*: the change dS
+ * solves (I - (1-eps) L*) dS = (1-eps) J + eps B - S with L* restricted to the
+ * 27-voxel neighbourhoods; Jacobi sweeps
+ *   dS_v <- [r_v + (1-eps_v) sum_{u != v} L*_vu dS_u] / (1 - (1-eps_v) L*_vv)
+ * from dS = 0 until max |sweep change| <= jtol max |dS| (at most jmax sweeps;
+ * *sweeps receives the count).  S <- S + dS; returns max |dS| / |S_new|. */
+double orc_nn_ali_update(const orc_grid *g, double *S, const double *J, const double *L27, const double *eps,
+                         const double *B, double jtol, int jmax, int *sweeps)
+{
+    const int nvox = g->nvox;
+    double *r = (double *)malloc(sizeof(double) * nvox);
+    double *x = (double *)calloc(nvox, sizeof(double));
+    double *y = (double *)malloc(sizeof(double) * nvox);
+    for (int v = 0; v < nvox; ++v) r[v] = (1.0 - eps[v]) * J[v] + eps[v] * B[v] - S[v];
+    int m;
+    for (m = 1; m <= jmax; ++m) {
+        double dmax = 0.0, xmax = 0.0;
+        for (int v = 0; v < nvox; ++v) {
+            const double *L = L27 + 27 * (size_t)v;
+            double off = 0.0;
+            for (int q = 0; q < 27; ++q) {
+                if (q == 13) continue;
+                const int u = nn_voxel(g, v, q);
+                if (u >= 0) off += L[q] * x[u];
+            }
+            y[v] = (r[v] + (1.0 - eps[v]) * off) / (1.0 - (1.0 - eps[v]) * L[13]);
+        }
+        for (int v = 0; v < nvox; ++v) {
+            if (fabs(y[v] - x[v]) > dmax) dmax = fabs(y[v] - x[v]);
+            if (fabs(y[v]) > xmax) xmax = fabs(y[v]);
+            x[v] = y[v];
+        }
+        if (!(dmax > jtol * xmax)) break;
+    }
+    if (sweeps) *sweeps = m > jmax ? jmax : m;
+    double maxrel = 0.0;
+    for (int v = 0; v < nvox; ++v) {
+        const double Snew = S[v] + x[v];
+        const double rel = fabs(x[v]) / fabs(Snew);
+        if (rel > maxrel) maxrel = rel;
+        S[v] = Snew;
+    }
+    free(r); free(x); free(y);
+    return maxrel;
+}
+
 /* ALI iteration to max rel dS < tol (R10, R11).  S holds the start value on
- * entry (the caller passes B) and the result on exit.  ng = 1 applies Ng
- * whenever four ALI iterates have accumulated since the last extrapolation.
- * hist (optional, max_iter entries) receives max rel dS of every step.
- * Returns the number of steps taken (negative: not converged). */
+ * entry (the caller passes B) and the result on exit.  use_lstar: 0 Lambda
+ * iteration, 1 diagonal Lambda*, 2 nearest-neighbour Lambda* (built once,
+ * OS step solved by Jacobi sweeps to 1e-14).  ng = 1 applies Ng whenever four
+ * ALI iterates have accumulated since the last extrapolation.  hist
+ * (optional, max_iter entries) receives max rel dS of every step.  Returns
+ * the number of steps taken (negative: not converged). */
 int orc_solve(orc_grid *g, double *S, const double *chi, const double *eps, const double *B, double tol,
               int max_iter, int use_lstar, int ng, double *hist)
 {
@@ -778,10 +946,20 @@ int orc_solve(orc_grid *g, double *S, const double *chi, const double *eps, cons
     double *J = (double *)malloc(sizeof(double) * nvox);
     double *L = (double *)malloc(sizeof(double) * nvox);
     double *H = (double *)malloc(sizeof(double) * 4 * (size_t)nvox);
+    double *L27 = NULL;
+    if (use_lstar == 2) {
+        L27 = (double *)malloc(sizeof(double) * 27 * (size_t)nvox);
+        if (orc_nn_lstar(g, chi, L27) < 0) {
+            free(J); free(L); free(H); free(L27);
+            return -max_iter;
+        }
+    }
     int nh = 0, it, done = 0;
     for (it = 1; it <= max_iter; ++it) {
         orc_formal_solution(g, S, chi, B, 0, J, L, NULL);
-        double rel = orc_ali_update(nvox, S, J, L, eps, B, use_lstar);
+        double rel;
+        if (use_lstar == 2) rel = orc_nn_ali_update(g, S, J, L27, eps, B, 1e-14, 100000, NULL);
+        else rel = orc_ali_update(nvox, S, J, L, eps, B, use_lstar);
         if (hist) hist[it - 1] = rel;
         if (rel < tol) { done = 1; break; }
         if (ng) {
@@ -794,7 +972,7 @@ int orc_solve(orc_grid *g, double *S, const double *chi, const double *eps, cons
             }
         }
     }
-    free(J); free(L); free(H);
+    free(J); free(L); free(H); free(L27);
     return done ? it : -max_iter;
 }
 
