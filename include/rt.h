@@ -57,6 +57,12 @@ extern "C" {
 /* source-function interpolation along a characteristic */
 #define RT_PARABOLIC 0
 #define RT_LINEAR 1
+/* approximate Lambda operator of the ALI iteration (Sect. 2, 3.2.1): none
+ * (Lambda iteration), the diagonal, or the 3^3 nearest neighbours built
+ * exactly (needs n_phi >= 3) */
+#define RT_LSTAR_NONE 0
+#define RT_LSTAR_DIAG 1
+#define RT_LSTAR_NN 2
 /* memory spaces */
 #define RT_HOST 0
 #define RT_DEVICE 1
@@ -78,7 +84,8 @@ typedef struct rt_grid_desc {
     int interp;             /* RT_PARABOLIC (default) or RT_LINEAR */
     double I_outer;         /* incident intensity at the outer boundary (paper: 0) */
     int precision;          /* RT_FP64 or RT_MIXED */
-    int use_lstar;          /* 1: diagonal Lambda* ALI; 0: plain Lambda iteration */
+    int use_lstar;          /* RT_LSTAR_DIAG (1): diagonal Lambda* ALI; RT_LSTAR_NN (2): nearest-neighbour
+                               Lambda*; RT_LSTAR_NONE (0): plain Lambda iteration */
     int ng;                 /* 1: order-2 Ng acceleration every 4 ALI iterates */
     int refine_every;       /* RT_MIXED: maximum FP32 correction sweeps per FP64
                              * refinement (0 = default 16) */
@@ -197,6 +204,15 @@ int rt_solve(rt_grid *g, double tol, int max_iter, int *iters);
 int rt_get_J(const rt_grid *g, double *out, int where);
 int rt_get_S(const rt_grid *g, double *out, int where);
 int rt_get_Lstar(const rt_grid *g, double *out, int where);
+/* Nearest-neighbour Lambda* of the current chi (grid created with
+ * use_lstar = RT_LSTAR_NN; built on demand, in FP64, and reused until
+ * rt_set_opacity): out27[27 v + q] = dJ_v/dS_u for the voxel u at offset
+ * (q/9 - 1, (q/3)%3 - 1, q%3 - 1) of v in (i, j, k), the phi index periodic;
+ * 0 where that offset leaves the grid.  n_vox x 27 doubles, caller-owned.
+ * With RT_LSTAR_NN the ALI step solves (I - (1-eps) L*) dS = (1-eps) J +
+ * eps B - S by Jacobi sweeps to max |sweep change| <= 1e-14 max |dS|, and
+ * rt_get_Lstar returns the diagonal. */
+int rt_get_Lstar_nn(rt_grid *g, double *out27, int where);
 int rt_get_flux(const rt_grid *g, double *out3, int where);
 
 /* Convergence history of the last rt_solve / rt_ali_step sequence: up to max

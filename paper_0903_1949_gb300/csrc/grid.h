@@ -90,6 +90,14 @@ struct rt_grid {
     cudaStream_t st2 = nullptr;  // second stream of the overlapped gather (created on first use)
     cudaEvent_t sev[6] = {};     // fork, join, march done x2, gather done x2
     int2 *d_bnd = nullptr;    // bundle bounds of every block for bnd_chunk
+    // nearest-neighbour Lambda* (use_lstar = 2)
+    double *d_L27 = nullptr;            // 27 per voxel
+    double *d_nnx = nullptr, *d_nny = nullptr;  // Jacobi iterates (2 n) and right-hand side (n)
+    unsigned long long *d_nnmx = nullptr;
+    bool nn_ok = false;                 // d_L27 matches the current chi
+    int nn_sweeps = 0;                  // Jacobi sweeps of the last OS step
+    double nn_jtol = 1e-14;
+    int nn_jmax = 100000;
     std::vector<int64_t> h_bnd_off;
     int bnd_chunk = 0;
 };

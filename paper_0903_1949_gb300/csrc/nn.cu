@@ -1,0 +1,296 @@
+// nn.cu -- nearest-neighbour approximate Lambda operator (3^3 neighbour voxels
+// built exactly, Sect. 2 and 3.2.1) and its operator-splitting step.
+//
+// L27[27 v + q] = dJ_v / dS_u for the voxel u at offset (q/9 - 1, (q/3)%3 - 1,
+// q%3 - 1) of v in (i, j, k), the phi index periodic (axis 3 spherical, axis 2
+// cylindrical).  Along a characteristic I_s = E_s I_{s-1} + alpha_s S_prev +
+// beta_s S_{v_s} + gamma_s S_{v_{s+1}}, so the derivatives d_u = dI_s/dS_u obey
+// d_u <- E_s d_u + (the weight of S_u in segment s's increment).  One thread
+// per characteristic carries d_u for the NNW most recently touched voxels (the
+// least recently touched makes room when the window is full) and emits, per segment,
+// c_s d_u with u's neighbour slot of v_s (c_s = w_Omega l_s / L_{Omega v_s});
+// one thread per voxel sums them over its ownership list in list order.  The
+// OS step (I - (1-eps) L*) x = y is solved by Jacobi sweeps.  All FP64.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "coef.cuh"
+#include "rt_internal.h"
+
+namespace rtk {
+namespace {
+
+constexpr int NNW = RTK_NNW;
+
+struct Ijk {
+    int i, j, k;
+};
+
+__device__ __forceinline__ Ijk decode(int v, int n2, int n3)
+{
+    Ijk r;
+    r.k = v % n3;
+    r.j = (v / n3) % n2;
+    r.i = v / (n2 * n3);
+    return r;
+}
+
+// neighbour slot of b in a's 3x3x3 neighbourhood, or -1
+__device__ __forceinline__ int slot_of(const Ijk &a, const Ijk &b, int sph, int n2, int n3)
+{
+    int d0 = b.i - a.i, d1 = b.j - a.j, d2 = b.k - a.k;
+    if (sph) {
+        if (d2 == n3 - 1) d2 = -1;
+        else if (d2 == 1 - n3) d2 = 1;
+    } else {
+        if (d1 == n2 - 1) d1 = -1;
+        else if (d1 == 1 - n2) d1 = 1;
+    }
+    if (d0 < -1 || d0 > 1 || d1 < -1 || d1 > 1 || d2 < -1 || d2 > 1) return -1;
+    return (d0 + 1) * 9 + (d1 + 1) * 3 + (d2 + 1);
+}
+
+struct Window {
+    int vox[NNW];
+    Ijk ijk[NNW];
+    double d[NNW];
+    int t[NNW];  // segment count at the last touch
+};
+
+// d_u += val for voxel u at touch time now (inserted when absent; a full window
+// gives up its least recently touched entry, the one farthest back along the
+// characteristic)
+__device__ __forceinline__ void win_add(Window &W, int u, double val, int now, int n2, int n3)
+{
+    int hit = -1, empty = -1, old = 0;
+    int tmin = 0;
+#pragma unroll
+    for (int e = 0; e < NNW; ++e) {
+        if (W.vox[e] == u) hit = e;
+        if (empty < 0 && W.vox[e] < 0) empty = e;
+        if (e == 0 || W.t[e] < tmin) {
+            tmin = W.t[e];
+            old = e;
+        }
+    }
+    const int tgt = hit >= 0 ? hit : (empty >= 0 ? empty : old);
+    const Ijk c = decode(u, n2, n3);
+#pragma unroll
+    for (int e = 0; e < NNW; ++e) {
+        if (e == tgt) {
+            if (hit >= 0) {
+                W.d[e] += val;
+            } else {
+                W.vox[e] = u;
+                W.ijk[e] = c;
+                W.d[e] = val;
+            }
+            W.t[e] = now;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_nn_walk(NnWalk a)
+{
+    const int64_t r = a.r_lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= a.r_hi) return;
+    const int64_t s0 = a.ray_off[r], s1 = a.ray_off[r + 1];
+    const int ang = a.ray_angle[r];
+    const double wq = a.wt[ang];
+    const double *invLq = a.invL + (int64_t)ang * a.nvox;
+    Window W;
+#pragma unroll
+    for (int e = 0; e < NNW; ++e) {
+        W.vox[e] = -1;
+        W.d[e] = 0.0;
+        W.ijk[e] = Ijk{0, 0, 0};
+        W.t[e] = -1;
+    }
+    int now = 0;
+    int vprev = -1;
+    for (int64_t s = s0; s < s1; ++s) {
+        const uint32_t w = a.vox[s];
+        const int v = (int)(w & RTK_VOXMASK);
+        const bool para = (w & RTK_PARA) != 0u;
+        const bool run0 = (w & (RTK_RAYSTART | RTK_RESTART)) != 0u;
+        const double x = a.chi[v] * a.len64[s];
+        int vn = -1;
+        double p = 0.0;
+        if (para) {
+            vn = (int)(a.vox[s + 1] & RTK_VOXMASK);
+            p = a.chi[vn] * a.len64[s + 1];
+        }
+        double E, al, be, ga;
+        Coef64::eval(x, p, para, E, al, be, ga);
+#pragma unroll
+        for (int e = 0; e < NNW; ++e) W.d[e] *= E;
+        ++now;
+        if (run0) {
+            win_add(W, v, al + be, now, a.n2, a.n3);  // S_0 := S_1 at the start of a run
+        } else {
+            win_add(W, vprev, al, now, a.n2, a.n3);
+            win_add(W, v, be, now, a.n2, a.n3);
+        }
+        if (para) win_add(W, vn, ga, now, a.n2, a.n3);
+        const double c = wq * a.len64[s] * invLq[v];
+        const Ijk cv = decode(v, a.n2, a.n3);
+        const int64_t o = (s - a.seg_lo) * NNW;
+#pragma unroll
+        for (int e = 0; e < NNW; ++e) {
+            const int q = W.vox[e] >= 0 ? slot_of(cv, W.ijk[e], a.sph, a.n2, a.n3) : -1;
+            a.slot[o + e] = (int8_t)q;
+            a.val[o + e] = q >= 0 ? c * W.d[e] : 0.0;
+        }
+        vprev = v;
+    }
+}
+
+// L27 rows of one block: thread per voxel, entries in list order, slots in window order.
+__global__ void __launch_bounds__(128) k_nn_gather(int nvox, const int32_t *off, const int32_t *perm,
+                                                   const int8_t *slot, const double *val, double *L27, int first)
+{
+    __shared__ double acc[27][128];
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) acc[q][threadIdx.x] = 0.0;
+    if (v >= nvox) return;
+    for (int e = off[v]; e < off[v + 1]; ++e) {
+        const int64_t o = (int64_t)perm[e] * NNW;
+        for (int k = 0; k < NNW; ++k) {
+            const int q = slot[o + k];
+            if (q >= 0) acc[q][threadIdx.x] += val[o + k];
+        }
+    }
+    double *row = L27 + 27 * (int64_t)v;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) row[q] = first ? acc[q][threadIdx.x] : row[q] + acc[q][threadIdx.x];
+}
+
+__global__ void k_nn_diag(int nvox, const double *L27, double *L)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < nvox) L[v] = L27[27 * (int64_t)v + 13];
+}
+
+__device__ __forceinline__ void max_to(double x, unsigned long long *dst)
+{
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(dst, (unsigned long long)__double_as_longlong(x));
+}
+
+// One Jacobi sweep of (I - (1-eps) L*) x = y: xo = (y + (1-eps) sum_{q != 13} L*_q xi[u_q]) / (1 - (1-eps) L*_13).
+__global__ void k_nn_jacobi(int nvox, int sph, int n1, int n2, int n3, const double *L27, const double *eps,
+                            const double *y, const double *xi, double *xo, unsigned long long *mx)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    double dd = 0.0, xa = 0.0;
+    if (v < nvox) {
+        const Ijk c = decode(v, n2, n3);
+        const double *L = L27 + 27 * (int64_t)v;
+        double off = 0.0;
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            if (q == 13) continue;
+            int i = c.i + q / 9 - 1, j = c.j + (q / 3) % 3 - 1, k = c.k + q % 3 - 1;
+            if (sph) k = (k + n3) % n3;
+            else j = (j + n2) % n2;
+            if (i < 0 || i >= n1 || j < 0 || j >= n2 || k < 0 || k >= n3) continue;
+            off += L[q] * xi[(i * n2 + j) * n3 + k];
+        }
+        const double e = 1.0 - eps[v];
+        const double xn = (y[v] + e * off) / (1.0 - e * L[13]);
+        dd = fabs(xn - xi[v]);
+        xa = fabs(xn);
+        xo[v] = xn;
+    }
+    max_to(dd, mx);
+    max_to(xa, mx + 1);
+}
+
+// y = (1-eps) J + eps B - S   (ALI step, and the residual of the refinement)
+__global__ void k_nn_rhs(int n, const double *S, const double *J, const double *eps, const double *B, double *y)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) y[v] = (1.0 - eps[v]) * J[v] + eps[v] * B[v] - S[v];
+}
+
+// y = (1-eps) Jd + r - d   (correction sweep of the refinement)
+__global__ void k_nn_rhs_corr(int n, const double *d, const double *Jd, const double *r, const double *eps, double *y)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) y[v] = (1.0 - eps[v]) * Jd[v] + r[v] - d[v];
+}
+
+// target += x (when target is not NULL); maxrel of |x| / |ref + target_new| (ref may be NULL)
+__global__ void k_nn_apply(int n, double *target, const double *x, const double *ref, double *slot,
+                           unsigned long long *maxrel)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    double rel = 0.0;
+    if (v < n) {
+        const double xv = x[v];
+        double t = xv;
+        if (target) {
+            t = target[v] + xv;
+            target[v] = t;
+            if (slot) slot[v] = t;
+        }
+        const double den = (ref ? ref[v] : 0.0) + t;
+        rel = fabs(xv) / fabs(den);
+    }
+    max_to(rel, maxrel);
+}
+
+unsigned nb(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+cudaError_t nn_walk(const NnWalk &a, cudaStream_t st)
+{
+    if (a.r_hi <= a.r_lo) return cudaSuccess;
+    k_nn_walk<<<nb(a.r_hi - a.r_lo, 128), 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_gather(int nvox, const int32_t *off, const int32_t *perm, const int8_t *slot, const double *val,
+                      double *L27, int first, cudaStream_t st)
+{
+    k_nn_gather<<<nb(nvox, 128), 128, 0, st>>>(nvox, off, perm, slot, val, L27, first);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_diag(int nvox, const double *L27, double *L, cudaStream_t st)
+{
+    k_nn_diag<<<nb(nvox, 256), 256, 0, st>>>(nvox, L27, L);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_jacobi(int nvox, int sph, int n1, int n2, int n3, const double *L27, const double *eps, const double *y,
+                      const double *xi, double *xo, unsigned long long *mx, cudaStream_t st)
+{
+    k_nn_jacobi<<<nb(nvox, 256), 256, 0, st>>>(nvox, sph, n1, n2, n3, L27, eps, y, xi, xo, mx);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_rhs(int n, const double *S, const double *J, const double *eps, const double *B, double *y,
+                   cudaStream_t st)
+{
+    k_nn_rhs<<<nb(n, 256), 256, 0, st>>>(n, S, J, eps, B, y);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_rhs_corr(int n, const double *d, const double *Jd, const double *r, const double *eps, double *y,
+                        cudaStream_t st)
+{
+    k_nn_rhs_corr<<<nb(n, 256), 256, 0, st>>>(n, d, Jd, r, eps, y);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_apply(int n, double *target, const double *x, const double *ref, double *slot,
+                     unsigned long long *maxrel, cudaStream_t st)
+{
+    k_nn_apply<<<nb(n, 256), 256, 0, st>>>(n, target, x, ref, slot, maxrel);
+    return cudaGetLastError();
+}
+
+}  // namespace rtk

@@ -179,6 +179,10 @@ int check_desc(const rt_grid_desc *d)
     if (d->precision != RT_FP64 && d->precision != RT_MIXED) return fail(RT_EINVAL, "bad precision");
     if (!std::isfinite(d->I_outer) || d->I_outer < 0.0) return fail(RT_EINVAL, "I_outer must be finite and >= 0");
     if (d->angle_block < 0 || d->angle_block > MAX_BLOCK_ANGLES) return fail(RT_EINVAL, "angle_block must be in [0, 256]");
+    if (d->use_lstar != RT_LSTAR_NONE && d->use_lstar != RT_LSTAR_DIAG && d->use_lstar != RT_LSTAR_NN)
+        return fail(RT_EINVAL, "use_lstar must be RT_LSTAR_NONE, RT_LSTAR_DIAG or RT_LSTAR_NN");
+    if (d->use_lstar == RT_LSTAR_NN && (d->coord == RT_SPHERICAL ? d->n[2] : d->n[1]) < 3)
+        return fail(RT_EINVAL, "the nearest-neighbour Lambda* needs at least 3 phi cells");
     if (d->refine_every < 0) return fail(RT_EINVAL, "refine_every must be >= 0");
     return RT_OK;
 }
@@ -567,6 +571,12 @@ int alloc_fields(rt_grid *g)
     RCK(dalloc(g, &g->d_F, 3 * (size_t)n));
     RCK(dalloc(g, &g->d_cs64, n));
     RCK(dalloc(g, &g->d_cs32, n));
+    if (g->use_lstar == RT_LSTAR_NN) {
+        RCK(dalloc(g, &g->d_L27, 27 * (size_t)n));
+        RCK(dalloc(g, &g->d_nnx, 2 * (size_t)n));
+        RCK(dalloc(g, &g->d_nny, n));
+        RCK(dalloc(g, &g->d_nnmx, 2));
+    }
     RCK(dalloc(g, &g->d_B32, n));
     RCK(dalloc(g, &g->d_S32, n));
     RCK(dalloc(g, &g->d_H, 4 * (size_t)n));
@@ -939,8 +949,112 @@ int ng_maybe(rt_grid *g, double *out, const double *wref)
     return RT_OK;
 }
 
+// Nearest-neighbour Lambda* of the current chi (FP64, once per chi): per
+// angle block, a walker thread per characteristic and a per-voxel sum in list
+// order; the diagonal is copied to d_L.
+int build_nn(rt_grid *g)
+{
+    if (g->nn_ok) return RT_OK;
+    const int n = g->nvox;
+    int8_t *slot = nullptr;
+    double *val = nullptr;
+    if (cudaMalloc(&slot, (size_t)RTK_NNW * std::max<int64_t>(1, g->max_blk_seg)) != cudaSuccess ||
+        cudaMalloc(&val, sizeof(double) * RTK_NNW * std::max<int64_t>(1, g->max_blk_seg)) != cudaSuccess) {
+        cudaGetLastError();
+        if (slot) cudaFree(slot);
+        return fail(RT_ENOMEM, "NN Lambda* work arrays could not be allocated");
+    }
+    struct Free {
+        void *a, *b;
+        ~Free()
+        {
+            cudaFree(a);
+            cudaFree(b);
+        }
+    } fr{slot, val};
+    for (int b = 0; b < g->nblk; ++b) {
+        const int w0 = g->blk_w0[b], nw = g->blk_nw[b];
+        NnWalk a{};
+        a.vox = g->d_vox;
+        a.len64 = g->d_len64;
+        a.ray_off = g->d_ray_off;
+        a.ray_angle = g->d_ray_angle;
+        a.r_lo = g->h_ang_ray_off[w0];
+        a.r_hi = g->h_ang_ray_off[w0 + nw];
+        a.seg_lo = g->h_ang_seg_off[w0];
+        a.chi = g->d_chi;
+        a.wt = g->d_wt;
+        a.invL = g->d_invL;
+        a.nvox = n;
+        a.n2 = g->n2;
+        a.n3 = g->n3;
+        a.sph = g->coord == RT_SPHERICAL;
+        a.slot = slot;
+        a.val = val;
+        CK(nn_walk(a, g->st));
+        CK(nn_gather(n, g->d_csr_off + (size_t)b * (n + 1), g->d_perm + a.seg_lo, slot, val, g->d_L27, b == 0, g->st));
+        g->launches += 2;
+    }
+    CK(nn_diag(n, g->d_L27, g->d_L, g->st));
+    g->launches++;
+    RCK(sync(g));  // the work arrays are freed on return
+    g->nn_ok = true;
+    g->lstar_prec = RT_FP64;
+    return RT_OK;
+}
+
+// x = (I - (1-eps) L*_NN)^-1 y by Jacobi sweeps from x = 0 until the sweep
+// change is <= nn_jtol max |x| (checked every 4 sweeps); returns the result's
+// buffer in *x_out.
+int nn_solve(rt_grid *g, const double *y, double **x_out)
+{
+    const int n = g->nvox;
+    double *xa = g->d_nnx, *xb = g->d_nnx + n;
+    CK(cudaMemsetAsync(xa, 0, sizeof(double) * n, g->st));
+    int m = 0;
+    for (;;) {
+        CK(cudaMemsetAsync(g->d_nnmx, 0, 2 * sizeof(unsigned long long), g->st));
+        for (int q = 0; q < 4; ++q) {
+            CK(nn_jacobi(n, g->coord == RT_SPHERICAL, g->n1, g->n2, g->n3, g->d_L27, g->d_eps, y, xa, xb, g->d_nnmx,
+                         g->st));
+            std::swap(xa, xb);
+            ++m;
+        }
+        g->launches += 4;
+        unsigned long long h[2];
+        CK(cudaMemcpyAsync(g->h_pin + 4, g->d_nnmx, sizeof(h), cudaMemcpyDeviceToHost, g->st));
+        RCK(sync(g));
+        std::memcpy(h, g->h_pin + 4, sizeof(h));
+        double dmax, xmax;
+        std::memcpy(&dmax, &h[0], sizeof(double));
+        std::memcpy(&xmax, &h[1], sizeof(double));
+        if (!std::isfinite(dmax) || !std::isfinite(xmax)) return fail(RT_EDEVICE, "NN Lambda* OS step diverged");
+        if (!(dmax > g->nn_jtol * xmax)) break;
+        if (m >= g->nn_jmax) return fail(RT_ENOTCONVERGED, "NN Lambda* OS step: no convergence in %d sweeps", m);
+    }
+    g->nn_sweeps = m;
+    *x_out = xa;
+    return RT_OK;
+}
+
 int ali_step_impl(rt_grid *g, int prec, double *rel_out)
 {
+    if (g->use_lstar == RT_LSTAR_NN) {
+        RCK(build_nn(g));
+        RCK(run_fs_J(g, prec, 0, g->d_S, g->d_J));
+        CK(nn_rhs(g->nvox, g->d_S, g->d_J, g->d_eps, g->d_B, g->d_nny, g->st));
+        double *x = nullptr;
+        RCK(nn_solve(g, g->d_nny, &x));
+        CK(cudaMemsetAsync(g->d_maxrel, 0, sizeof(unsigned long long), g->st));
+        double *slot = g->ng ? ng_append_slot(g) : nullptr;
+        CK(nn_apply(g->nvox, g->d_S, x, nullptr, slot, g->d_maxrel, g->st));
+        g->launches += 2;
+        double rel = 0.0;
+        RCK(read_maxrel(g, &rel));
+        *rel_out = rel;
+        g->history.push_back(rel);
+        return RT_OK;
+    }
     RCK(fs_iteration(g, prec, g->d_S, g->d_J));
     CK(cudaMemsetAsync(g->d_maxrel, 0, sizeof(unsigned long long), g->st));
     double *slot = g->ng ? ng_append_slot(g) : nullptr;
@@ -1021,7 +1135,7 @@ int rt_grid_create(rt_grid **out, const rt_grid_desc *d)
     g->inner_bc = d->inner_bc;
     g->interp = d->interp;
     g->precision = d->precision;
-    g->use_lstar = d->use_lstar ? 1 : 0;
+    g->use_lstar = d->use_lstar;
     g->ng = d->ng ? 1 : 0;
     g->refine_every = d->refine_every > 0 ? d->refine_every : 16;
     g->I_outer = d->I_outer;
@@ -1093,6 +1207,7 @@ int rt_set_opacity(rt_grid *g, const double *chi, const double *eps, const doubl
     g->launches++;
     g->lstar_prec = -1;
     g->cw_ok = false;
+    g->nn_ok = false;
     if (where == RT_HOST) RCK(sync(g));
     reset_ng(g);
     g->history.clear();
@@ -1213,12 +1328,21 @@ int rt_solve(rt_grid *g, double tol, int max_iter, int *iters)
     }
     // mixed precision: FP64 residual, FP32 correction sweeps, FP64 update
     const int n = g->nvox;
+    if (g->use_lstar == RT_LSTAR_NN) RCK(build_nn(g));
     int total = 0;
     while (total < max_iter) {
         RCK(fs_iteration(g, RT_FP64, g->d_S, g->d_J));
         total++;
         CK(cudaMemsetAsync(g->d_maxrel, 0, sizeof(unsigned long long), g->st));
-        CK(residual(n, g->d_S, g->d_J, g->d_L, g->d_eps, g->d_B, g->use_lstar, g->d_r, g->d_maxrel, g->st));
+        if (g->use_lstar == RT_LSTAR_NN) {  // residual and its NN-preconditioned step
+            CK(nn_rhs(n, g->d_S, g->d_J, g->d_eps, g->d_B, g->d_r, g->st));
+            double *x = nullptr;
+            RCK(nn_solve(g, g->d_r, &x));
+            CK(cudaMemsetAsync(g->d_maxrel, 0, sizeof(unsigned long long), g->st));
+            CK(nn_apply(n, nullptr, x, g->d_S, nullptr, g->d_maxrel, g->st));
+        } else {
+            CK(residual(n, g->d_S, g->d_J, g->d_L, g->d_eps, g->d_B, g->use_lstar, g->d_r, g->d_maxrel, g->st));
+        }
         g->launches++;
         double rel = 0.0;
         RCK(read_maxrel(g, &rel));
@@ -1237,8 +1361,16 @@ int rt_solve(rt_grid *g, double tol, int max_iter, int *iters)
             total++;
             CK(cudaMemsetAsync(g->d_maxrel, 0, sizeof(unsigned long long), g->st));
             double *slot = g->ng ? ng_append_slot(g) : nullptr;
-            CK(ali_correction(n, g->d_delta, g->d_Jd, g->d_r, g->d_Lkeep, g->d_eps, g->d_S, g->use_lstar, slot,
-                              g->d_maxrel, g->st));
+            if (g->use_lstar == RT_LSTAR_NN) {
+                CK(nn_rhs_corr(n, g->d_delta, g->d_Jd, g->d_r, g->d_eps, g->d_nny, g->st));
+                double *x = nullptr;
+                RCK(nn_solve(g, g->d_nny, &x));
+                CK(cudaMemsetAsync(g->d_maxrel, 0, sizeof(unsigned long long), g->st));
+                CK(nn_apply(n, g->d_delta, x, g->d_S, slot, g->d_maxrel, g->st));
+            } else {
+                CK(ali_correction(n, g->d_delta, g->d_Jd, g->d_r, g->d_Lkeep, g->d_eps, g->d_S, g->use_lstar, slot,
+                                  g->d_maxrel, g->st));
+            }
             g->launches++;
             double rd = 0.0;
             RCK(read_maxrel(g, &rd));
@@ -1268,6 +1400,16 @@ int rt_get_Lstar(const rt_grid *g, double *out, int where)
 {
     if (!g) return fail(RT_EINVAL, "grid is NULL");
     return copy_out((rt_grid *)g, g->d_L, out, g->nvox, where);
+}
+
+int rt_get_Lstar_nn(rt_grid *g, double *out27, int where)
+{
+    if (!g) return fail(RT_EINVAL, "grid is NULL");
+    if (g->use_lstar != RT_LSTAR_NN) return fail(RT_EINVAL, "the grid was not created with use_lstar = RT_LSTAR_NN");
+    RCK(check_lost(g));
+    CK(cudaSetDevice(g->device));
+    RCK(build_nn(g));
+    return copy_out(g, g->d_L27, out27, 27 * (size_t)g->nvox, where);
 }
 
 int rt_get_flux(const rt_grid *g, double *out3, int where)

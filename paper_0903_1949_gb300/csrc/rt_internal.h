@@ -18,6 +18,8 @@
 #define RTK_JCHUNK 1024
 // Lists of at most this many entries are summed by one thread (J-only gathers).
 #define RTK_JSHORT 64
+// Upstream voxels whose derivative a characteristic carries while building the NN Lambda*.
+#define RTK_NNW 16
 
 #define RTK_END_EXIT 1
 #define RTK_END_CORE 2
@@ -240,6 +242,32 @@ template <typename T, typename P>
 cudaError_t march_block(const uint32_t *vox, const T *len, const int64_t *ray_off, int64_t r_lo, int64_t r_hi,
                         int64_t seg_lo, int64_t nseg, const P *chiS, const T *B, T I_outer, int homog,
                         int parabolic, P *out, int chunk, cudaStream_t st);
+
+// ---- nearest-neighbour Lambda* (nn.cu) ----
+struct NnWalk {
+    const uint32_t *vox;
+    const double *len64;
+    const int64_t *ray_off;
+    const int32_t *ray_angle;
+    int64_t r_lo, r_hi, seg_lo;  // characteristics of one angle block; segments relative to seg_lo
+    const double *chi, *wt, *invL;
+    int nvox, n2, n3, sph;
+    int8_t *slot;                // RTK_NNW per segment: neighbour slot of v_s or -1
+    double *val;                 // RTK_NNW per segment: w l / L times dI_s/dS_u
+};
+cudaError_t nn_walk(const NnWalk &a, cudaStream_t st);
+cudaError_t nn_gather(int nvox, const int32_t *off, const int32_t *perm, const int8_t *slot, const double *val,
+                      double *L27, int first, cudaStream_t st);
+cudaError_t nn_diag(int nvox, const double *L27, double *L, cudaStream_t st);
+// One Jacobi sweep of (I - (1-eps) L*) x = y; mx[0] <- max |xo - xi|, mx[1] <- max |xo| (bits of doubles)
+cudaError_t nn_jacobi(int nvox, int sph, int n1, int n2, int n3, const double *L27, const double *eps, const double *y,
+                      const double *xi, double *xo, unsigned long long *mx, cudaStream_t st);
+cudaError_t nn_rhs(int n, const double *S, const double *J, const double *eps, const double *B, double *y,
+                   cudaStream_t st);
+cudaError_t nn_rhs_corr(int n, const double *d, const double *Jd, const double *r, const double *eps, double *y,
+                        cudaStream_t st);
+cudaError_t nn_apply(int n, double *target, const double *x, const double *ref, double *slot,
+                     unsigned long long *maxrel, cudaStream_t st);
 
 // ---- ALI, Ng, refinement (ali.cu) ----
 cudaError_t pack_chiS64(int nvox, const double *chi, const double *S, double2 *cs, cudaStream_t st);

@@ -18,6 +18,7 @@ RT_SPHERICAL, RT_CYLINDRICAL = 0, 1
 RT_CORE_B, RT_TRANSPARENT = 0, 1
 RT_FP64, RT_MIXED = 0, 1
 RT_PARABOLIC, RT_LINEAR = 0, 1
+RT_LSTAR_NONE, RT_LSTAR_DIAG, RT_LSTAR_NN = 0, 1, 2
 RT_HOST, RT_DEVICE = 0, 1
 RT_TUNE_MARCH_CHUNK, RT_TUNE_STREAMED_WEIGHTS, RT_TUNE_MARCH_COARSEN, RT_TUNE_OVERLAP, RT_TUNE_SCATTER = 1, 2, 3, 4, 5
 RT_TUNE_MARCH_STAGES, RT_TUNE_MARCH_BULK = 6, 7
@@ -102,6 +103,7 @@ def load():
                               ctypes.POINTER(ctypes.c_double)],
         "rt_get_timing": [_P, ctypes.POINTER(rt_timing)],
         "rt_adjoint": [_P, _P, _P, _P, ctypes.c_double, _I, _P, _P, _P, _I, ctypes.POINTER(_I)],
+        "rt_get_Lstar_nn": [_P, _P, _I],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -148,7 +150,8 @@ def rt_grid_create(coord, edges, dirs, weights, inner_bc=RT_CORE_B, interp=RT_PA
     d.dirs = dirs.ctypes.data
     d.weights = wts.ctypes.data
     d.inner_bc, d.interp, d.I_outer = int(inner_bc), int(interp), float(I_outer)
-    d.precision, d.use_lstar, d.ng = int(precision), 1 if use_lstar else 0, 1 if ng else 0
+    lst = (1 if use_lstar else 0) if isinstance(use_lstar, bool) else int(use_lstar)
+    d.precision, d.use_lstar, d.ng = int(precision), lst, 1 if ng else 0
     d.refine_every, d.angle_block, d.device = int(refine_every), int(angle_block), int(device)
     d.stream = stream if stream else None
     h = ctypes.c_void_p()
@@ -220,6 +223,11 @@ def rt_get_S(h, n_vox, out=None):
 
 def rt_get_Lstar(h, n_vox, out=None):
     return _get(load().rt_get_Lstar, h, n_vox, out)
+
+
+def rt_get_Lstar_nn(h, n_vox, out=None):
+    f = _get(load().rt_get_Lstar_nn, h, 27 * n_vox, out)
+    return f.reshape(n_vox, 27) if isinstance(f, np.ndarray) else f
 
 
 def rt_get_flux(h, n_vox, out=None):
@@ -464,6 +472,9 @@ class Grid:
 
     def flux(self, out=None):
         return rt_get_flux(self.h, self.nvox, out)
+
+    def Lstar_nn(self, out=None):
+        return rt_get_Lstar_nn(self.h, self.nvox, out)
 
     def history(self):
         return rt_get_history(self.h)

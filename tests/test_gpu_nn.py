@@ -1,0 +1,140 @@
+"""Nearest-neighbour Lambda* on the GPU (rt_get_Lstar_nn, use_lstar =
+RT_LSTAR_NN) against the oracle's exact construction, and the ALI iteration
+with it: iterate by iterate, converged, and in mixed precision with FP64
+refinement.  At the paper's full grid size: every entry against the oracle with
+few solid angles, its rows against Lambda's row sums with all 1024, and the
+convergence gain over the diagonal operator."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_0903_1949_gb300 import build as Bd
+from paper_0903_1949_gb300 import inputs as I
+from paper_0903_1949_gb300 import rt
+from tests.helpers import tiny_problem
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "sph_core": lambda: (tiny_problem(I.SPHERICAL, (5, 4, 6), 4, 4, I.CORE_B, seed=31), rt.RT_PARABOLIC),
+    "sph_hole": lambda: (tiny_problem(I.SPHERICAL, (4, 5, 5), 4, 4, I.TRANSPARENT, seed=32), rt.RT_PARABOLIC),
+    "cyl_hole": lambda: (tiny_problem(I.CYLINDRICAL, (5, 6, 4), 4, 4, I.TRANSPARENT, seed=33), rt.RT_PARABOLIC),
+    "sph_linear": lambda: (tiny_problem(I.SPHERICAL, (5, 4, 6), 4, 4, I.CORE_B, seed=34), rt.RT_LINEAR),
+    "sph17": lambda: (dict(I.make_problem("sph17"), nvox=17 * 9 * 17), rt.RT_PARABOLIC),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    Bd.build()
+    rt.load()
+
+
+def pair(p, interp, **kw):
+    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"], interp=interp)
+    g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], interp=interp,
+                use_lstar=rt.RT_LSTAR_NN, **kw)
+    return o, g
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_nn_lstar_matches_oracle(name):
+    p, interp = CASES[name]()
+    o, g = pair(p, interp)
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    L_gpu = g.Lstar_nn()
+    L_o = o.nn_lstar(p["chi"])
+    scale = np.max(np.abs(L_o))
+    assert np.max(np.abs(L_gpu - L_o)) <= 1e-13 * scale, float(np.max(np.abs(L_gpu - L_o)) / scale)
+    assert np.array_equal(g.Lstar(), L_gpu[:, 13])  # rt_get_Lstar gives the diagonal
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["sph_core", "cyl_hole", "sph17"])
+def test_nn_ali_iterates_match_oracle(name):
+    p, interp = CASES[name]()
+    o, g = pair(p, interp, precision=rt.RT_FP64, ng=False)
+    eps = np.full(p["nvox"], 1e-3)
+    g.set_opacity(p["chi"], eps, p["B"])
+    steps = 5
+    for _ in range(steps):
+        g.ali_step()
+    S_o, _, _ = o.solve(p["chi"], eps, p["B"], tol=0.0, max_iter=steps, use_lstar=2, ng=False)
+    assert np.max(np.abs(g.S() - S_o) / np.abs(S_o)) < 1e-11
+    g.close()
+
+
+def test_nn_solve_fp64_and_mixed_reach_oracle_fixed_point():
+    p, interp = CASES["sph17"]()
+    eps = np.full(p["nvox"], 1e-4)
+    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"])
+    S_o, it_o, _ = o.solve(p["chi"], eps, p["B"], tol=1e-13, max_iter=2000, use_lstar=2, ng=True)
+    assert it_o > 0
+    for prec, tol, bar in ((rt.RT_FP64, 1e-12, 1e-10), (rt.RT_MIXED, 1e-10, 1e-5)):
+        g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=prec,
+                    use_lstar=rt.RT_LSTAR_NN, refine_every=8)
+        g.set_opacity(p["chi"], eps, p["B"])
+        it, ok = g.solve(tol, 3000)
+        assert ok, (prec, g.history()[-4:])
+        assert np.max(np.abs(g.S() - S_o) / np.abs(S_o)) < bar, prec
+        g.close()
+
+
+@pytest.fixture(scope="module")
+def sph65_nn():
+    p = I.make_problem("sph65")
+    g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=rt.RT_MIXED,
+                use_lstar=rt.RT_LSTAR_NN)
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    yield p, g
+    g.close()
+
+
+def test_full_size_grid_nn_matches_oracle_with_few_angles():
+    """The paper's 65 x 33 x 65 grid (poles, the phi seam, characteristics of ~100
+    segments) with 2 x 2 solid angles, small enough for the oracle's exact
+    construction: every entry of every row."""
+    p = I.make_problem("sph65", n_mu=2, n_phi=2)
+    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"])
+    g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], use_lstar=rt.RT_LSTAR_NN)
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    L_gpu = g.Lstar_nn()
+    g.close()
+    L_o = o.nn_lstar(p["chi"])
+    scale = np.max(np.abs(L_o))
+    assert np.max(np.abs(L_gpu - L_o)) <= 1e-13 * scale, float(np.max(np.abs(L_gpu - L_o)) / scale)
+
+
+def test_full_size_nn_rows_within_lambda_rows(sph65_nn):
+    p, g = sph65_nn
+    L27 = g.Lstar_nn()
+    n = p["chi"].size
+    # a row of the neighbourhood never exceeds the whole row of Lambda (J of S = 1
+    # without incoming light), and its diagonal is positive
+    g.set_S(np.ones(n))
+    g.formal_solution(rt.RT_FP64, homog=True)
+    rowsum = g.J()
+    assert np.all(L27.sum(axis=1) <= rowsum + 1e-10)
+    assert np.all(L27[:, 13] > 0)
+    # the neighbourhood carries most of the row (thick interior: nearly all of it)
+    assert np.median(L27.sum(axis=1) / rowsum) > 0.5
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+
+
+def test_full_size_nn_converges_faster_than_diagonal(sph65_nn):
+    """Sect. 3.2.1: with the non-local operator the eps = 1e-4 case converges in
+    tens of iterations; the diagonal one is still far from it after as many."""
+    p, g = sph65_nn
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    tol = 1e-5
+    k = 0
+    for k in range(1, 121):
+        if g.ali_step() < tol:
+            break
+    assert k < 120, g.history()[-5:]
+    d = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=rt.RT_MIXED)
+    d.set_opacity(p["chi"], p["eps"], p["B"])
+    for _ in range(k):
+        rel_dg = d.ali_step()
+    d.close()
+    assert rel_dg > 30 * tol, (k, rel_dg)
