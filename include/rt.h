@@ -169,6 +169,11 @@ int rt_set_precision(rt_grid *g, int precision);
  * rt_ali_step / rt_solve return RT_ETIMEOUT. */
 #define RT_TUNE_MARCH_STAGES 6
 #define RT_TUNE_MARCH_BULK 7
+/* RT_TUNE_NN_JTOL: the OS step of the nearest-neighbour Lambda* stops its
+ * Jacobi sweeps when a sweep changes dS by at most 10^-value max |dS|,
+ * value 1..15 (default 14: the step solved to FP64 rounding).  A looser step
+ * changes the iterates, not the fixed point. */
+#define RT_TUNE_NN_JTOL 8
 int rt_tune(rt_grid *g, int knob, int value);
 
 /* Formal solution from the current S with the grid's precision: J, the

@@ -1250,6 +1250,11 @@ int rt_tune(rt_grid *g, int knob, int value)
         g->sw_bulk = value;
         return RT_OK;
     }
+    if (knob == RT_TUNE_NN_JTOL) {
+        if (value < 1 || value > 15) return fail(RT_EINVAL, "NN Jacobi tolerance exponent must be in [1, 15]");
+        g->nn_jtol = std::pow(10.0, -value);
+        return RT_OK;
+    }
     if (knob == RT_TUNE_SCATTER) {
         if (value != 0 && value != 1) return fail(RT_EINVAL, "scatter: 0 or 1");
         g->sw_scatter = value;

@@ -138,3 +138,26 @@ def test_full_size_nn_converges_faster_than_diagonal(sph65_nn):
         rel_dg = d.ali_step()
     d.close()
     assert rel_dg > 30 * tol, (k, rel_dg)
+
+
+def test_inexact_os_step_keeps_the_fixed_point():
+    p, interp = CASES["sph17"]()
+    eps = np.full(p["nvox"], 1e-4)
+    out = []
+    for jexp in (14, 4):
+        g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=rt.RT_FP64,
+                    use_lstar=rt.RT_LSTAR_NN)
+        g.tune(rt.RT_TUNE_NN_JTOL, jexp)
+        g.set_opacity(p["chi"], eps, p["B"])
+        it, ok = g.solve(1e-12, 3000)
+        assert ok, (jexp, g.history()[-3:])
+        out.append(g.S())
+        g.close()
+    assert np.max(np.abs(out[1] - out[0]) / np.abs(out[0])) < 1e-10
+    with pytest.raises(rt.RtError):
+        g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"],
+                    use_lstar=rt.RT_LSTAR_NN)
+        try:
+            g.tune(rt.RT_TUNE_NN_JTOL, 16)
+        finally:
+            g.close()
