@@ -1004,8 +1004,8 @@ int build_nn(rt_grid *g)
 }
 
 // x = (I - (1-eps) L*_NN)^-1 y by Jacobi sweeps from x = 0 until the sweep
-// change is <= nn_jtol max |x| (checked every 4 sweeps); returns the result's
-// buffer in *x_out.
+// change is <= nn_jtol max |x| (checked after 4 sweeps, then every 16; the max
+// covers the sweeps since the last check); returns the result's buffer in *x_out.
 int nn_solve(rt_grid *g, const double *y, double **x_out)
 {
     const int n = g->nvox;
@@ -1014,13 +1014,15 @@ int nn_solve(rt_grid *g, const double *y, double **x_out)
     int m = 0;
     for (;;) {
         CK(cudaMemsetAsync(g->d_nnmx, 0, 2 * sizeof(unsigned long long), g->st));
-        for (int q = 0; q < 4; ++q) {
+        // sweeps between convergence checks: few at first, then more (each check syncs the host)
+        const int batch = m < 16 ? 4 : 16;
+        for (int q = 0; q < batch; ++q) {
             CK(nn_jacobi(n, g->coord == RT_SPHERICAL, g->n1, g->n2, g->n3, g->d_L27, g->d_eps, y, xa, xb, g->d_nnmx,
                          g->st));
             std::swap(xa, xb);
             ++m;
         }
-        g->launches += 4;
+        g->launches += batch;
         unsigned long long h[2];
         CK(cudaMemcpyAsync(g->h_pin + 4, g->d_nnmx, sizeof(h), cudaMemcpyDeviceToHost, g->st));
         RCK(sync(g));
