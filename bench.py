@@ -304,7 +304,7 @@ def main():
     launches_per_step = launches_timed / args.steps
     info = g.info()  # device memory now includes the streamed-weight arrays
 
-    # ---- FP64 path, same step ----
+    # ---- FP64 path, same step: streamed FP64 weights, and the march that evaluates them ----
     g.set_precision(rt.RT_FP64)
     g.set_S(p["B"])
     for _ in range(max(1, args.warmup // 3)):
@@ -312,6 +312,12 @@ def main():
     k64 = max(2, args.steps // 4)
     ms64 = timed(g.ali_step, k64)
     value64 = world * units / (ms64 / 1e3)
+    g.tune(rt.RT_TUNE_STREAMED_WEIGHTS, 0)
+    g.set_S(p["B"])
+    g.ali_step()
+    ms64p = timed(g.ali_step, 2)
+    g.tune(rt.RT_TUNE_STREAMED_WEIGHTS, 1)
+    value64p = world * units / (ms64p / 1e3)
 
     # ---- end to end through the C ABI with pinned host buffers ----
     g.set_precision(rt.RT_MIXED)
@@ -370,7 +376,11 @@ def main():
                        "parallelism": "replicas" if world > 1 else "1 GPU",
                        "geometry_ms": info["geometry_ms"], "device_gb": info["device_bytes"] / 1e9},
             "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "steps": k64,
-                     "mixed_over_fp64": value / value64},
+                     "mixed_over_fp64": value / value64,
+                     "path": "FP64 march with FP64 weights streamed per chi (48 B per segment), FP64 gather",
+                     "plain": {"value": value64p, "ms_per_step": ms64p, "steps": 2,
+                               "mixed_over_fp64_plain": value / value64p,
+                               "path": "FP64 march evaluating its weights per segment (FP64-ALU bound)"}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_march_sw<2> (FP32 streamed-weight ray march, J only)",

@@ -142,11 +142,12 @@ int rt_set_precision(rt_grid *g, int precision);
  * warp bundle in the ray march, 64..16384 (default 512); a bundle always holds
  * whole characteristics, so results do not depend on it beyond rounding. */
 #define RT_TUNE_MARCH_CHUNK 1
-/* RT_TUNE_STREAMED_WEIGHTS (default 1): the FP32 J-only march of the ALI
- * iteration streams per-segment weights (E, alpha, beta, gamma) evaluated once
- * per chi in FP64 and the gather weight w l / L (20 extra bytes per segment of
- * device memory, allocated at the first use); 0, or when that memory is not
- * available: the march evaluates the weights itself from chi and l.
+/* RT_TUNE_STREAMED_WEIGHTS (default 1): the J-only march of the ALI iteration
+ * streams per-segment weights (E, alpha, beta, gamma) evaluated once per chi
+ * in FP64 and the gather weight w l / L: as FP32 for RT_MIXED (20 extra bytes
+ * per segment of device memory), as FP64 for RT_FP64 (40 bytes), each
+ * allocated at its first use; 0, or when that memory is not available: the
+ * march evaluates the weights itself from chi and l.
  * RT_TUNE_MARCH_COARSEN: segments per lane of the streamed-weight march, 1, 2
  * (default) or 4.  RT_TUNE_OVERLAP (default 1): the J gather of angle block b
  * runs on a second stream of the library while block b + 1 is marched (the

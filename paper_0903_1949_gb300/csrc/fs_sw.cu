@@ -1,5 +1,6 @@
-// fs_sw.cu -- FP32 J-only formal solution of the ALI iteration with streamed
-// segment weights (the hot loop of the mixed-precision path).
+// fs_sw.cu -- J-only formal solution of the ALI iteration with streamed
+// segment weights (the hot loop of the mixed-precision path, FP32; the same
+// march in FP64 for the FP64 path).
 //
 // The weights of a segment in the recurrence I_k = I_{k-1} E_k + alpha_k
 // S_{k-1} + beta_k S_k + gamma_k S_{k+1} (scheme R6 of Papers I-II, Sect. 2)
@@ -51,6 +52,23 @@ struct Kahan {
     }
 };
 
+// Plain FP64 accumulation for the FP64 gathers (same interface as Kahan).
+struct Sum64 {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ void warp_reduce()
+    {
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+};
+template <typename T> struct AccOf;
+template <> struct AccOf<float> { using type = Kahan; };
+template <> struct AccOf<double> { using type = Sum64; };
+template <typename T> __device__ __forceinline__ const T *gbuf(const SwGather &t);
+template <> __device__ __forceinline__ const float *gbuf<float>(const SwGather &t) { return t.buf; }
+template <> __device__ __forceinline__ const double *gbuf<double>(const SwGather &t) { return t.buf64; }
+
 __device__ __forceinline__ int64_t lb64(const int64_t *a, int64_t lo, int64_t hi, int64_t key)
 {
     while (lo < hi) {
@@ -78,9 +96,19 @@ __global__ void k_bundles(const int64_t *ray_off, int64_t r_lo, int64_t r_hi, in
 // One warp marches bundle wg: K consecutive segments per lane, the lane maps
 // I -> A I + b composed by an inclusive shuffle scan over the warp; the next
 // tile's words and weights are fetched before the current one is processed.
-template <int K>
-__device__ __forceinline__ void march_sw(const SwMarch &m, int64_t wg)
+__device__ __forceinline__ float4 ldw(const float4 *p) { return __ldcs(p); }
+__device__ __forceinline__ Wd4 ldw(const Wd4 *p)
 {
+    const double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+    return Wd4{a.x, a.y, b.x, b.y};
+}
+
+template <typename M, int K>
+__device__ __forceinline__ void march_sw(const M &m, int64_t wg)
+{
+    using T = typename M::T;
+    using W = typename M::W;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     if (wg >= m.nbundles) return;
@@ -88,103 +116,103 @@ __device__ __forceinline__ void march_sw(const SwMarch &m, int64_t wg)
     const int s_begin = be.x, s_end = be.y;
     if (s_begin >= s_end) return;
     const uint32_t *vx = m.vox + m.seg_lo;
-    const float4 *cf = m.cw + m.seg_lo;
-    const float *gw = m.cg + m.seg_lo;
-    float *o = m.out;
-    float Icarry = 0.f, Sprev = 0.f;
+    const W *cf = m.cw + m.seg_lo;
+    const T *gw = m.cg + m.seg_lo;
+    T *o = m.out;
+    T Icarry = 0, Sprev = 0;
     const int32_t *ps = m.pos ? m.pos + m.seg_lo : nullptr;
     uint32_t w[K];
-    float4 c[K];
-    float g[K];
+    W c[K];
+    T g[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         const int s = s_begin + K * lane + j;
         const bool ok = s < s_end;
         w[j] = ok ? __ldcs(vx + s) : 0u;
-        c[j] = ok ? __ldcs(cf + s) : make_float4(1.f, 0.f, 0.f, 0.f);
-        g[j] = ok ? __ldcs(gw + s) : 0.f;
+        c[j] = ok ? ldw(cf + s) : W{1, 0, 0, 0};
+        g[j] = ok ? __ldcs(gw + s) : T(0);
     }
     // The last segment of a tile may use S of the next tile's first segment
     // (gamma); its value is completed and stored at the start of the next tile,
     // so no tile waits for the loads of the one after it.
-    float pend_I = 0.f, pend_gam = 0.f, pend_g = 0.f;
+    T pend_I = 0, pend_gam = 0, pend_g = 0;
     int pend_o = 0;
     bool pend = false;  // warp-uniform
     for (int base = s_begin; base < s_end; base += 32 * K) {
         const int s0 = base + K * lane;
         uint32_t wN[K];
-        float4 cN[K];
-        float gN[K];
+        W cN[K];
+        T gN[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             const int s = base + 32 * K + K * lane + j;
             const bool ok = s < s_end;
             wN[j] = ok ? __ldcs(vx + s) : 0u;
-            cN[j] = ok ? __ldcs(cf + s) : make_float4(1.f, 0.f, 0.f, 0.f);
-            gN[j] = ok ? __ldcs(gw + s) : 0.f;
+            cN[j] = ok ? ldw(cf + s) : W{1, 0, 0, 0};
+            gN[j] = ok ? __ldcs(gw + s) : T(0);
         }
         int pN[K];  // output positions of this tile (voxel order) when scattering
 #pragma unroll
         for (int j = 0; j < K; ++j) pN[j] = (ps && s0 + j < s_end) ? __ldcs(ps + s0 + j) : 0;
-        float S[K];
+        T S[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) S[j] = (s0 + j < s_end) ? m.S32[w[j] & RTK_VOXMASK] : 0.f;
+        for (int j = 0; j < K; ++j) S[j] = (s0 + j < s_end) ? m.S[w[j] & RTK_VOXMASK] : T(0);
         if (pend) {  // complete the previous tile's last segment
-            const float Sf = __shfl_sync(FULL, S[0], 0);
+            const T Sf = __shfl_sync(FULL, S[0], 0);
             if (lane == 31) {
-                pend_I = fmaf(pend_gam * pend_g, Sf, pend_I);
+                pend_I = fma(pend_gam * pend_g, Sf, pend_I);
                 __stcg(o + pend_o, pend_I);
             }
-            Icarry = fmaf(pend_gam, Sf, Icarry);
+            Icarry = fma(pend_gam, Sf, Icarry);
         }
-        float Snx = __shfl_down_sync(FULL, S[0], 1);  // S after this lane's last segment
-        if (lane == 31) Snx = 0.f;                    // next tile: added when it is loaded
-        float Sp = __shfl_up_sync(FULL, S[K - 1], 1); // S before this lane's first segment
+        T Snx = __shfl_down_sync(FULL, S[0], 1);  // S after this lane's last segment
+        if (lane == 31) Snx = 0;                    // next tile: added when it is loaded
+        T Sp = __shfl_up_sync(FULL, S[K - 1], 1); // S before this lane's first segment
         if (lane == 0) Sp = Sprev;
-        float A[K], b[K];
+        T A[K], b[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            const float Sm = (j == 0) ? Sp : S[j - 1];
-            const float Sn = (j + 1 < K) ? S[j + 1] : Snx;
-            const float src = fmaf(c[j].y, Sm, fmaf(c[j].z, S[j], c[j].w * Sn));
+            const T Sm = (j == 0) ? Sp : S[j - 1];
+            const T Sn = (j + 1 < K) ? S[j + 1] : Snx;
+            const T src = fma(c[j].y, Sm, fma(c[j].z, S[j], c[j].w * Sn));
             A[j] = c[j].x;
             b[j] = src;
             if (w[j] & RTK_RAYSTART) {
-                const float Iin = m.homog ? 0.f : ((w[j] & RTK_CORE) ? m.B32[w[j] & RTK_VOXMASK] : m.I_outer);
-                b[j] = fmaf(c[j].x, Iin, src);
-                A[j] = 0.f;
+                const T Iin = m.homog ? T(0) : ((w[j] & RTK_CORE) ? m.B[w[j] & RTK_VOXMASK] : m.I_outer);
+                b[j] = fma(c[j].x, Iin, src);
+                A[j] = 0;
             }
             if (s0 + j >= s_end) {
-                A[j] = 1.f;
-                b[j] = 0.f;
+                A[j] = 1;
+                b[j] = 0;
             }
         }
-        float LA = A[0], LB = b[0];
+        T LA = A[0], LB = b[0];
 #pragma unroll
         for (int j = 1; j < K; ++j) {
-            LB = fmaf(A[j], LB, b[j]);
+            LB = fma(A[j], LB, b[j]);
             LA = A[j] * LA;
         }
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const float Ao = __shfl_up_sync(FULL, LA, off);
-            const float bo = __shfl_up_sync(FULL, LB, off);
+            const T Ao = __shfl_up_sync(FULL, LA, off);
+            const T bo = __shfl_up_sync(FULL, LB, off);
             if (lane >= off) {
-                LB = fmaf(LA, bo, LB);
+                LB = fma(LA, bo, LB);
                 LA = LA * Ao;
             }
         }
-        float PA = __shfl_up_sync(FULL, LA, 1);
-        float PB = __shfl_up_sync(FULL, LB, 1);
+        T PA = __shfl_up_sync(FULL, LA, 1);
+        T PB = __shfl_up_sync(FULL, LB, 1);
         if (lane == 0) {
-            PA = 1.f;
-            PB = 0.f;
+            PA = 1;
+            PB = 0;
         }
         pend = base + 32 * K < s_end;
-        float I = fmaf(PA, Icarry, PB);
+        T I = fma(PA, Icarry, PB);
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            I = fmaf(A[j], I, b[j]);
+            I = fma(A[j], I, b[j]);
             const int oi = ps ? pN[j] : s0 + j;
             if (j == K - 1 && lane == 31 && pend) {
                 pend_I = g[j] * I;
@@ -389,7 +417,7 @@ __device__ __forceinline__ void march_tma(const SwMarch &m, int64_t wg, SwStage<
         }
         float S[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) S[j] = (s0 + j < s_end) ? m.S32[w[j] & RTK_VOXMASK] : 0.f;
+        for (int j = 0; j < K; ++j) S[j] = (s0 + j < s_end) ? m.S[w[j] & RTK_VOXMASK] : 0.f;
         if (pend) {
             const float Sf = __shfl_sync(FULL, S[0], 0);
             if (lane == 31) {
@@ -411,7 +439,7 @@ __device__ __forceinline__ void march_tma(const SwMarch &m, int64_t wg, SwStage<
             A[j] = c[j].x;
             b[j] = src;
             if (w[j] & RTK_RAYSTART) {
-                const float Iin = m.homog ? 0.f : ((w[j] & RTK_CORE) ? m.B32[w[j] & RTK_VOXMASK] : m.I_outer);
+                const float Iin = m.homog ? 0.f : ((w[j] & RTK_CORE) ? m.B[w[j] & RTK_VOXMASK] : m.I_outer);
                 b[j] = fmaf(c[j].x, Iin, src);
                 A[j] = 0.f;
             }
@@ -478,8 +506,11 @@ __global__ void __launch_bounds__(256, 5) k_march_tma(SwMarch m)
 // flight); the other warps take one RTK_JCHUNK-entry chunk of a long list each
 // (32 entries per lane, 8 in flight), and the warp that completes a voxel's
 // last chunk adds the chunk sums in chunk order.
+template <typename T>
 __global__ void __launch_bounds__(256) k_gather_sw(SwGather t)
 {
+    using Acc = typename AccOf<T>::type;
+    const T *buf = gbuf<T>(t);
     const int64_t cta = blockIdx.x;
     if (cta < t.nbs) {
         const int64_t i = cta * 256 + threadIdx.x;
@@ -487,14 +518,14 @@ __global__ void __launch_bounds__(256) k_gather_sw(SwGather t)
         const int v = t.jorder[i];
         const int L = t.off[v + 1] - t.off[v];
         const int32_t *lst = t.jsell + t.jgbase[i >> 5] + (i & 31);
-        Kahan acc;
+        Acc acc;
         for (int k = 0; k < L; k += 8) {
             int ss[8];
-            float val[8];
+            T val[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) ss[j] = (k + j < L) ? __ldcs(lst + 32 * (k + j)) : -1;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) val[j] = (ss[j] >= 0) ? __ldcg(t.buf + ss[j]) : 0.f;
+            for (int j = 0; j < 8; ++j) val[j] = (ss[j] >= 0) ? __ldcg(buf + ss[j]) : T(0);
 #pragma unroll
             for (int j = 0; j < 8; ++j)
                 if (ss[j] >= 0) acc.add(val[j]);
@@ -509,14 +540,14 @@ __global__ void __launch_bounds__(256) k_gather_sw(SwGather t)
     const int v = t.crow[c];
     const int e0 = t.cbeg[c];
     const int e1 = min(e0 + CHUNK, t.off[v + 1]);
-    Kahan acc;
+    Acc acc;
     for (int k = e0 + lane; k < e1; k += 32 * 8) {
         int ss[8];
-        float val[8];
+        T val[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) ss[j] = (k + 32 * j < e1) ? __ldcs(t.perm + k + 32 * j) : -1;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) val[j] = (ss[j] >= 0) ? __ldcg(t.buf + ss[j]) : 0.f;
+        for (int j = 0; j < 8; ++j) val[j] = (ss[j] >= 0) ? __ldcg(buf + ss[j]) : T(0);
 #pragma unroll
         for (int j = 0; j < 8; ++j)
             if (ss[j] >= 0) acc.add(val[j]);
@@ -541,19 +572,22 @@ __global__ void __launch_bounds__(256) k_gather_sw(SwGather t)
 // scattered c_s I_s to the list positions): short lists thread per voxel in
 // voxel order (adjacent threads read adjacent rows), long lists one warp per
 // chunk; same summation order as k_gather_sw.
+template <typename T>
 __global__ void __launch_bounds__(256) k_gather_rows_sw(SwGather t, int nvox, int64_t nvb)
 {
+    using Acc = typename AccOf<T>::type;
+    const T *buf = gbuf<T>(t);
     const int64_t cta = blockIdx.x;
     if (cta < nvb) {
         const int v = (int)(cta * 256 + threadIdx.x);
         if (v >= nvox) return;
         const int a = t.off[v], L = t.off[v + 1] - a;
         if (L > RTK_JSHORT) return;  // long list: chunk warps
-        Kahan acc;
+        Acc acc;
         for (int k = 0; k < L; k += 8) {
-            float val[8];
+            T val[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) val[j] = (k + j < L) ? __ldcg(t.buf + a + k + j) : 0.f;
+            for (int j = 0; j < 8; ++j) val[j] = (k + j < L) ? __ldcg(buf + a + k + j) : T(0);
 #pragma unroll
             for (int j = 0; j < 8; ++j)
                 if (k + j < L) acc.add(val[j]);
@@ -568,11 +602,11 @@ __global__ void __launch_bounds__(256) k_gather_rows_sw(SwGather t, int nvox, in
     const int v = t.crow[c];
     const int e0 = t.cbeg[c];
     const int e1 = min(e0 + CHUNK, t.off[v + 1]);
-    Kahan acc;
+    Acc acc;
     for (int k = e0 + lane; k < e1; k += 32 * 8) {
-        float val[8];
+        T val[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) val[j] = (k + 32 * j < e1) ? __ldcg(t.buf + k + 32 * j) : 0.f;
+        for (int j = 0; j < 8; ++j) val[j] = (k + 32 * j < e1) ? __ldcg(buf + k + 32 * j) : T(0);
 #pragma unroll
         for (int j = 0; j < 8; ++j)
             if (k + 32 * j < e1) acc.add(val[j]);
@@ -600,10 +634,10 @@ __global__ void k_inv_perm(const int32_t *perm, int64_t n, int32_t *pos)
         pos[perm[e]] = (int32_t)e;
 }
 
-template <int K>
-__global__ void __launch_bounds__(256) k_march_sw(SwMarch m)
+template <typename M, int K>
+__global__ void __launch_bounds__(256) k_march_sw(M m)
 {
-    march_sw<K>(m, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    march_sw<M, K>(m, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
 }
 
 // FP64 weights of every segment for the current chi, rounded to FP32.
@@ -622,6 +656,40 @@ __global__ void k_coef_stream(const uint32_t *__restrict__ vox, const double *__
             al = 0.0;
         }
         cw[s] = make_float4((float)E, (float)al, (float)be, (float)ga);
+    }
+}
+
+// FP64 weights of every segment for the current chi (FP64 streamed march).
+__global__ void k_coef_stream64(const uint32_t *__restrict__ vox, const double *__restrict__ len64,
+                                const double *__restrict__ chi, int64_t nseg, Wd4 *__restrict__ cw)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nseg; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = vox[s];
+        const bool para = (w & RTK_PARA) != 0u;
+        const double x = chi[w & RTK_VOXMASK] * len64[s];
+        const double p = para ? chi[vox[s + 1] & RTK_VOXMASK] * len64[s + 1] : 0.0;
+        double E, al, be, ga;
+        Coef64::eval(x, p, para, E, al, be, ga);
+        if (w & (RTK_RAYSTART | RTK_RESTART)) {
+            be += al;
+            al = 0.0;
+        }
+        cw[s] = Wd4{E, al, be, ga};
+    }
+}
+
+__global__ void k_seg_weight64(const uint32_t *__restrict__ vox, const double *__restrict__ len64,
+                               const int64_t *__restrict__ ang_seg_off, int n_ang, const double *__restrict__ wt,
+                               const double *__restrict__ invL, int nvox, int64_t nseg, double *__restrict__ cg)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nseg; s += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_ang;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (ang_seg_off[mid] <= s) lo = mid;
+            else hi = mid;
+        }
+        cg[s] = wt[lo] * len64[s] * invL[(int64_t)lo * nvox + (vox[s] & RTK_VOXMASK)];
     }
 }
 
@@ -688,9 +756,9 @@ cudaError_t march_sw_launch(const SwMarch &m, int coarsen, cudaStream_t st)
     const int64_t grid = (m.nbundles + 7) / 8;
     if (grid <= 0) return cudaSuccess;
     if (m.stages >= 2) return m.bulk ? launch_ring_k<true>(m, coarsen, grid, st) : launch_ring_k<false>(m, coarsen, grid, st);
-    if (coarsen == 4) k_march_sw<4><<<(unsigned)grid, 256, 0, st>>>(m);
-    else if (coarsen == 1) k_march_sw<1><<<(unsigned)grid, 256, 0, st>>>(m);
-    else k_march_sw<2><<<(unsigned)grid, 256, 0, st>>>(m);
+    if (coarsen == 4) k_march_sw<SwMarch, 4><<<(unsigned)grid, 256, 0, st>>>(m);
+    else if (coarsen == 1) k_march_sw<SwMarch, 1><<<(unsigned)grid, 256, 0, st>>>(m);
+    else k_march_sw<SwMarch, 2><<<(unsigned)grid, 256, 0, st>>>(m);
     return cudaGetLastError();
 }
 
@@ -699,7 +767,8 @@ cudaError_t gather_rows_sw_launch(const SwGather &t, int nvox, cudaStream_t st)
     const int64_t nvb = (nvox + 255) / 256;
     const int64_t grid = nvb + (t.nchunks * 32 + 255) / 256;
     if (grid <= 0) return cudaSuccess;
-    k_gather_rows_sw<<<(unsigned)grid, 256, 0, st>>>(t, nvox, nvb);
+    if (t.buf64) k_gather_rows_sw<double><<<(unsigned)grid, 256, 0, st>>>(t, nvox, nvb);
+    else k_gather_rows_sw<float><<<(unsigned)grid, 256, 0, st>>>(t, nvox, nvb);
     return cudaGetLastError();
 }
 
@@ -714,7 +783,32 @@ cudaError_t gather_sw_launch(const SwGather &t, cudaStream_t st)
 {
     const int64_t grid = t.nbs + (t.nchunks * 32 + 255) / 256;
     if (grid <= 0) return cudaSuccess;
-    k_gather_sw<<<(unsigned)grid, 256, 0, st>>>(t);
+    if (t.buf64) k_gather_sw<double><<<(unsigned)grid, 256, 0, st>>>(t);
+    else k_gather_sw<float><<<(unsigned)grid, 256, 0, st>>>(t);
+    return cudaGetLastError();
+}
+
+cudaError_t march_sw64_launch(const SwMarch64 &m, cudaStream_t st)
+{
+    const int64_t grid = (m.nbundles + 7) / 8;
+    if (grid <= 0) return cudaSuccess;
+    k_march_sw<SwMarch64, 1><<<(unsigned)grid, 256, 0, st>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t coef_stream64(const uint32_t *vox, const double *len64, const double *chi, int64_t nseg, Wd4 *cw,
+                          cudaStream_t st)
+{
+    if (nseg <= 0) return cudaSuccess;
+    k_coef_stream64<<<grid_cap(nseg), 256, 0, st>>>(vox, len64, chi, nseg, cw);
+    return cudaGetLastError();
+}
+
+cudaError_t seg_weight64(const uint32_t *vox, const double *len64, const int64_t *ang_seg_off, int n_ang,
+                         const double *wt, const double *invL, int nvox, int64_t nseg, double *cg, cudaStream_t st)
+{
+    if (nseg <= 0) return cudaSuccess;
+    k_seg_weight64<<<grid_cap(nseg), 256, 0, st>>>(vox, len64, ang_seg_off, n_ang, wt, invL, nvox, nseg, cg);
     return cudaGetLastError();
 }
 

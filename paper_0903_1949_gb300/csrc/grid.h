@@ -79,6 +79,11 @@ struct rt_grid {
     float *d_cg = nullptr;    // w_Omega l / L per segment
     int sw_enabled = 1;
     int sw_state = 0;         // 0 not allocated yet, 1 allocated, -1 allocation failed
+    rtk::Wd4 *d_cw64 = nullptr;  // FP64 weights per segment (FP64 streamed march)
+    double *d_cg64 = nullptr;    // FP64 w l / L per segment
+    int sw64_state = 0;
+    bool cw64_ok = false;
+    int pos_state = 0;        // list positions: 0 not tried, 1 allocated, -1 not available
     bool cw_ok = false;       // d_cw4 matches the current chi
     int sw_coarsen = 2;       // segments per lane (RT_TUNE_MARCH_COARSEN)
     int sw_overlap = 1;       // gather of block b on st2 while block b + 1 is marched (RT_TUNE_OVERLAP)

@@ -668,6 +668,66 @@ int run_fs(rt_grid *g, int prec, int homog, const double *S_src, double *J, doub
 // computed then, from the geometry) and refresh (E, alpha, beta, gamma) after
 // chi changed.  Returns false when disabled or when the arrays do not fit; the
 // FP32 march then evaluates the weights itself.
+// Streamed-weight march, parts shared by both precisions: list positions
+// (optional; without them the gather reads through perm) and the bundle bounds
+// of the current chunk.  Returns false when they cannot be set up.
+bool sw_common(rt_grid *g)
+{
+    if (g->pos_state == 0) {
+        void *c = nullptr;
+        if (cudaMalloc(&c, sizeof(int32_t) * (size_t)(g->n_seg + 4)) == cudaSuccess) {
+            g->allocs.push_back(c);
+            g->bytes += (int64_t)(4 * g->n_seg);
+            g->d_pos = (int32_t *)c;
+            for (int b = 0; b < g->nblk; ++b) {
+                const int64_t lo = g->h_ang_seg_off[g->blk_w0[b]];
+                const int64_t ns = g->h_ang_seg_off[g->blk_w0[b] + g->blk_nw[b]] - lo;
+                if (inv_perm(g->d_perm + lo, ns, g->d_pos + lo, g->st) != cudaSuccess) return false;
+                g->launches++;
+            }
+            g->pos_state = 1;
+        } else {
+            cudaGetLastError();
+            g->pos_state = -1;
+        }
+    }
+    if (g->bnd_chunk != g->march_chunk) {  // bundle bounds for the current chunk
+        std::vector<int64_t> off(g->nblk + 1, 0);
+        for (int b = 0; b < g->nblk; ++b) {
+            const int w0 = g->blk_w0[b], nw = g->blk_nw[b];
+            const int64_t ns = g->h_ang_seg_off[w0 + nw] - g->h_ang_seg_off[w0];
+            off[b + 1] = off[b] + (ns + g->march_chunk - 1) / g->march_chunk;
+        }
+        if (g->d_bnd) {
+            cudaFree(g->d_bnd);
+            for (auto &q : g->allocs)
+                if (q == (void *)g->d_bnd) q = nullptr;
+            g->d_bnd = nullptr;
+        }
+        void *q = nullptr;
+        if (cudaMalloc(&q, sizeof(int2) * (size_t)std::max<int64_t>(1, off[g->nblk])) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        g->allocs.push_back(q);
+        g->d_bnd = (int2 *)q;
+        for (int b = 0; b < g->nblk; ++b) {
+            const int w0 = g->blk_w0[b], nw = g->blk_nw[b];
+            const int64_t lo = g->h_ang_seg_off[w0], ns = g->h_ang_seg_off[w0 + nw] - lo;
+            if (sw_bundles(g->d_ray_off, g->h_ang_ray_off[w0], g->h_ang_ray_off[w0 + nw], lo, ns, g->march_chunk,
+                           g->d_bnd + off[b], g->st) != cudaSuccess)
+                return false;
+            g->launches++;
+        }
+        g->h_bnd_off = off;
+        g->bnd_chunk = g->march_chunk;
+    }
+    return true;
+}
+
+// FP32 streamed weights: allocated on first use (w l / L computed then, from the
+// geometry), (E, alpha, beta, gamma) refreshed after chi changed.  false when
+// disabled or out of memory (the FP32 march then evaluates the weights itself).
 bool use_sw(rt_grid *g)
 {
     if (!g->sw_enabled || g->sw_state < 0) return false;
@@ -691,20 +751,6 @@ bool use_sw(rt_grid *g)
             return false;
         }
         g->launches++;
-        void *c = nullptr;  // list positions (optional: without them the gather reads through perm)
-        if (cudaMalloc(&c, sizeof(int32_t) * (size_t)(g->n_seg + 4)) == cudaSuccess) {
-            g->allocs.push_back(c);
-            g->bytes += (int64_t)(4 * g->n_seg);
-            g->d_pos = (int32_t *)c;
-            for (int b = 0; b < g->nblk; ++b) {
-                const int64_t lo = g->h_ang_seg_off[g->blk_w0[b]];
-                const int64_t ns = g->h_ang_seg_off[g->blk_w0[b] + g->blk_nw[b]] - lo;
-                if (inv_perm(g->d_perm + lo, ns, g->d_pos + lo, g->st) != cudaSuccess) return false;
-                g->launches++;
-            }
-        } else {
-            cudaGetLastError();
-        }
         g->sw_state = 1;
         g->cw_ok = false;
     }
@@ -713,39 +759,42 @@ bool use_sw(rt_grid *g)
         g->launches++;
         g->cw_ok = true;
     }
-    if (g->bnd_chunk != g->march_chunk) {  // bundle bounds for the current chunk
-        std::vector<int64_t> off(g->nblk + 1, 0);
-        for (int b = 0; b < g->nblk; ++b) {
-            const int w0 = g->blk_w0[b], nw = g->blk_nw[b];
-            const int64_t ns = g->h_ang_seg_off[w0 + nw] - g->h_ang_seg_off[w0];
-            off[b + 1] = off[b] + (ns + g->march_chunk - 1) / g->march_chunk;
-        }
-        if (g->d_bnd) {
-            cudaFree(g->d_bnd);
-            for (auto &q : g->allocs)
-                if (q == (void *)g->d_bnd) q = nullptr;
-            g->d_bnd = nullptr;
-        }
-        void *q = nullptr;
-        if (cudaMalloc(&q, sizeof(int2) * (size_t)std::max<int64_t>(1, off[g->nblk])) != cudaSuccess) {
+    return sw_common(g);
+}
+
+// FP64 streamed weights (40 bytes per segment), the same life cycle.
+bool use_sw64(rt_grid *g)
+{
+    if (!g->sw_enabled || g->sw64_state < 0) return false;
+    if (g->sw64_state == 0) {
+        void *a = nullptr, *b = nullptr;
+        if (cudaMalloc(&a, sizeof(Wd4) * (size_t)g->n_seg) != cudaSuccess ||
+            cudaMalloc(&b, sizeof(double) * (size_t)(g->n_seg + 4)) != cudaSuccess) {
             cudaGetLastError();
-            g->sw_state = -1;
+            if (a) cudaFree(a);
+            g->sw64_state = -1;
             return false;
         }
-        g->allocs.push_back(q);
-        g->d_bnd = (int2 *)q;
-        for (int b = 0; b < g->nblk; ++b) {
-            const int w0 = g->blk_w0[b], nw = g->blk_nw[b];
-            const int64_t lo = g->h_ang_seg_off[w0], ns = g->h_ang_seg_off[w0 + nw] - lo;
-            if (sw_bundles(g->d_ray_off, g->h_ang_ray_off[w0], g->h_ang_ray_off[w0 + nw], lo, ns, g->march_chunk,
-                           g->d_bnd + off[b], g->st) != cudaSuccess)
-                return false;
-            g->launches++;
+        g->allocs.push_back(a);
+        g->allocs.push_back(b);
+        g->bytes += (int64_t)(40 * g->n_seg);
+        g->d_cw64 = (Wd4 *)a;
+        g->d_cg64 = (double *)b;
+        if (seg_weight64(g->d_vox, g->d_len64, g->d_ang_seg_off, g->n_ang, g->d_wt, g->d_invL, g->nvox, g->n_seg,
+                         g->d_cg64, g->st) != cudaSuccess) {
+            g->sw64_state = -1;
+            return false;
         }
-        g->h_bnd_off = off;
-        g->bnd_chunk = g->march_chunk;
+        g->launches++;
+        g->sw64_state = 1;
+        g->cw64_ok = false;
     }
-    return true;
+    if (!g->cw64_ok) {
+        if (coef_stream64(g->d_vox, g->d_len64, g->d_chi, g->n_seg, g->d_cw64, g->st) != cudaSuccess) return false;
+        g->launches++;
+        g->cw64_ok = true;
+    }
+    return sw_common(g);
 }
 
 SwMarch sw_march(rt_grid *g, int b, int homog, float *out)
@@ -763,9 +812,28 @@ SwMarch sw_march(rt_grid *g, int b, int homog, float *out)
     m.err = g->d_err;
     m.seg_lo = g->h_ang_seg_off[w0];
     m.nbundles = g->h_bnd_off[b + 1] - g->h_bnd_off[b];
-    m.S32 = g->d_S32;
-    m.B32 = g->d_B32;
+    m.S = g->d_S32;
+    m.B = g->d_B32;
     m.I_outer = (float)g->I_outer;
+    m.homog = homog;
+    m.out = out;
+    return m;
+}
+
+SwMarch64 sw_march64(rt_grid *g, int b, int homog, double *out)
+{
+    SwMarch64 m{};
+    const int w0 = g->blk_w0[b];
+    m.vox = g->d_vox;
+    m.cw = g->d_cw64;
+    m.cg = g->d_cg64;
+    m.bnd = g->d_bnd + g->h_bnd_off[b];
+    m.pos = (g->sw_scatter && g->d_pos) ? g->d_pos : nullptr;
+    m.seg_lo = g->h_ang_seg_off[w0];
+    m.nbundles = g->h_bnd_off[b + 1] - g->h_bnd_off[b];
+    m.S = nullptr;  // set by the caller (the S of this formal solution)
+    m.B = g->d_B;
+    m.I_outer = g->I_outer;
     m.homog = homog;
     m.out = out;
     return m;
@@ -801,20 +869,38 @@ SwGather sw_gather(rt_grid *g, int b, const float *buf, double *J)
 // buffer b % 2) waits only for the gather of block b - 2, which read that
 // buffer; the gathers run in block order on the second stream, each after its
 // march, so J accumulates in the same order as without overlap.
-int run_fs_J_sw(rt_grid *g, int homog, double *J)
+int run_fs_J_sw(rt_grid *g, int prec, int homog, const double *S_src, double *J)
 {
-    float *bufs[2] = {(float *)g->d_segbuf, (float *)g->d_segbuf + g->max_blk_seg};
+    const bool f64 = prec == RT_FP64;
+    const bool scatter = g->sw_scatter && g->d_pos;
+    // double buffer of per-segment values: FP32 or FP64 (the segment buffer holds 16 bytes per segment)
+    float *b32[2] = {(float *)g->d_segbuf, (float *)g->d_segbuf + g->max_blk_seg};
+    double *b64[2] = {(double *)g->d_segbuf, (double *)g->d_segbuf + g->max_blk_seg};
+    const int64_t bps = f64 ? (scatter ? 48 : 44) : (scatter ? 28 : 24);  // streamed bytes per segment
     auto segs = [&](int b) -> int64_t {
         return g->h_ang_seg_off[g->blk_w0[b] + g->blk_nw[b]] - g->h_ang_seg_off[g->blk_w0[b]];
+    };
+    auto march = [&](int b, int q, cudaStream_t st) -> cudaError_t {
+        if (!f64) return march_sw_launch(sw_march(g, b, homog, b32[q]), g->sw_coarsen, st);
+        SwMarch64 m = sw_march64(g, b, homog, b64[q]);
+        m.S = S_src;
+        return march_sw64_launch(m, st);
+    };
+    auto gather = [&](int b, int q, cudaStream_t st) -> cudaError_t {
+        SwGather t = sw_gather(g, b, b32[q], J);
+        if (f64) {
+            t.buf = nullptr;
+            t.buf64 = b64[q];
+        }
+        return scatter ? gather_rows_sw_launch(t, g->nvox, st) : gather_sw_launch(t, st);
     };
     if (!g->sw_overlap) {
         for (int b = 0; b < g->nblk; ++b) {
             int t0 = tstart(g, 0);
-            CK(march_sw_launch(sw_march(g, b, homog, bufs[0]), g->sw_coarsen, g->st));
-            tstop(g, t0, 0, segs(b), (g->sw_scatter && g->d_pos ? 28 : 24) * segs(b));
+            CK(march(b, 0, g->st));
+            tstop(g, t0, 0, segs(b), bps * segs(b));
             t0 = tstart(g, 1);
-            if (g->sw_scatter && g->d_pos) CK(gather_rows_sw_launch(sw_gather(g, b, bufs[0], J), g->nvox, g->st));
-            else CK(gather_sw_launch(sw_gather(g, b, bufs[0], J), g->st));
+            CK(gather(b, 0, g->st));
             tstop(g, t0, 1, segs(b));
             g->launches += 2;
         }
@@ -830,13 +916,12 @@ int run_fs_J_sw(rt_grid *g, int homog, double *J)
     for (int b = 0; b < g->nblk; ++b) {
         if (b >= 2) CK(cudaStreamWaitEvent(g->st, gdone[b & 1], 0));
         int t0 = tstart(g, 0);
-        CK(march_sw_launch(sw_march(g, b, homog, bufs[b & 1]), g->sw_coarsen, g->st));
-        tstop(g, t0, 0, segs(b), (g->sw_scatter && g->d_pos ? 28 : 24) * segs(b));
+        CK(march(b, b & 1, g->st));
+        tstop(g, t0, 0, segs(b), bps * segs(b));
         CK(cudaEventRecord(mdone[b & 1], g->st));
         CK(cudaStreamWaitEvent(g->st2, mdone[b & 1], 0));
         t0 = tstart(g, 1, g->st2);
-        if (g->sw_scatter && g->d_pos) CK(gather_rows_sw_launch(sw_gather(g, b, bufs[b & 1], J), g->nvox, g->st2));
-        else CK(gather_sw_launch(sw_gather(g, b, bufs[b & 1], J), g->st2));
+        CK(gather(b, b & 1, g->st2));
         tstop(g, t0, 1, segs(b), 0, g->st2);
         CK(cudaEventRecord(gdone[b & 1], g->st2));
         g->launches += 2;
@@ -854,7 +939,8 @@ int run_fs_J(rt_grid *g, int prec, int homog, const double *S_src, double *J)
     if (prec == RT_FP64) CK(pack_chiS64(n, g->d_chi, S_src, g->d_cs64, g->st));
     else CK(pack_chiS32(n, g->d_chi, S_src, g->d_B, g->d_cs32, g->d_B32, g->d_S32, g->st));
     g->launches++;
-    if (prec == RT_MIXED && use_sw(g)) return run_fs_J_sw(g, homog, J);
+    if (prec == RT_MIXED && use_sw(g)) return run_fs_J_sw(g, prec, homog, S_src, J);
+    if (prec == RT_FP64 && use_sw64(g)) return run_fs_J_sw(g, prec, homog, S_src, J);
     CK(cudaGetLastError());
     for (int b = 0; b < g->nblk; ++b) {
         int w0 = g->blk_w0[b], nw = g->blk_nw[b];
@@ -1209,6 +1295,7 @@ int rt_set_opacity(rt_grid *g, const double *chi, const double *eps, const doubl
     g->launches++;
     g->lstar_prec = -1;
     g->cw_ok = false;
+    g->cw64_ok = false;
     g->nn_ok = false;
     if (where == RT_HOST) RCK(sync(g));
     reset_ng(g);

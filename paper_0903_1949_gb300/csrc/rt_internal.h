@@ -179,6 +179,8 @@ cudaError_t seg_weight(const uint32_t *vox, const double *len64, const int64_t *
 // Streamed-weight J-only formal solution (fs_sw.cu): march of one angle block,
 // J gather of one block.
 struct SwMarch {
+    using T = float;
+    using W = float4;
     const uint32_t *vox;
     const float4 *cw;      // (E, alpha, beta, gamma) per segment (coef_stream)
     const float *cg;       // w_Omega l / L per segment (seg_weight)
@@ -188,18 +190,39 @@ struct SwMarch {
     int bulk;              // ring filled by bulk copies (1) or by per-lane 16-byte cp.async (0)
     int *err;              // raised when a bounded wait of the staged march gives up
     int64_t seg_lo, nbundles;
-    const float *S32;      // S per voxel, FP32
-    const float *B32;
+    const float *S;        // S per voxel, FP32
+    const float *B;
     float I_outer;
     int homog;
     float *out;            // c_s I_s per segment of the block
+};
+// FP64 weights of one segment (E, alpha, beta + [run start] alpha, gamma).
+struct alignas(32) Wd4 {
+    double x, y, z, w;
+};
+// The same march in FP64 (streamed FP64 weights and w l / L).
+struct SwMarch64 {
+    using T = double;
+    using W = Wd4;
+    const uint32_t *vox;
+    const Wd4 *cw;
+    const double *cg;
+    const int2 *bnd;
+    const int32_t *pos;
+    int64_t seg_lo, nbundles;
+    const double *S;
+    const double *B;
+    double I_outer;
+    int homog;
+    double *out;
 };
 struct SwGather {
     const int32_t *off, *jorder, *jsell, *crow, *cbeg, *clr, *lfirst, *perm;
     const int64_t *jgbase;
     int *cnt;
     double *part;
-    const float *buf;      // c_s I_s of the block
+    const float *buf;      // c_s I_s of the block (FP32 march)
+    const double *buf64;   // c_s I_s of the block (FP64 march); used when not NULL
     double *J;
     int64_t nshort, nchunks, nbs;
     int nlong, first;
@@ -207,6 +230,12 @@ struct SwGather {
 cudaError_t sw_bundles(const int64_t *ray_off, int64_t r_lo, int64_t r_hi, int64_t seg_lo, int64_t nseg, int chunk,
                        int2 *bnd, cudaStream_t st);
 cudaError_t march_sw_launch(const SwMarch &m, int coarsen, cudaStream_t st);
+cudaError_t march_sw64_launch(const SwMarch64 &m, cudaStream_t st);
+// FP64 weights and w l / L per segment for the FP64 streamed march.
+cudaError_t coef_stream64(const uint32_t *vox, const double *len64, const double *chi, int64_t nseg, Wd4 *cw,
+                          cudaStream_t st);
+cudaError_t seg_weight64(const uint32_t *vox, const double *len64, const int64_t *ang_seg_off, int n_ang,
+                         const double *wt, const double *invL, int nvox, int64_t nseg, double *cg, cudaStream_t st);
 cudaError_t gather_sw_launch(const SwGather &t, cudaStream_t st);
 // J from values in ownership-list order (march with pos): contiguous rows.
 cudaError_t gather_rows_sw_launch(const SwGather &t, int nvox, cudaStream_t st);

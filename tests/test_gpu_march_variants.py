@@ -32,9 +32,9 @@ def _problems():
     return {"sph17": (p1, rt.RT_PARABOLIC), "cyl_hole": (p2, rt.RT_PARABOLIC), "sph_linear": (p3, rt.RT_LINEAR)}
 
 
-def _iterate(p, interp, knobs):
+def _iterate(p, interp, knobs, precision=rt.RT_MIXED):
     g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], interp=interp,
-                precision=rt.RT_MIXED, ng=False)
+                precision=precision, ng=False)
     for k, v in knobs.items():
         g.tune(k, v)
     g.set_opacity(p["chi"], p["eps"], p["B"])
@@ -82,6 +82,21 @@ def test_march_configurations(name):
     o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"], interp=interp)
     S_o, _, _ = o.solve(p["chi"], p["eps"], p["B"], tol=0.0, max_iter=STEPS, ng=False)
     assert np.max(np.abs(S0 - S_o) / np.abs(S_o)) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["sph17", "cyl_hole", "sph_linear"])
+def test_fp64_march_configurations(name):
+    """The FP64 streamed-weight march against the FP64 march that evaluates its
+    weights itself, and against the oracle's iterates at the FP64 bar."""
+    p, interp = _problems()[name]
+    S0 = _iterate(p, interp, BASE, rt.RT_FP64)
+    for var in ({T.RT_TUNE_SCATTER: 0}, {T.RT_TUNE_OVERLAP: 0}, {T.RT_TUNE_SCATTER: 0, T.RT_TUNE_OVERLAP: 0}):
+        assert np.array_equal(_iterate(p, interp, {**BASE, **var}, rt.RT_FP64), S0), var
+    S_plain = _iterate(p, interp, {**BASE, T.RT_TUNE_STREAMED_WEIGHTS: 0}, rt.RT_FP64)
+    assert np.max(np.abs(S_plain - S0) / np.abs(S0)) < 1e-13
+    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"], interp=interp)
+    S_o, _, _ = o.solve(p["chi"], p["eps"], p["B"], tol=0.0, max_iter=STEPS, ng=False)
+    assert np.max(np.abs(S0 - S_o) / np.abs(S_o)) < 1e-11
 
 
 def test_tune_rejects_bad_values():
