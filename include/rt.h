@@ -175,6 +175,9 @@ int rt_set_precision(rt_grid *g, int precision);
  * value 1..15 (default 14: the step solved to FP64 rounding).  A looser step
  * changes the iterates, not the fixed point. */
 #define RT_TUNE_NN_JTOL 8
+/* RT_TUNE_MARCH64_COARSEN: segments per lane of the FP64 streamed-weight
+ * march, 1 or 2 (default). */
+#define RT_TUNE_MARCH64_COARSEN 9
 int rt_tune(rt_grid *g, int knob, int value);
 
 /* Formal solution from the current S with the grid's precision: J, the

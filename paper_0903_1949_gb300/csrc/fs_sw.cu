@@ -788,11 +788,12 @@ cudaError_t gather_sw_launch(const SwGather &t, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t march_sw64_launch(const SwMarch64 &m, cudaStream_t st)
+cudaError_t march_sw64_launch(const SwMarch64 &m, int coarsen, cudaStream_t st)
 {
     const int64_t grid = (m.nbundles + 7) / 8;
     if (grid <= 0) return cudaSuccess;
-    k_march_sw<SwMarch64, 1><<<(unsigned)grid, 256, 0, st>>>(m);
+    if (coarsen == 2) k_march_sw<SwMarch64, 2><<<(unsigned)grid, 256, 0, st>>>(m);
+    else k_march_sw<SwMarch64, 1><<<(unsigned)grid, 256, 0, st>>>(m);
     return cudaGetLastError();
 }
 

@@ -82,6 +82,7 @@ struct rt_grid {
     rtk::Wd4 *d_cw64 = nullptr;  // FP64 weights per segment (FP64 streamed march)
     double *d_cg64 = nullptr;    // FP64 w l / L per segment
     int sw64_state = 0;
+    int sw64_coarsen = 2;     // segments per lane of the FP64 streamed march (RT_TUNE_MARCH64_COARSEN)
     bool cw64_ok = false;
     int pos_state = 0;        // list positions: 0 not tried, 1 allocated, -1 not available
     bool cw_ok = false;       // d_cw4 matches the current chi

@@ -884,7 +884,7 @@ int run_fs_J_sw(rt_grid *g, int prec, int homog, const double *S_src, double *J)
         if (!f64) return march_sw_launch(sw_march(g, b, homog, b32[q]), g->sw_coarsen, st);
         SwMarch64 m = sw_march64(g, b, homog, b64[q]);
         m.S = S_src;
-        return march_sw64_launch(m, st);
+        return march_sw64_launch(m, g->sw64_coarsen, st);
     };
     auto gather = [&](int b, int q, cudaStream_t st) -> cudaError_t {
         SwGather t = sw_gather(g, b, b32[q], J);
@@ -1327,6 +1327,11 @@ int rt_tune(rt_grid *g, int knob, int value)
     if (knob == RT_TUNE_STREAMED_WEIGHTS) {
         if (value != 0 && value != 1) return fail(RT_EINVAL, "streamed weights: 0 or 1");
         g->sw_enabled = value;
+        return RT_OK;
+    }
+    if (knob == RT_TUNE_MARCH64_COARSEN) {
+        if (value != 1 && value != 2) return fail(RT_EINVAL, "FP64 march coarsening must be 1 or 2");
+        g->sw64_coarsen = value;
         return RT_OK;
     }
     if (knob == RT_TUNE_MARCH_STAGES) {

@@ -230,7 +230,8 @@ struct SwGather {
 cudaError_t sw_bundles(const int64_t *ray_off, int64_t r_lo, int64_t r_hi, int64_t seg_lo, int64_t nseg, int chunk,
                        int2 *bnd, cudaStream_t st);
 cudaError_t march_sw_launch(const SwMarch &m, int coarsen, cudaStream_t st);
-cudaError_t march_sw64_launch(const SwMarch64 &m, cudaStream_t st);
+// coarsen: segments per lane, 1 or 2.
+cudaError_t march_sw64_launch(const SwMarch64 &m, int coarsen, cudaStream_t st);
 // FP64 weights and w l / L per segment for the FP64 streamed march.
 cudaError_t coef_stream64(const uint32_t *vox, const double *len64, const double *chi, int64_t nseg, Wd4 *cw,
                           cudaStream_t st);
