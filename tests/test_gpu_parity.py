@@ -274,3 +274,55 @@ def test_full_size_sph65_fp32_formal_solution_within_1e5(sph65):
     g.formal_solution(rt.RT_MIXED)
     assert relerr(g.J(), J64) < TOL32
     assert relerr(g.Lstar(), L64) < TOL32
+
+
+@pytest.fixture(scope="module")
+def cyl65():
+    """The cylindrical disc workload at its full grid size (65^3 voxels, R 0.1..10,
+    |z| <= 2, transparent hole), 16 x 16 solid angles."""
+    p = I.make_problem("cyl65", n_mu=16, n_phi=16)
+    g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=rt.RT_MIXED)
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    yield p, g
+    g.close()
+
+
+SAMPLED_CYL = [0, 77, 200, 255]
+
+
+def test_full_size_cyl65_sampled_crossings_and_intensities(cyl65):
+    p, g = cyl65
+    assert g.info()["lost_rays"] == 0
+    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"])
+    rng = np.random.default_rng(6)
+    S = p["B"] * rng.uniform(0.8, 1.2, p["B"].size)
+    g.set_S(S)
+    Ib64, Lb64 = g.fs_angles(SAMPLED_CYL, rt.RT_FP64)
+    Ib32, _ = g.fs_angles(SAMPLED_CYL, rt.RT_MIXED)
+    for q, w in enumerate(SAMPLED_CYL):
+        _same_crossings(o, g, w)
+        Ib, Lb, _, miss = o.fs_angle(w, S, p["chi"], p["B"])
+        assert miss == 0
+        assert relerr(Ib64[q], Ib) < TOL64
+        assert relerr(Lb64[q], Lb) < TOL64
+        assert relerr(Ib32[q], Ib) < TOL32
+        o.free_angle(w)
+
+
+def test_full_size_cyl65_mixed_iterates_follow_fp64(cyl65):
+    """FP32 formal solution within 1e-5 of FP64 over all solid angles, and five
+    mixed-precision ALI iterations within 1e-5 of five FP64 ones."""
+    p, g = cyl65
+    g.set_S(p["B"])
+    g.formal_solution(rt.RT_FP64)
+    J64 = g.J()
+    g.formal_solution(rt.RT_MIXED)
+    assert relerr(g.J(), J64) < TOL32
+    out = {}
+    for prec in (rt.RT_FP64, rt.RT_MIXED):
+        g.set_precision(prec)
+        g.set_opacity(p["chi"], p["eps"], p["B"])
+        for _ in range(5):
+            g.ali_step()
+        out[prec] = g.S()
+    assert relerr(out[rt.RT_MIXED], out[rt.RT_FP64]) < TOL32
