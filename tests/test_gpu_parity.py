@@ -311,18 +311,24 @@ def test_full_size_cyl65_sampled_crossings_and_intensities(cyl65):
 
 def test_full_size_cyl65_mixed_iterates_follow_fp64(cyl65):
     """FP32 formal solution within 1e-5 of FP64 over all solid angles, and five
-    mixed-precision ALI iterations within 1e-5 of five FP64 ones."""
+    mixed-precision ALI iterations within 1e-5 of five FP64 ones.  Each ALI update
+    multiplies the FP32 rounding of J by (1 - eps) / (1 - (1 - eps) Lambda*), up to
+    ~1e3 in the eps = 1e-6 disc (what the FP64 refinement of rt_solve is for), so the
+    iterates are compared at eps = 0.1, where the factor is at most 10."""
     p, g = cyl65
     g.set_S(p["B"])
     g.formal_solution(rt.RT_FP64)
-    J64 = g.J()
+    J64, L64 = g.J(), g.Lstar()
     g.formal_solution(rt.RT_MIXED)
     assert relerr(g.J(), J64) < TOL32
+    assert relerr(g.Lstar(), L64) < TOL32
+    eps = np.full(p["B"].size, 0.1)
     out = {}
     for prec in (rt.RT_FP64, rt.RT_MIXED):
         g.set_precision(prec)
-        g.set_opacity(p["chi"], p["eps"], p["B"])
+        g.set_opacity(p["chi"], eps, p["B"])
         for _ in range(5):
             g.ali_step()
         out[prec] = g.S()
     assert relerr(out[rt.RT_MIXED], out[rt.RT_FP64]) < TOL32
+    g.set_opacity(p["chi"], p["eps"], p["B"])
