@@ -61,6 +61,23 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(x, dist, device):
+    """Largest x over the ranks of the process group (x itself without one)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms_max):
+    """Whole-job throughput: every rank processes units_per_rank per step (replicas, weak
+    scaling); the job's step time is the slowest rank's."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -267,12 +284,7 @@ def main():
             fn()
         ev1.record(stream)
         barrier_sync()
-        ms = ev0.elapsed_time(ev1) / k
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(ev0.elapsed_time(ev1) / k, dist, "cuda")
 
     # ---- mixed-precision ALI iterations (the headline) ----
     # Every TIMING_EVERY-th angle block's march launch is bracketed by CUDA events on
@@ -288,7 +300,7 @@ def main():
     clocks.mark()
     ck = clocks.stop()
     tm = g.timing()
-    value = world * units / (ms / 1e3)
+    value = job_throughput(units, world, ms)
     march_avg_ms = tm["march_ms"] / max(1, tm["march_launches"])
     seg_per_launch = tm["march_segments"] / max(1, tm["march_launches"])
     bytes_per_seg = tm["march_bytes"] / max(1, tm["march_segments"])
@@ -311,14 +323,14 @@ def main():
         g.ali_step()
     k64 = max(2, args.steps // 4)
     ms64 = timed(g.ali_step, k64)
-    value64 = world * units / (ms64 / 1e3)
+    value64 = job_throughput(units, world, ms64)
     g.tune(rt.RT_TUNE_STREAMED_WEIGHTS, 0)
     g.set_S(p["B"])
     g.ali_step()
     g.ali_step()
     ms64p = timed(g.ali_step, 2)
     g.tune(rt.RT_TUNE_STREAMED_WEIGHTS, 1)
-    value64p = world * units / (ms64p / 1e3)
+    value64p = job_throughput(units, world, ms64p)
 
     # ---- end to end through the C ABI with pinned host buffers ----
     g.set_precision(rt.RT_MIXED)
@@ -338,12 +350,8 @@ def main():
     for _ in range(args.steps):
         e2e_step()
     barrier_sync()
-    ms_e2e = (time.perf_counter() - t0) * 1e3 / args.steps
-    if dist:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e = {"value": world * units / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": 8 * nvox,
+    ms_e2e = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, dist, "cuda")
+    e2e = {"value": job_throughput(units, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": 8 * nvox,
            "d2h_bytes_per_step": 8 * nvox, "ms_per_step": ms_e2e,
            "path": "rt_set_S(pinned host S) + rt_ali_step + rt_get_J(pinned host J) per step"}
 
