@@ -159,6 +159,37 @@ def make_batch_problem(n_members=256, n_angle=16, shapes=((33, 17, 33), (65, 33,
     return grids, member_grid, members
 
 
+def line_profile(n_freq=32, width=1.0, span=4.0):
+    """Frequency sampling of a Doppler (Gaussian) line over +-span widths, the outer
+    points effectively continuum (the paper's 32 wavelength points, Sect. 3.1):
+    (phi, w) with trapezoid weights w and phi normalised to sum_k w_k phi_k = 1."""
+    x = np.linspace(-span, span, n_freq)
+    w = np.full(n_freq, x[1] - x[0]) if n_freq > 1 else np.ones(1)
+    if n_freq > 1:
+        w[0] *= 0.5
+        w[-1] *= 0.5
+    phi = np.exp(-(x / width) ** 2)
+    phi /= np.sum(w * phi)
+    return phi, w
+
+
+def line_problem(name="sph17", n_freq=32, ratio=1e6, eps_l=1e-2, **over):
+    """The paper's two-level test on a named grid: grey continuum chi_c (the grid's chi
+    law scaled to a radial continuum tau of 1e-2, so the line centre reaches 1e4 with
+    chi_l / chi_c = ratio), thermal B, line profile of line_profile(n_freq)."""
+    p = make_problem(name, **over)
+    rmin, rmax = p["edges"][0][0], p["edges"][0][-1]
+    c1, _, _ = voxel_centres(p["coord"], p["edges"])
+    if p["coord"] == SPHERICAL:
+        chi_c = (1e-2 / (1.0 / rmin - 1.0 / rmax)) / (c1 * c1)
+    else:
+        chi_c = np.full(c1.shape, 1e-2 / (rmax - rmin))
+    chi_c = np.ascontiguousarray(chi_c.reshape(-1))
+    phi, w = line_profile(n_freq)
+    p.update(chi_c=chi_c, chi_l=ratio * chi_c, eps_l=np.full(chi_c.size, eps_l), phi=phi, wq=w)
+    return p
+
+
 def voxel_angle_count(n, n_ang):
     return int(np.prod(n)) * int(n_ang)
 
