@@ -327,6 +327,43 @@ int rt_batch_get(const rt_batch *b, int m, int what, double *out, int where);
  * NULL).  Member S is restored afterwards. */
 int rt_batch_autotune(rt_batch *b, int32_t *chunk_out, int32_t *grid_out, double *ms_out);
 
+/* ---- Two-level-atom line transfer (Sect. 3.1, 3.2.2) ----
+ *
+ * A line sampled at n_freq frequencies on one grid: profile phi[k] >= 0 and
+ * quadrature weights wq[k] >= 0 with sum_k wq[k] phi[k] = 1 (checked to 1e-10,
+ * else RT_EINVAL).  At frequency k the opacity is chi_k = chi_c + chi_l phi_k
+ * and the source function mixes a thermal continuum (S_c = B) and the line,
+ *     S_k = (chi_c B + chi_l phi_k S_l) / chi_k,
+ *     S_l = (1 - eps_l) Jbar + eps_l B,   Jbar = sum_k wq_k phi_k J_k.
+ * The problem is an rt_batch whose member k is frequency k (rt_batch_get
+ * reads S_k, J_k and Lambda*_k; rt_batch_autotune tunes it and restores S_l;
+ * rt_batch_set_member, rt_batch_ali_step and rt_batch_solve are RT_EINVAL on
+ * it).  One iteration, a single CUDA graph: S_k from S_l for every k, the
+ * n_freq FP32 J-only formal solutions, then Jbar (frequencies summed in
+ * ascending order, FP64) and the ALI update of S_l with the frequency-averaged
+ * diagonal operator Lbar* = sum_k wq_k phi_k (chi_l phi_k / chi_k) Lambda*_k:
+ *     S_l <- S_l + [(1 - eps_l) Jbar + eps_l B - S_l] / (1 - (1 - eps_l) Lbar*).
+ * Lambda*_k comes from one full FP32 formal solution per frequency.
+ * The grid must outlive the problem; it is used on the problem's stream. */
+int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, const double *wq, void *stream);
+
+/* chi_c, chi_l (>= 0, with chi_c + chi_l phi_k > 0 for every k), eps_l in
+ * (0, 1] and B >= 0, n_vox each (host arrays validated, device arrays not);
+ * computes every frequency's parabola choices, Lambda*_k and Lbar*, and sets
+ * S_l = B.  Required before the first step. */
+int rt_line_set(rt_batch *b, const double *chi_c, const double *chi_l, const double *eps_l, const double *B,
+                int where);
+
+/* One iteration; max_rel_dSl (may be NULL) gets max_v |dS_l| / |S_l|. */
+int rt_line_step(rt_batch *b, double *max_rel_dSl);
+
+/* Iterate until max rel dS_l < tol (RT_ENOTCONVERGED after max_iter);
+ * iters (may be NULL) gets the iterations done. */
+int rt_line_solve(rt_batch *b, double tol, int max_iter, int32_t *iters);
+
+/* S_l (what = 0), Jbar of the last iteration (1) or Lbar* (2), n_vox values. */
+int rt_line_get(const rt_batch *b, int what, double *out, int where);
+
 /* Device timing of the hot kernels.  rt_set_timing(g, 1) resets the counters
  * and brackets every ray-march and gather launch of later calls with CUDA
  * events on the stream each runs on; rt_set_timing(g, N) with N > 1 brackets

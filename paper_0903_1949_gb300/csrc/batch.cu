@@ -12,6 +12,12 @@
 // appears at most once per wave, so its J accumulates over its angle blocks
 // in a fixed order.  The whole iteration is captured once as a CUDA graph and
 // replayed; rt_batch_autotune picks the bundle size and the persistent grid.
+//
+// A two-level-atom line problem (rt_line_*) is a batch whose members are the
+// frequencies of one grid: each iteration sets S_k from the line source
+// function S_l, solves the n_freq formal solutions and updates S_l from
+// Jbar = sum_k w_k phi_k J_k with the frequency-averaged diagonal Lambda*
+// (Sect. 3.1, 3.2.2).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -73,6 +79,58 @@ __global__ void k_bali(int64_t n, const int64_t *voff, int nm, double *S, const 
     }
 }
 
+// Line mode.  S_k = (chi_c B + chi_l phi_k S_l) / chi_k for every frequency k
+// (members k*nvox .. (k+1)*nvox - 1 of the concatenated arrays).
+__global__ void k_line_src(int nvox, int nf, const double *chi, const double *chi_c, const double *chi_l,
+                           const double *B, const double *phi, const double *S_l, double *S)
+{
+    const int64_t n = (int64_t)nvox * nf;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i / nvox), v = (int)(i % nvox);
+        S[i] = (chi_c[v] * B[v] + chi_l[v] * phi[k] * S_l[v]) / chi[i];
+    }
+}
+
+__global__ void k_line_chik(int nvox, const double *chi_c, const double *chi_l, double phik, double *chik)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < nvox) chik[v] = chi_c[v] + chi_l[v] * phik;
+}
+
+// Lbar* = sum_k w_k phi_k (chi_l phi_k / chi_k) Lambda*_k
+__global__ void k_line_lbar(int nvox, int nf, const double *L, const double *chi, const double *chi_l,
+                            const double *phi, const double *wq, double *Lbar)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    double acc = 0.0;
+    for (int k = 0; k < nf; ++k) {
+        const int64_t i = (int64_t)k * nvox + v;
+        acc += wq[k] * phi[k] * (chi_l[v] * phi[k] / chi[i]) * L[i];
+    }
+    Lbar[v] = acc;
+}
+
+// Jbar = sum_k w_k phi_k J_k (k ascending); S_l <- S_l + [(1-eps_l) Jbar + eps_l B - S_l] / (1 - (1-eps_l) Lbar*)
+__global__ void k_line_update(int nvox, int nf, const double *J, const double *phi, const double *wq,
+                              const double *eps_l, const double *B, const double *Lbar, double *S_l, double *Jbar,
+                              unsigned long long *maxrel)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    double rel = 0.0;
+    if (v < nvox) {
+        double jb = 0.0;
+        for (int k = 0; k < nf; ++k) jb += wq[k] * phi[k] * J[(int64_t)k * nvox + v];
+        const double e = eps_l[v], s = S_l[v];
+        const double sn = s + ((1.0 - e) * jb + e * B[v] - s) / (1.0 - (1.0 - e) * Lbar[v]);
+        rel = fabs(sn - s) / fabs(sn);
+        S_l[v] = sn;
+        Jbar[v] = jb;
+    }
+    for (int o = 16; o > 0; o >>= 1) rel = fmax(rel, __shfl_down_sync(0xffffffffu, rel, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(maxrel, (unsigned long long)__double_as_longlong(rel));
+}
+
 struct Wave {
     int n = 0;            // items
     int64_t mi0 = 0;      // first item in the concatenated item arrays
@@ -115,6 +173,13 @@ struct rt_batch {
     int grid_march = 152 * 5, grid_gather = 152 * 5;
     cudaGraphExec_t graph = nullptr;
     std::vector<double> history;  // max over members of max rel dS per iteration
+    // two-level line mode (rt_line_*): the members are the frequencies of one grid
+    int line = 0;
+    int nf = 0, lnvox = 0;
+    double *chi_c = nullptr, *chi_l = nullptr, *eps_l = nullptr, *Bl = nullptr;
+    double *phi = nullptr, *wq = nullptr, *S_l = nullptr, *Jbar = nullptr, *Lbar = nullptr, *ones = nullptr, *tmp = nullptr;
+    std::vector<double> h_phi;
+    bool line_ready = false;
 };
 
 namespace {
@@ -177,6 +242,11 @@ int build_prefixes(rt_batch *b)
 // The kernels of one ALI iteration of all members (captured into the graph).
 int enqueue_iteration(rt_batch *b)
 {
+    if (b->line) {
+        k_line_src<<<152 * 8, 256, 0, b->st>>>(b->lnvox, b->nf, b->chi, b->chi_c, b->chi_l, b->Bl, b->phi, b->S_l,
+                                                b->S);
+        BCK(cudaGetLastError());
+    }
     k_bpack<<<152 * 8, 256, 0, b->st>>>(b->ntot, b->chi, b->S, b->B, b->cs, b->B32);
     BCK(cudaGetLastError());
     for (const Wave &w : b->waves) {
@@ -186,7 +256,12 @@ int enqueue_iteration(rt_batch *b)
         BCK(gather_J_batch(b->d_gi + w.mi0, b->d_wpfx + w.pf0, w.n, w.work, b->counters + 1, b->grid_gather, b->st));
     }
     BCK(cudaMemsetAsync(b->maxrel, 0, sizeof(unsigned long long) * b->nm, b->st));
-    k_bali<<<152 * 8, 256, 0, b->st>>>(b->ntot, b->d_voff, b->nm, b->S, b->J, b->L, b->eps, b->B, b->maxrel);
+    if (b->line) {
+        k_line_update<<<(b->lnvox + 255) / 256, 256, 0, b->st>>>(b->lnvox, b->nf, b->J, b->phi, b->wq, b->eps_l, b->Bl,
+                                                                 b->Lbar, b->S_l, b->Jbar, b->maxrel);
+    } else {
+        k_bali<<<152 * 8, 256, 0, b->st>>>(b->ntot, b->d_voff, b->nm, b->S, b->J, b->L, b->eps, b->B, b->maxrel);
+    }
     BCK(cudaGetLastError());
     return RT_OK;
 }
@@ -395,7 +470,15 @@ int rt_batch_destroy(rt_batch *b)
     return RT_OK;
 }
 
+int batch_set_member(rt_batch *b, int m, const double *chi, const double *eps, const double *B, int where);
+
 int rt_batch_set_member(rt_batch *b, int m, const double *chi, const double *eps, const double *B, int where)
+{
+    if (b && b->line) return bfail(RT_EINVAL, "the frequencies of a line problem are set by rt_line_set");
+    return batch_set_member(b, m, chi, eps, B, where);
+}
+
+int batch_set_member(rt_batch *b, int m, const double *chi, const double *eps, const double *B, int where)
 {
     if (!b || !chi || !eps || !B) return bfail(RT_EINVAL, "NULL argument");
     if (m < 0 || m >= b->nm) return bfail(RT_EINVAL, "member out of range");
@@ -431,6 +514,7 @@ int rt_batch_set_member(rt_batch *b, int m, const double *chi, const double *eps
 int rt_batch_ali_step(rt_batch *b, double *max_rel_dS)
 {
     if (!b) return bfail(RT_EINVAL, "batch is NULL");
+    if (b->line) return bfail(RT_EINVAL, "a line problem iterates with rt_line_step");
     BCK(cudaSetDevice(b->device));
     return step(b, max_rel_dS);
 }
@@ -438,6 +522,7 @@ int rt_batch_ali_step(rt_batch *b, double *max_rel_dS)
 int rt_batch_solve(rt_batch *b, double tol, int max_iter, int32_t *iters)
 {
     if (!b) return bfail(RT_EINVAL, "batch is NULL");
+    if (b->line) return bfail(RT_EINVAL, "a line problem iterates with rt_line_solve");
     if (!(tol > 0.0) || max_iter < 1) return bfail(RT_EINVAL, "need tol > 0 and max_iter >= 1");
     BCK(cudaSetDevice(b->device));
     std::vector<double> rel(b->nm);
@@ -480,9 +565,12 @@ int rt_batch_autotune(rt_batch *b, int32_t *chunk_out, int32_t *grid_out, double
     BCK(cudaSetDevice(b->device));
     for (int m = 0; m < b->nm; ++m)
         if (!b->ready[m]) return bfail(RT_EINVAL, "set every member before autotuning");
-    double *saveS = nullptr;
-    BRCK(balloc(b, &saveS, b->ntot));
+    double *saveS = nullptr;  // line mode: the iteration also moves S_l, kept after the member S
+    const size_t nsave = b->ntot + (b->line ? b->lnvox : 0);
+    BRCK(balloc(b, &saveS, nsave));
     BCK(cudaMemcpyAsync(saveS, b->S, sizeof(double) * b->ntot, cudaMemcpyDeviceToDevice, b->st));
+    if (b->line)
+        BCK(cudaMemcpyAsync(saveS + b->ntot, b->S_l, sizeof(double) * b->lnvox, cudaMemcpyDeviceToDevice, b->st));
     const int chunks[3] = {512, 1024, 2048};
     const int grids[2] = {152 * 4, 152 * 8};
     double best = 1e300;
@@ -510,6 +598,9 @@ int rt_batch_autotune(rt_batch *b, int32_t *chunk_out, int32_t *grid_out, double
                 bg = gsz;
             }
             BCK(cudaMemcpyAsync(b->S, saveS, sizeof(double) * b->ntot, cudaMemcpyDeviceToDevice, b->st));
+            if (b->line)
+                BCK(cudaMemcpyAsync(b->S_l, saveS + b->ntot, sizeof(double) * b->lnvox, cudaMemcpyDeviceToDevice,
+                                    b->st));
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -525,6 +616,125 @@ int rt_batch_autotune(rt_batch *b, int32_t *chunk_out, int32_t *grid_out, double
     if (chunk_out) *chunk_out = bc;
     if (grid_out) *grid_out = bg;
     if (ms_out) *ms_out = best;
+    return RT_OK;
+}
+
+// ---- two-level-atom line transfer (the members are the frequencies) ----
+
+int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, const double *wq, void *stream)
+{
+    if (!out || !g || n_freq < 1 || !phi || !wq) return bfail(RT_EINVAL, "bad arguments");
+    double norm = 0.0;
+    for (int k = 0; k < n_freq; ++k) {
+        if (!(phi[k] >= 0.0) || !std::isfinite(phi[k]) || !(wq[k] >= 0.0) || !std::isfinite(wq[k]))
+            return bfail(RT_EINVAL, "phi and wq must be >= 0 and finite");
+        norm += wq[k] * phi[k];
+    }
+    if (!(std::fabs(norm - 1.0) <= 1e-10)) return bfail(RT_EINVAL, "sum_k wq_k phi_k must be 1");
+    std::vector<int32_t> mg(n_freq, 0);
+    rt_grid *gs[1] = {g};
+    rt_batch *b = nullptr;
+    BRCK(rt_batch_create(&b, gs, 1, n_freq, mg.data(), stream));
+    b->line = 1;
+    b->nf = n_freq;
+    b->lnvox = g->nvox;
+    b->h_phi.assign(phi, phi + n_freq);
+    const int n = g->nvox;
+    int rc = RT_OK;
+    if ((rc = balloc(b, &b->chi_c, n)) != RT_OK || (rc = balloc(b, &b->chi_l, n)) != RT_OK ||
+        (rc = balloc(b, &b->eps_l, n)) != RT_OK || (rc = balloc(b, &b->Bl, n)) != RT_OK ||
+        (rc = balloc(b, &b->phi, n_freq)) != RT_OK || (rc = balloc(b, &b->wq, n_freq)) != RT_OK ||
+        (rc = balloc(b, &b->S_l, n)) != RT_OK || (rc = balloc(b, &b->Jbar, n)) != RT_OK ||
+        (rc = balloc(b, &b->Lbar, n)) != RT_OK || (rc = balloc(b, &b->ones, n)) != RT_OK ||
+        (rc = balloc(b, &b->tmp, n)) != RT_OK) {
+        std::string keep = rt_last_error();
+        rt_batch_destroy(b);
+        set_last_error(keep.c_str());
+        return rc;
+    }
+    if (cudaMemcpyAsync(b->phi, phi, sizeof(double) * n_freq, cudaMemcpyHostToDevice, b->st) != cudaSuccess ||
+        cudaMemcpyAsync(b->wq, wq, sizeof(double) * n_freq, cudaMemcpyHostToDevice, b->st) != cudaSuccess ||
+        fill_const(n, b->ones, 1.0, b->st) != cudaSuccess || cudaStreamSynchronize(b->st) != cudaSuccess) {
+        rt_batch_destroy(b);
+        return bfail(RT_ECUDA, "line set-up copies failed");
+    }
+    *out = b;
+    return RT_OK;
+}
+
+int rt_line_set(rt_batch *b, const double *chi_c, const double *chi_l, const double *eps_l, const double *B, int where)
+{
+    if (!b || !chi_c || !chi_l || !eps_l || !B) return bfail(RT_EINVAL, "NULL argument");
+    if (!b->line) return bfail(RT_EINVAL, "not a line problem (rt_line_create)");
+    if (where != RT_HOST && where != RT_DEVICE) return bfail(RT_EINVAL, "where must be RT_HOST or RT_DEVICE");
+    BCK(cudaSetDevice(b->device));
+    const int n = b->lnvox;
+    if (where == RT_HOST) {
+        for (int v = 0; v < n; ++v) {
+            if (!(chi_c[v] >= 0.0) || !(chi_l[v] >= 0.0) || !std::isfinite(chi_c[v]) || !std::isfinite(chi_l[v]))
+                return bfail(RT_EINVAL, "chi_c and chi_l must be >= 0 and finite");
+            for (int k = 0; k < b->nf; ++k)
+                if (!(chi_c[v] + chi_l[v] * b->h_phi[k] > 0.0)) return bfail(RT_EINVAL, "chi_c + chi_l phi_k must be > 0");
+            if (!(eps_l[v] > 0.0 && eps_l[v] <= 1.0)) return bfail(RT_EINVAL, "eps_l must be in (0, 1]");
+            if (!(B[v] >= 0.0) || !std::isfinite(B[v])) return bfail(RT_EINVAL, "B must be >= 0 and finite");
+        }
+    }
+    const cudaMemcpyKind kind = where == RT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    BCK(cudaMemcpyAsync(b->chi_c, chi_c, sizeof(double) * n, kind, b->st));
+    BCK(cudaMemcpyAsync(b->chi_l, chi_l, sizeof(double) * n, kind, b->st));
+    BCK(cudaMemcpyAsync(b->eps_l, eps_l, sizeof(double) * n, kind, b->st));
+    BCK(cudaMemcpyAsync(b->Bl, B, sizeof(double) * n, kind, b->st));
+    for (int k = 0; k < b->nf; ++k) {  // frequency k: chi_k, its parabola choices and Lambda*_k
+        k_line_chik<<<(n + 255) / 256, 256, 0, b->st>>>(n, b->chi_c, b->chi_l, b->h_phi[k], b->tmp);
+        BCK(cudaGetLastError());
+        BRCK(batch_set_member(b, k, b->tmp, b->ones, b->Bl, RT_DEVICE));
+    }
+    k_line_lbar<<<(n + 255) / 256, 256, 0, b->st>>>(n, b->nf, b->L, b->chi, b->chi_l, b->phi, b->wq, b->Lbar);
+    BCK(cudaGetLastError());
+    BCK(cudaMemcpyAsync(b->S_l, b->Bl, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    b->line_ready = true;
+    b->history.clear();
+    return RT_OK;
+}
+
+int rt_line_step(rt_batch *b, double *max_rel_dSl)
+{
+    if (!b) return bfail(RT_EINVAL, "batch is NULL");
+    if (!b->line) return bfail(RT_EINVAL, "not a line problem (rt_line_create)");
+    if (!b->line_ready) return bfail(RT_EINVAL, "rt_line_set first");
+    BCK(cudaSetDevice(b->device));
+    std::vector<double> rel(b->nm);
+    BRCK(step(b, rel.data()));
+    if (max_rel_dSl) *max_rel_dSl = rel[0];
+    return RT_OK;
+}
+
+int rt_line_solve(rt_batch *b, double tol, int max_iter, int32_t *iters)
+{
+    if (!b) return bfail(RT_EINVAL, "batch is NULL");
+    if (!(tol > 0.0) || max_iter < 1) return bfail(RT_EINVAL, "need tol > 0 and max_iter >= 1");
+    if (iters) *iters = 0;
+    for (int it = 1; it <= max_iter; ++it) {
+        double rel = 0.0;
+        BRCK(rt_line_step(b, &rel));
+        if (iters) *iters = it;
+        if (rel < tol) return RT_OK;
+    }
+    return bfail(RT_ENOTCONVERGED, "line source function not converged in " + std::to_string(max_iter) + " iterations");
+}
+
+int rt_line_get(const rt_batch *b, int what, double *out, int where)
+{
+    if (!b || !out) return bfail(RT_EINVAL, "NULL argument");
+    if (!b->line) return bfail(RT_EINVAL, "not a line problem (rt_line_create)");
+    if (where != RT_HOST && where != RT_DEVICE) return bfail(RT_EINVAL, "where must be RT_HOST or RT_DEVICE");
+    const double *src = what == 0 ? b->S_l : what == 1 ? b->Jbar : what == 2 ? b->Lbar : nullptr;
+    if (!src) return bfail(RT_EINVAL, "what must be 0 (S_l), 1 (Jbar) or 2 (Lbar*)");
+    BCK(cudaSetDevice(b->device));
+    BCK(cudaMemcpyAsync(out, src, sizeof(double) * b->lnvox,
+                        where == RT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, b->st));
+    BCK(cudaStreamSynchronize(b->st));
     return RT_OK;
 }
 

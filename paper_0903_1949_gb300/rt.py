@@ -104,6 +104,11 @@ def load():
         "rt_get_timing": [_P, ctypes.POINTER(rt_timing)],
         "rt_adjoint": [_P, _P, _P, _P, ctypes.c_double, _I, _P, _P, _P, _I, ctypes.POINTER(_I)],
         "rt_get_Lstar_nn": [_P, _P, _I],
+        "rt_line_create": [ctypes.POINTER(_P), _P, _I, _P, _P, _P],
+        "rt_line_set": [_P, _P, _P, _P, _P, _I],
+        "rt_line_step": [_P, _P],
+        "rt_line_solve": [_P, ctypes.c_double, _I, ctypes.POINTER(ctypes.c_int32)],
+        "rt_line_get": [_P, _I, _P, _I],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -412,6 +417,72 @@ class Batch:
 
     def autotune(self):
         return rt_batch_autotune(self.h)
+
+
+def rt_line_create(grid_handle, phi, wq, stream=None):
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    wq = np.ascontiguousarray(wq, dtype=np.float64)
+    if phi.shape != wq.shape or phi.ndim != 1:
+        raise ValueError("phi and wq: one value per frequency each")
+    h = ctypes.c_void_p()
+    _check(load().rt_line_create(ctypes.byref(h), grid_handle, int(phi.size), ctypes.c_void_p(phi.ctypes.data),
+                                 ctypes.c_void_p(wq.ctypes.data), stream if stream else None))
+    return h
+
+
+def rt_line_set(h, chi_c, chi_l, eps_l, B):
+    ptrs = [_ptr(a) for a in (chi_c, chi_l, eps_l, B)]
+    if len({w for _, w, _ in ptrs}) != 1:
+        raise TypeError("chi_c, chi_l, eps_l and B must live in the same memory space")
+    return _check(load().rt_line_set(h, *[p for p, _, _ in ptrs], ptrs[0][1]))
+
+
+def rt_line_step(h):
+    rel = ctypes.c_double()
+    _check(load().rt_line_step(h, ctypes.byref(rel)))
+    return rel.value
+
+
+def rt_line_solve(h, tol, max_iter):
+    it = ctypes.c_int32()
+    rc = load().rt_line_solve(h, float(tol), int(max_iter), ctypes.byref(it))
+    if rc not in (RT_OK, RT_ENOTCONVERGED):
+        _check(rc)
+    return it.value, rc == RT_OK
+
+
+def rt_line_get(h, what, n_vox, out=None):
+    return _get(lambda hh, p, w: load().rt_line_get(hh, int(what), p, w), h, n_vox, out)
+
+
+class Line(Batch):
+    """Two-level-atom line on one grid, one batch member per frequency (see rt_line_* in rt.h)."""
+
+    def __init__(self, grid, phi, wq, stream=None):
+        self.grids = [grid]
+        self.member_grid = [0] * len(phi)
+        self.h = None
+        self.h = rt_line_create(grid.h, phi, wq, stream)
+        self.nvox = [grid.nvox] * len(phi)
+        self.n = grid.nvox
+
+    def set(self, chi_c, chi_l, eps_l, B):
+        rt_line_set(self.h, chi_c, chi_l, eps_l, B)
+
+    def step(self):
+        return rt_line_step(self.h)
+
+    def solve(self, tol, max_iter):
+        return rt_line_solve(self.h, tol, max_iter)
+
+    def S_l(self):
+        return rt_line_get(self.h, 0, self.n)
+
+    def Jbar(self):
+        return rt_line_get(self.h, 1, self.n)
+
+    def Lbar(self):
+        return rt_line_get(self.h, 2, self.n)
 
 
 class Grid:
