@@ -126,6 +126,7 @@ class OracleGrid:
 
     def __init__(self, coord, edges, dirs, weights, inner_bc=CORE_B, I_outer=0.0, interp=PARABOLIC):
         self._keep = [_d(e) for e in edges]
+        self.coord = int(coord)
         self.n = tuple(len(e) - 1 for e in edges)
         self.nvox = int(np.prod(self.n))
         dirs, pdir = _d(np.asarray(dirs).reshape(-1, 3))
