@@ -344,8 +344,17 @@ int rt_batch_autotune(rt_batch *b, int32_t *chunk_out, int32_t *grid_out, double
  * diagonal operator Lbar* = sum_k wq_k phi_k (chi_l phi_k / chi_k) Lambda*_k:
  *     S_l <- S_l + [(1 - eps_l) Jbar + eps_l B - S_l] / (1 - (1 - eps_l) Lbar*).
  * Lambda*_k comes from one full FP32 formal solution per frequency.
+ * use_lstar = RT_LSTAR_NN (needs n_phi >= 3) replaces the diagonal operator by
+ * the exact dJbar_v / dS_l,u on the 3 x 3 x 3 index neighbourhood of v,
+ *     Lbar*_vu = sum_k wq_k phi_k Lambda*_NN,k,vu (chi_l phi_k / chi_k)_u,
+ * built once per rt_line_set from each frequency's exact nearest-neighbour
+ * Lambda* (as rt_get_Lstar_nn), and each iteration solves
+ * (I - (1 - eps_l) Lbar*) dS_l = (1 - eps_l) Jbar + eps_l B - S_l by Jacobi
+ * sweeps to a sweep change <= 1e-14 max |dS_l| after the graph.  use_lstar
+ * other than RT_LSTAR_DIAG / RT_LSTAR_NN is RT_EINVAL.
  * The grid must outlive the problem; it is used on the problem's stream. */
-int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, const double *wq, void *stream);
+int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, const double *wq, int use_lstar,
+                   void *stream);
 
 /* chi_c, chi_l (>= 0, with chi_c + chi_l phi_k > 0 for every k), eps_l in
  * (0, 1] and B >= 0, n_vox each (host arrays validated, device arrays not);
@@ -361,7 +370,9 @@ int rt_line_step(rt_batch *b, double *max_rel_dSl);
  * iters (may be NULL) gets the iterations done. */
 int rt_line_solve(rt_batch *b, double tol, int max_iter, int32_t *iters);
 
-/* S_l (what = 0), Jbar of the last iteration (1) or Lbar* (2), n_vox values. */
+/* S_l (what = 0), Jbar of the last iteration (1) or the diagonal Lbar* (2),
+ * n_vox values; of a nearest-neighbour line also its Lbar* (3), 27 n_vox values
+ * in the slot order of rt_get_Lstar_nn (RT_EINVAL on a diagonal line). */
 int rt_line_get(const rt_batch *b, int what, double *out, int where);
 
 /* Device timing of the hot kernels.  rt_set_timing(g, 1) resets the counters

@@ -94,7 +94,7 @@ __global__ void k_line_src(int nvox, int nf, const double *chi, const double *ch
 __global__ void k_line_chik(int nvox, const double *chi_c, const double *chi_l, double phik, double *chik)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < nvox) chik[v] = chi_c[v] + chi_l[v] * phik;
+    if (v < nvox) chik[v] = fma(chi_l[v], phik, chi_c[v]);
 }
 
 // Lbar* = sum_k w_k phi_k (chi_l phi_k / chi_k) Lambda*_k
@@ -129,6 +129,42 @@ __global__ void k_line_update(int nvox, int nf, const double *J, const double *p
     }
     for (int o = 16; o > 0; o >>= 1) rel = fmax(rel, __shfl_down_sync(0xffffffffu, rel, o));
     if ((threadIdx.x & 31) == 0) atomicMax(maxrel, (unsigned long long)__double_as_longlong(rel));
+}
+
+// Nearest-neighbour line operator, frequency k's share:
+// Lbar27[v][q] (+)= w_k phi_k L27_k[v][q] (chi_l phi_k / chi_k) at the voxel u in slot q.
+__global__ void k_line_lbar_nn(int nvox, int sph, int n1, int n2, int n3, const double *L27k, const double *chi_c,
+                               const double *chi_l, double phik, double wphi, double *Lbar27, int first)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    const int c3 = v % n3, c2 = (v / n3) % n2, c1 = v / (n3 * n2);
+    for (int q = 0; q < 27; ++q) {
+        int i = c1 + q / 9 - 1, j = c2 + (q / 3) % 3 - 1, k = c3 + q % 3 - 1;
+        if (sph) k = (k + n3) % n3;
+        else j = (j + n2) % n2;
+        double f = 0.0;
+        if (i >= 0 && i < n1 && j >= 0 && j < n2 && k >= 0 && k < n3) {
+            const int u = (i * n2 + j) * n3 + k;
+            f = chi_l[u] * phik / fma(chi_l[u], phik, chi_c[u]);
+        }
+        const int64_t e = 27 * (int64_t)v + q;
+        const double add = wphi * L27k[e] * f;
+        Lbar27[e] = first ? add : Lbar27[e] + add;
+    }
+}
+
+// Jbar = sum_k w_k phi_k J_k (k ascending) and the right-hand side of the
+// nearest-neighbour OS step, y = (1 - eps_l) Jbar + eps_l B - S_l.
+__global__ void k_line_rhs(int nvox, int nf, const double *J, const double *phi, const double *wq,
+                           const double *eps_l, const double *B, const double *S_l, double *Jbar, double *y)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    double jb = 0.0;
+    for (int k = 0; k < nf; ++k) jb += wq[k] * phi[k] * J[(int64_t)k * nvox + v];
+    Jbar[v] = jb;
+    y[v] = (1.0 - eps_l[v]) * jb + eps_l[v] * B[v] - S_l[v];
 }
 
 struct Wave {
@@ -178,8 +214,12 @@ struct rt_batch {
     int nf = 0, lnvox = 0;
     double *chi_c = nullptr, *chi_l = nullptr, *eps_l = nullptr, *Bl = nullptr;
     double *phi = nullptr, *wq = nullptr, *S_l = nullptr, *Jbar = nullptr, *Lbar = nullptr, *ones = nullptr, *tmp = nullptr;
-    std::vector<double> h_phi;
+    std::vector<double> h_phi, h_wq;
     bool line_ready = false;
+    int lstar = RT_LSTAR_DIAG;  // line operator: diagonal or nearest-neighbour
+    double *Lbar27 = nullptr, *L27k = nullptr, *nnx = nullptr, *nny = nullptr;
+    unsigned long long *nnmx = nullptr;
+    int nn_sweeps = 0;
 };
 
 namespace {
@@ -256,7 +296,10 @@ int enqueue_iteration(rt_batch *b)
         BCK(gather_J_batch(b->d_gi + w.mi0, b->d_wpfx + w.pf0, w.n, w.work, b->counters + 1, b->grid_gather, b->st));
     }
     BCK(cudaMemsetAsync(b->maxrel, 0, sizeof(unsigned long long) * b->nm, b->st));
-    if (b->line) {
+    if (b->line && b->lstar == RT_LSTAR_NN) {  // the OS solve follows the graph (line_nn_os)
+        k_line_rhs<<<(b->lnvox + 255) / 256, 256, 0, b->st>>>(b->lnvox, b->nf, b->J, b->phi, b->wq, b->eps_l, b->Bl,
+                                                              b->S_l, b->Jbar, b->nny);
+    } else if (b->line) {
         k_line_update<<<(b->lnvox + 255) / 256, 256, 0, b->st>>>(b->lnvox, b->nf, b->J, b->phi, b->wq, b->eps_l, b->Bl,
                                                                  b->Lbar, b->S_l, b->Jbar, b->maxrel);
     } else {
@@ -287,12 +330,47 @@ int capture(rt_batch *b)
     return RT_OK;
 }
 
+// Nearest-neighbour OS step of the line: (I - (1 - eps_l) Lbar27) dS_l = y by
+// Jacobi sweeps from dS_l = 0 until a sweep changes dS_l by <= 1e-14 max |dS_l|
+// (checked after 4 sweeps, then every 16), then S_l += dS_l and the max rel dS_l.
+int line_nn_os(rt_batch *b)
+{
+    const rt_grid *g = b->grids[0];
+    const int n = b->lnvox;
+    double *xa = b->nnx, *xb = b->nnx + n;
+    BCK(cudaMemsetAsync(xa, 0, sizeof(double) * n, b->st));
+    int m = 0;
+    for (;;) {
+        BCK(cudaMemsetAsync(b->nnmx, 0, 2 * sizeof(unsigned long long), b->st));
+        const int batch = m < 16 ? 4 : 16;
+        for (int q = 0; q < batch; ++q) {
+            BCK(nn_jacobi(n, g->coord == RT_SPHERICAL, g->n1, g->n2, g->n3, b->Lbar27, b->eps_l, b->nny, xa, xb,
+                          b->nnmx, b->st));
+            std::swap(xa, xb);
+            ++m;
+        }
+        unsigned long long h[2];
+        BCK(cudaMemcpyAsync(h, b->nnmx, sizeof(h), cudaMemcpyDeviceToHost, b->st));
+        BCK(cudaStreamSynchronize(b->st));
+        double dmax, xmax;
+        std::memcpy(&dmax, &h[0], sizeof(double));
+        std::memcpy(&xmax, &h[1], sizeof(double));
+        if (!std::isfinite(dmax) || !std::isfinite(xmax)) return bfail(RT_EDEVICE, "line NN OS step diverged");
+        if (!(dmax > 1e-14 * xmax)) break;
+        if (m >= 100000) return bfail(RT_ENOTCONVERGED, "line NN OS step: no convergence in 100000 sweeps");
+    }
+    b->nn_sweeps = m;
+    BCK(nn_apply(n, b->S_l, xa, nullptr, nullptr, b->maxrel, b->st));
+    return RT_OK;
+}
+
 int step(rt_batch *b, double *rel_out)
 {
     for (int m = 0; m < b->nm; ++m)
         if (!b->ready[m]) return bfail(RT_EINVAL, "member " + std::to_string(m) + " has no opacity yet");
     if (!b->graph) BRCK(capture(b));
     BCK(cudaGraphLaunch(b->graph, b->st));
+    if (b->line && b->lstar == RT_LSTAR_NN) BRCK(line_nn_os(b));
     BCK(cudaMemcpyAsync(b->h_maxrel.data(), b->maxrel, sizeof(unsigned long long) * b->nm, cudaMemcpyDeviceToHost,
                         b->st));
     BCK(cudaStreamSynchronize(b->st));
@@ -621,9 +699,13 @@ int rt_batch_autotune(rt_batch *b, int32_t *chunk_out, int32_t *grid_out, double
 
 // ---- two-level-atom line transfer (the members are the frequencies) ----
 
-int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, const double *wq, void *stream)
+int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, const double *wq, int use_lstar,
+                   void *stream)
 {
     if (!out || !g || n_freq < 1 || !phi || !wq) return bfail(RT_EINVAL, "bad arguments");
+    if (use_lstar != RT_LSTAR_DIAG && use_lstar != RT_LSTAR_NN)
+        return bfail(RT_EINVAL, "use_lstar must be RT_LSTAR_DIAG or RT_LSTAR_NN");
+    if (use_lstar == RT_LSTAR_NN && g->nphi < 3) return bfail(RT_EINVAL, "the nearest-neighbour Lambda* needs n_phi >= 3");
     double norm = 0.0;
     for (int k = 0; k < n_freq; ++k) {
         if (!(phi[k] >= 0.0) || !std::isfinite(phi[k]) || !(wq[k] >= 0.0) || !std::isfinite(wq[k]))
@@ -636,9 +718,11 @@ int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, co
     rt_batch *b = nullptr;
     BRCK(rt_batch_create(&b, gs, 1, n_freq, mg.data(), stream));
     b->line = 1;
+    b->lstar = use_lstar;
     b->nf = n_freq;
     b->lnvox = g->nvox;
     b->h_phi.assign(phi, phi + n_freq);
+    b->h_wq.assign(wq, wq + n_freq);
     const int n = g->nvox;
     int rc = RT_OK;
     if ((rc = balloc(b, &b->chi_c, n)) != RT_OK || (rc = balloc(b, &b->chi_l, n)) != RT_OK ||
@@ -646,7 +730,11 @@ int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, co
         (rc = balloc(b, &b->phi, n_freq)) != RT_OK || (rc = balloc(b, &b->wq, n_freq)) != RT_OK ||
         (rc = balloc(b, &b->S_l, n)) != RT_OK || (rc = balloc(b, &b->Jbar, n)) != RT_OK ||
         (rc = balloc(b, &b->Lbar, n)) != RT_OK || (rc = balloc(b, &b->ones, n)) != RT_OK ||
-        (rc = balloc(b, &b->tmp, n)) != RT_OK) {
+        (rc = balloc(b, &b->tmp, n)) != RT_OK ||
+        (use_lstar == RT_LSTAR_NN &&
+         ((rc = balloc(b, &b->Lbar27, 27 * (size_t)n)) != RT_OK || (rc = balloc(b, &b->L27k, 27 * (size_t)n)) != RT_OK ||
+          (rc = balloc(b, &b->nnx, 2 * (size_t)n)) != RT_OK || (rc = balloc(b, &b->nny, n)) != RT_OK ||
+          (rc = balloc(b, &b->nnmx, 2)) != RT_OK))) {
         std::string keep = rt_last_error();
         rt_batch_destroy(b);
         set_last_error(keep.c_str());
@@ -688,6 +776,14 @@ int rt_line_set(rt_batch *b, const double *chi_c, const double *chi_l, const dou
         k_line_chik<<<(n + 255) / 256, 256, 0, b->st>>>(n, b->chi_c, b->chi_l, b->h_phi[k], b->tmp);
         BCK(cudaGetLastError());
         BRCK(batch_set_member(b, k, b->tmp, b->ones, b->Bl, RT_DEVICE));
+        if (b->lstar == RT_LSTAR_NN) {
+            const rt_grid *g = b->grids[0];
+            BRCK(rt_grid_nn_lstar(b->grids[0], b->tmp, b->L27k, b->st));
+            k_line_lbar_nn<<<(n + 127) / 128, 128, 0, b->st>>>(n, g->coord == RT_SPHERICAL, g->n1, g->n2, g->n3, b->L27k,
+                                                                b->chi_c, b->chi_l, b->h_phi[k],
+                                                                b->h_wq[k] * b->h_phi[k], b->Lbar27, k == 0);
+            BCK(cudaGetLastError());
+        }
     }
     k_line_lbar<<<(n + 255) / 256, 256, 0, b->st>>>(n, b->nf, b->L, b->chi, b->chi_l, b->phi, b->wq, b->Lbar);
     BCK(cudaGetLastError());
@@ -729,10 +825,10 @@ int rt_line_get(const rt_batch *b, int what, double *out, int where)
     if (!b || !out) return bfail(RT_EINVAL, "NULL argument");
     if (!b->line) return bfail(RT_EINVAL, "not a line problem (rt_line_create)");
     if (where != RT_HOST && where != RT_DEVICE) return bfail(RT_EINVAL, "where must be RT_HOST or RT_DEVICE");
-    const double *src = what == 0 ? b->S_l : what == 1 ? b->Jbar : what == 2 ? b->Lbar : nullptr;
-    if (!src) return bfail(RT_EINVAL, "what must be 0 (S_l), 1 (Jbar) or 2 (Lbar*)");
+    const double *src = what == 0 ? b->S_l : what == 1 ? b->Jbar : what == 2 ? b->Lbar : what == 3 ? b->Lbar27 : nullptr;
+    if (!src) return bfail(RT_EINVAL, "what must be 0 (S_l), 1 (Jbar), 2 (Lbar*) or 3 (Lbar*_NN of a NN line)");
     BCK(cudaSetDevice(b->device));
-    BCK(cudaMemcpyAsync(out, src, sizeof(double) * b->lnvox,
+    BCK(cudaMemcpyAsync(out, src, sizeof(double) * b->lnvox * (what == 3 ? 27 : 1),
                         where == RT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, b->st));
     BCK(cudaStreamSynchronize(b->st));
     return RT_OK;

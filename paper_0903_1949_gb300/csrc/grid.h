@@ -113,3 +113,8 @@ struct rt_grid {
 // Writes J, Lambda* and the Cartesian flux sums Fc; returns an RT_ status.
 int rt_grid_member_fs(rt_grid *g, const float2 *cs, const float *B32, const uint32_t *pbits, double *J, double *L,
                       double *Fc, cudaStream_t st);
+
+// The exact nearest-neighbour Lambda* (27 entries per voxel, slot q = 9 (di+1) +
+// 3 (dj+1) + (dk+1), phi periodic) of another opacity field chi on this grid's
+// geometry, into L27; runs on st and returns after it has drained.
+int rt_grid_nn_lstar(rt_grid *g, const double *chi, double *L27, cudaStream_t st);

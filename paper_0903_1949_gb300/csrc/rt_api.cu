@@ -1038,9 +1038,10 @@ int ng_maybe(rt_grid *g, double *out, const double *wref)
 // Nearest-neighbour Lambda* of the current chi (FP64, once per chi): per
 // angle block, a walker thread per characteristic and a per-voxel sum in list
 // order; the diagonal is copied to d_L.
-int build_nn(rt_grid *g)
+// The exact nearest-neighbour Lambda* of opacity chi (device, n_vox) into L27
+// (device, 27 n_vox), on stream st; returns after the stream has drained.
+int nn_lstar_into(rt_grid *g, const double *chi, double *L27, cudaStream_t st)
 {
-    if (g->nn_ok) return RT_OK;
     const int n = g->nvox;
     int8_t *slot = nullptr;
     double *val = nullptr;
@@ -1052,12 +1053,14 @@ int build_nn(rt_grid *g)
     }
     struct Free {
         void *a, *b;
+        cudaStream_t st;
         ~Free()
         {
+            cudaStreamSynchronize(st);  // no launch may still use them
             cudaFree(a);
             cudaFree(b);
         }
-    } fr{slot, val};
+    } fr{slot, val, st};
     for (int b = 0; b < g->nblk; ++b) {
         const int w0 = g->blk_w0[b], nw = g->blk_nw[b];
         NnWalk a{};
@@ -1068,7 +1071,7 @@ int build_nn(rt_grid *g)
         a.r_lo = g->h_ang_ray_off[w0];
         a.r_hi = g->h_ang_ray_off[w0 + nw];
         a.seg_lo = g->h_ang_seg_off[w0];
-        a.chi = g->d_chi;
+        a.chi = chi;
         a.wt = g->d_wt;
         a.invL = g->d_invL;
         a.nvox = n;
@@ -1077,13 +1080,21 @@ int build_nn(rt_grid *g)
         a.sph = g->coord == RT_SPHERICAL;
         a.slot = slot;
         a.val = val;
-        CK(nn_walk(a, g->st));
-        CK(nn_gather(n, g->d_csr_off + (size_t)b * (n + 1), g->d_perm + a.seg_lo, slot, val, g->d_L27, b == 0, g->st));
+        CK(nn_walk(a, st));
+        CK(nn_gather(n, g->d_csr_off + (size_t)b * (n + 1), g->d_perm + a.seg_lo, slot, val, L27, b == 0, st));
         g->launches += 2;
     }
-    CK(nn_diag(n, g->d_L27, g->d_L, g->st));
+    CK(cudaStreamSynchronize(st));
+    return RT_OK;
+}
+
+int build_nn(rt_grid *g)
+{
+    if (g->nn_ok) return RT_OK;
+    RCK(nn_lstar_into(g, g->d_chi, g->d_L27, g->st));
+    CK(nn_diag(g->nvox, g->d_L27, g->d_L, g->st));
     g->launches++;
-    RCK(sync(g));  // the work arrays are freed on return
+    RCK(sync(g));
     g->nn_ok = true;
     g->lstar_prec = RT_FP64;
     return RT_OK;
@@ -1172,6 +1183,12 @@ int check_lost(rt_grid *g)
 }
 
 }  // namespace
+
+int rt_grid_nn_lstar(rt_grid *g, const double *chi, double *L27, cudaStream_t st)
+{
+    if (g->nphi < 3) return fail(RT_EINVAL, "the nearest-neighbour Lambda* needs n_phi >= 3");
+    return nn_lstar_into(g, chi, L27, st);
+}
 
 int rt_grid_member_fs(rt_grid *g, const float2 *cs, const float *B32, const uint32_t *pbits, double *J, double *L,
                       double *Fc, cudaStream_t st)

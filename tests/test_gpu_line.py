@@ -49,8 +49,8 @@ def _case(name):
     return p
 
 
-def _line(p, g):
-    ln = rt.Line(g, p["phi"], p["wq"])
+def _line(p, g, use_lstar=rt.RT_LSTAR_DIAG):
+    ln = rt.Line(g, p["phi"], p["wq"], use_lstar)
     ln.set(p["chi_c"], p["chi_l"], p["eps_l"], p["B"])
     return ln
 
@@ -177,6 +177,52 @@ def test_autotune_restores_the_line_source():
     g.close()
 
 
+@pytest.mark.parametrize("name", ["sph_core", "cyl_hole", "sph17"])
+def test_nn_line_operator_and_iterates_match_oracle(name):
+    """Nearest-neighbour line operator (exact, FP64) entry by entry, and the
+    iterates of the NN line ALI at the mixed-precision bar."""
+    p = _case(name)
+    p["eps_l"] = np.full(p["nvox"], 0.05)
+    o = _oracle(p)
+    g = _grid(p)
+    ln = _line(p, g, rt.RT_LSTAR_NN)
+    L_o = OL.line_lbar_nn(o, p["chi_c"], p["chi_l"], p["phi"], p["wq"])
+    scale = np.max(np.abs(L_o))
+    assert np.max(np.abs(ln.Lbar_nn() - L_o)) <= 1e-13 * scale, float(np.max(np.abs(ln.Lbar_nn() - L_o)) / scale)
+    steps = 5
+    rel = [ln.step() for _ in range(steps)]
+    S_o, _, h_o = OL.line_solve(o, p["chi_c"], p["chi_l"], p["eps_l"], p["B"], p["phi"], p["wq"], tol=0.0,
+                                max_iter=steps, use_lstar=2)
+    assert np.max(np.abs(ln.S_l() - S_o) / np.abs(S_o)) < MIXED
+    assert np.allclose(rel[:3], h_o[:3], rtol=1e-3, atol=0)
+    ln.close()
+    g.close()
+
+
+def test_nn_line_converges_faster_to_the_same_fixed_point():
+    """eps_l = 1e-3 with the line centre at tau ~ 3e2: the NN line operator needs
+    far fewer iterations than the diagonal one, to the oracle's fixed point."""
+    p = I.line_problem("sph17", n_freq=8, ratio=3e4, eps_l=1e-3)
+    o = _oracle(p)
+    S_o, it_o, _ = OL.line_solve(o, p["chi_c"], p["chi_l"], p["eps_l"], p["B"], p["phi"], p["wq"], tol=1e-10,
+                                 max_iter=400, use_lstar=2)
+    assert it_o > 0
+    g = _grid(p)
+    out = {}
+    ln = _line(p, g, rt.RT_LSTAR_NN)
+    out[rt.RT_LSTAR_NN] = ln.solve(1e-6, 150) + (ln.S_l(),)
+    ln.close()
+    ln = _line(p, g, rt.RT_LSTAR_DIAG)
+    out[rt.RT_LSTAR_DIAG] = ln.solve(1e-6, 3 * out[rt.RT_LSTAR_NN][0])
+    ln.close()
+    it_nn, ok_nn, S_nn = out[rt.RT_LSTAR_NN]
+    assert ok_nn, it_nn
+    assert not out[rt.RT_LSTAR_DIAG][1], (it_nn, out[rt.RT_LSTAR_DIAG])
+    # converged: the FP32 formal solutions' error, amplified at most by the OS operator
+    assert np.max(np.abs(S_nn - S_o) / np.abs(S_o)) < 1e-3
+    g.close()
+
+
 def test_line_argument_checks():
     p = _case("sph_core")
     n = p["nvox"]
@@ -197,9 +243,12 @@ def test_line_argument_checks():
     z.close()
     ln.set(p["chi_c"], p["chi_l"], p["eps_l"], p["B"])
     for call in (lambda: ln.ali_step(), lambda: ln.set_member(0, p["chi"], p["eps"], p["B"]),
-                 lambda: rt.rt_line_get(ln.h, 3, n)):
+                 lambda: rt.rt_line_get(ln.h, 3, 27 * n), lambda: rt.rt_line_get(ln.h, 4, n)):
         with pytest.raises(rt.RtError) as ei:
             call()
         assert ei.value.code == rt.RT_EINVAL
     ln.close()
+    with pytest.raises(rt.RtError) as ei:
+        rt.Line(g, p["phi"], p["wq"], use_lstar=rt.RT_LSTAR_NONE)
+    assert ei.value.code == rt.RT_EINVAL
     g.close()
