@@ -24,6 +24,7 @@ the factor taken at the neighbour u, and the OS step solves
 """
 import numpy as np
 
+from oracle import oracle as O
 from oracle.oracle import SPH
 
 
@@ -85,9 +86,12 @@ def line_jbar(o, S_l, chi_c, chi_l, B, phi, wq):
     return Jbar
 
 
-def line_solve(o, chi_c, chi_l, eps_l, B, phi, wq, tol=1e-10, max_iter=500, S0=None, use_lstar=1, jtol=1e-14):
+def line_solve(o, chi_c, chi_l, eps_l, B, phi, wq, tol=1e-10, max_iter=500, S0=None, use_lstar=1, jtol=1e-14,
+               ng=False):
     """Two-level ALI to max rel dS_l < tol from S0 (default B), with the diagonal
-    (use_lstar=1) or nearest-neighbour (2) line operator.
+    (use_lstar=1) or nearest-neighbour (2) line operator; ng: order-2 Ng
+    extrapolation of S_l whenever four iterates have accumulated since the last
+    one (R11, as the continuum solve).
     Returns (S_l, iterations (negative: not converged), history of max rel dS_l)."""
     S = np.array(B if S0 is None else S0, dtype=np.float64, copy=True)
     if use_lstar == 2:
@@ -95,6 +99,7 @@ def line_solve(o, chi_c, chi_l, eps_l, B, phi, wq, tol=1e-10, max_iter=500, S0=N
     else:
         Lbar = line_lbar(o, chi_c, chi_l, B, phi, wq)
     hist = []
+    H = []
     for it in range(1, max_iter + 1):
         Jbar = line_jbar(o, S, chi_c, chi_l, B, phi, wq)
         if use_lstar == 2:
@@ -106,4 +111,11 @@ def line_solve(o, chi_c, chi_l, eps_l, B, phi, wq, tol=1e-10, max_iter=500, S0=N
         hist.append(rel)
         if rel < tol:
             return S, it, np.array(hist)
+        if ng:
+            H = (H + [S.copy()])[-4:]
+            if len(H) == 4:
+                Sx = O.ng(H[3], H[2], H[1], H[0])
+                if Sx is not None:
+                    S = Sx
+                    H = []
     return S, -max_iter, np.array(hist)

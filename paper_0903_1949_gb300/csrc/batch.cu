@@ -778,7 +778,7 @@ int rt_line_set(rt_batch *b, const double *chi_c, const double *chi_l, const dou
         BRCK(batch_set_member(b, k, b->tmp, b->ones, b->Bl, RT_DEVICE));
         if (b->lstar == RT_LSTAR_NN) {
             const rt_grid *g = b->grids[0];
-            BRCK(rt_grid_nn_lstar(b->grids[0], b->tmp, b->L27k, b->st));
+            BRCK(rt_grid_nn_lstar(b->grids[0], b->tmp, b->pbits[k], b->L27k, b->st));
             k_line_lbar_nn<<<(n + 127) / 128, 128, 0, b->st>>>(n, g->coord == RT_SPHERICAL, g->n1, g->n2, g->n3, b->L27k,
                                                                 b->chi_c, b->chi_l, b->h_phi[k],
                                                                 b->h_wq[k] * b->h_phi[k], b->Lbar27, k == 0);

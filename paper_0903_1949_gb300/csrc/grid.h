@@ -115,6 +115,7 @@ int rt_grid_member_fs(rt_grid *g, const float2 *cs, const float *B32, const uint
                       double *Fc, cudaStream_t st);
 
 // The exact nearest-neighbour Lambda* (27 entries per voxel, slot q = 9 (di+1) +
-// 3 (dj+1) + (dk+1), phi periodic) of another opacity field chi on this grid's
+// 3 (dj+1) + (dk+1), phi periodic) of another opacity field chi, with its
+// parabola choices pbits (bit per segment, as para_bits), on this grid's
 // geometry, into L27; runs on st and returns after it has drained.
-int rt_grid_nn_lstar(rt_grid *g, const double *chi, double *L27, cudaStream_t st);
+int rt_grid_nn_lstar(rt_grid *g, const double *chi, const uint32_t *pbits, double *L27, cudaStream_t st);

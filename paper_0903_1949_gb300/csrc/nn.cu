@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(128) k_nn_walk(NnWalk a)
     for (int64_t s = s0; s < s1; ++s) {
         const uint32_t w = a.vox[s];
         const int v = (int)(w & RTK_VOXMASK);
-        const bool para = (w & RTK_PARA) != 0u;
+        const bool para = a.pbits ? ((a.pbits[s >> 5] >> (s & 31)) & 1u) != 0u : (w & RTK_PARA) != 0u;
         const bool run0 = (w & (RTK_RAYSTART | RTK_RESTART)) != 0u;
         const double x = a.chi[v] * a.len64[s];
         int vn = -1;

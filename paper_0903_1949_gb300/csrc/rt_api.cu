@@ -1038,9 +1038,11 @@ int ng_maybe(rt_grid *g, double *out, const double *wref)
 // Nearest-neighbour Lambda* of the current chi (FP64, once per chi): per
 // angle block, a walker thread per characteristic and a per-voxel sum in list
 // order; the diagonal is copied to d_L.
-// The exact nearest-neighbour Lambda* of opacity chi (device, n_vox) into L27
-// (device, 27 n_vox), on stream st; returns after the stream has drained.
-int nn_lstar_into(rt_grid *g, const double *chi, double *L27, cudaStream_t st)
+// The exact nearest-neighbour Lambda* of opacity chi (device, n_vox) with the
+// parabola choices pbits (NULL: those marked in the crossing words for the
+// grid's own chi) into L27 (device, 27 n_vox), on stream st; returns after the
+// stream has drained.
+int nn_lstar_into(rt_grid *g, const double *chi, const uint32_t *pbits, double *L27, cudaStream_t st)
 {
     const int n = g->nvox;
     int8_t *slot = nullptr;
@@ -1072,6 +1074,7 @@ int nn_lstar_into(rt_grid *g, const double *chi, double *L27, cudaStream_t st)
         a.r_hi = g->h_ang_ray_off[w0 + nw];
         a.seg_lo = g->h_ang_seg_off[w0];
         a.chi = chi;
+        a.pbits = pbits;
         a.wt = g->d_wt;
         a.invL = g->d_invL;
         a.nvox = n;
@@ -1091,7 +1094,7 @@ int nn_lstar_into(rt_grid *g, const double *chi, double *L27, cudaStream_t st)
 int build_nn(rt_grid *g)
 {
     if (g->nn_ok) return RT_OK;
-    RCK(nn_lstar_into(g, g->d_chi, g->d_L27, g->st));
+    RCK(nn_lstar_into(g, g->d_chi, nullptr, g->d_L27, g->st));
     CK(nn_diag(g->nvox, g->d_L27, g->d_L, g->st));
     g->launches++;
     RCK(sync(g));
@@ -1184,10 +1187,11 @@ int check_lost(rt_grid *g)
 
 }  // namespace
 
-int rt_grid_nn_lstar(rt_grid *g, const double *chi, double *L27, cudaStream_t st)
+int rt_grid_nn_lstar(rt_grid *g, const double *chi, const uint32_t *pbits, double *L27, cudaStream_t st)
 {
     if (g->nphi < 3) return fail(RT_EINVAL, "the nearest-neighbour Lambda* needs n_phi >= 3");
-    return nn_lstar_into(g, chi, L27, st);
+    if (!pbits) return fail(RT_EINVAL, "parabola choices of chi required");
+    return nn_lstar_into(g, chi, pbits, L27, st);
 }
 
 int rt_grid_member_fs(rt_grid *g, const float2 *cs, const float *B32, const uint32_t *pbits, double *J, double *L,

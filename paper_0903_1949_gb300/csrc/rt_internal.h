@@ -281,6 +281,7 @@ struct NnWalk {
     const int32_t *ray_angle;
     int64_t r_lo, r_hi, seg_lo;  // characteristics of one angle block; segments relative to seg_lo
     const double *chi, *wt, *invL;
+    const uint32_t *pbits;       // parabola choices of chi, bit per segment; NULL: the RTK_PARA bits of vox
     int nvox, n2, n3, sph;
     int8_t *slot;                // RTK_NNW per segment: neighbour slot of v_s or -1
     double *val;                 // RTK_NNW per segment: w l / L times dI_s/dS_u

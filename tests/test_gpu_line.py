@@ -200,26 +200,29 @@ def test_nn_line_operator_and_iterates_match_oracle(name):
 
 
 def test_nn_line_converges_faster_to_the_same_fixed_point():
-    """eps_l = 1e-3 with the line centre at tau ~ 3e2: the NN line operator needs
-    far fewer iterations than the diagonal one, to the oracle's fixed point."""
-    p = I.line_problem("sph17", n_freq=8, ratio=3e4, eps_l=1e-3)
+    """eps_l = 1e-2 with the line centre at tau ~ 3e2: the NN line operator needs
+    a fraction of the diagonal one's iterations (the oracle: 28 against 97 to
+    1e-5), to the oracle's fixed point."""
+    p = I.line_problem("sph17", n_freq=8, ratio=3e4, eps_l=1e-2)
     o = _oracle(p)
-    S_o, it_o, _ = OL.line_solve(o, p["chi_c"], p["chi_l"], p["eps_l"], p["B"], p["phi"], p["wq"], tol=1e-10,
-                                 max_iter=400, use_lstar=2)
+    S_o, it_o, h_o = OL.line_solve(o, p["chi_c"], p["chi_l"], p["eps_l"], p["B"], p["phi"], p["wq"], tol=1e-8,
+                                   max_iter=400, use_lstar=2)
     assert it_o > 0
+    tol = 1e-5
+    it_o5 = int(np.argmax(h_o < tol)) + 1
     g = _grid(p)
-    out = {}
     ln = _line(p, g, rt.RT_LSTAR_NN)
-    out[rt.RT_LSTAR_NN] = ln.solve(1e-6, 150) + (ln.S_l(),)
+    it_nn, ok_nn = ln.solve(tol, 150)
+    S_nn = ln.S_l()
     ln.close()
-    ln = _line(p, g, rt.RT_LSTAR_DIAG)
-    out[rt.RT_LSTAR_DIAG] = ln.solve(1e-6, 3 * out[rt.RT_LSTAR_NN][0])
-    ln.close()
-    it_nn, ok_nn, S_nn = out[rt.RT_LSTAR_NN]
     assert ok_nn, it_nn
-    assert not out[rt.RT_LSTAR_DIAG][1], (it_nn, out[rt.RT_LSTAR_DIAG])
-    # converged: the FP32 formal solutions' error, amplified at most by the OS operator
-    assert np.max(np.abs(S_nn - S_o) / np.abs(S_o)) < 1e-3
+    assert abs(it_nn - it_o5) <= max(3, 0.15 * it_o5), (it_nn, it_o5)
+    ln = _line(p, g, rt.RT_LSTAR_DIAG)
+    it_d, ok_d = ln.solve(tol, 2 * it_nn)
+    ln.close()
+    assert not ok_d, (it_nn, it_d)
+    # within tol of convergence, plus the FP32 formal solutions' error amplified by the OS operator
+    assert np.max(np.abs(S_nn - S_o) / np.abs(S_o)) < 2e-4
     g.close()
 
 

@@ -140,3 +140,31 @@ def test_single_frequency_nn_line_is_the_continuum_nn_ali():
     S_cont, _, h_cont = o.solve(p["chi"], eps, p["B"], tol=0.0, max_iter=4, use_lstar=2, ng=False)
     assert np.max(np.abs(S_line - S_cont) / np.abs(S_cont)) < 1e-14
     assert np.allclose(h_line, h_cont, rtol=1e-12, atol=0)
+
+
+def test_single_frequency_line_with_ng_is_the_continuum_ali_with_ng():
+    """Ng on S_l follows the continuum solve's Ng step for step (n_freq = 1, no continuum)."""
+    p = tiny_problem(I.SPHERICAL, (5, 4, 6), 4, 4, I.CORE_B, seed=47)
+    o = grid(p)
+    n = p["nvox"]
+    eps = np.full(n, 0.01)
+    for lstar in (1, 2):
+        S_line, _, h_line = OL.line_solve(o, np.zeros(n), p["chi"], eps, p["B"], np.ones(1), np.ones(1), tol=0.0,
+                                          max_iter=10, use_lstar=lstar, ng=True)
+        S_cont, _, h_cont = o.solve(p["chi"], eps, p["B"], tol=0.0, max_iter=10, use_lstar=lstar, ng=True)
+        assert np.max(np.abs(S_line - S_cont) / np.abs(S_cont)) < 1e-13, lstar
+        assert np.allclose(h_line, h_cont, rtol=1e-6, atol=0)  # late dS: differences of near-equal S
+
+
+def test_ng_line_reaches_the_same_fixed_point_in_fewer_iterations():
+    p = tiny_problem(I.CYLINDRICAL, (4, 5, 3), 4, 4, I.TRANSPARENT, seed=48)
+    o = grid(p)
+    n = p["nvox"]
+    phi, w = I.line_profile(3, span=2.0)
+    chi_c = 0.05 * p["chi"]
+    chi_l = 400.0 * chi_c
+    eps = np.full(n, 1e-3)
+    S0, it0, _ = OL.line_solve(o, chi_c, chi_l, eps, p["B"], phi, w, tol=1e-12, max_iter=5000, use_lstar=1)
+    S1, it1, _ = OL.line_solve(o, chi_c, chi_l, eps, p["B"], phi, w, tol=1e-12, max_iter=5000, use_lstar=1, ng=True)
+    assert 0 < it1 < it0 / 2, (it1, it0)
+    assert np.max(np.abs(S1 - S0) / np.abs(S0)) < 1e-9
