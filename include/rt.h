@@ -351,9 +351,12 @@ int rt_batch_autotune(rt_batch *b, int32_t *chunk_out, int32_t *grid_out, double
  * Lambda* (as rt_get_Lstar_nn), and each iteration solves
  * (I - (1 - eps_l) Lbar*) dS_l = (1 - eps_l) Jbar + eps_l B - S_l by Jacobi
  * sweeps to a sweep change <= 1e-14 max |dS_l| after the graph.  use_lstar
- * other than RT_LSTAR_DIAG / RT_LSTAR_NN is RT_EINVAL.
+ * other than RT_LSTAR_DIAG / RT_LSTAR_NN is RT_EINVAL.  ng = 1 applies order-2
+ * Ng extrapolation to S_l whenever four iterates have accumulated since the
+ * last one (as rt_ali_step; rt_line_solve skips it once tol is met); ng other
+ * than 0 / 1 is RT_EINVAL.
  * The grid must outlive the problem; it is used on the problem's stream. */
-int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, const double *wq, int use_lstar,
+int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, const double *wq, int use_lstar, int ng,
                    void *stream);
 
 /* chi_c, chi_l (>= 0, with chi_c + chi_l phi_k > 0 for every k), eps_l in
@@ -363,7 +366,8 @@ int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, co
 int rt_line_set(rt_batch *b, const double *chi_c, const double *chi_l, const double *eps_l, const double *B,
                 int where);
 
-/* One iteration; max_rel_dSl (may be NULL) gets max_v |dS_l| / |S_l|. */
+/* One iteration (then Ng, if enabled and due); max_rel_dSl (may be NULL) gets
+ * max_v |dS_l| / |S_l| of the ALI update. */
 int rt_line_step(rt_batch *b, double *max_rel_dSl);
 
 /* Iterate until max rel dS_l < tol (RT_ENOTCONVERGED after max_iter);

@@ -220,6 +220,9 @@ struct rt_batch {
     double *Lbar27 = nullptr, *L27k = nullptr, *nnx = nullptr, *nny = nullptr;
     unsigned long long *nnmx = nullptr;
     int nn_sweeps = 0;
+    int ng = 0;  // Ng extrapolation of S_l
+    double *H = nullptr, *ng_part = nullptr, *ng_coef = nullptr;
+    int hs[4] = {0, 1, 2, 3}, nh = 0;
 };
 
 namespace {
@@ -361,6 +364,31 @@ int line_nn_os(rt_batch *b)
     }
     b->nn_sweeps = m;
     BCK(nn_apply(n, b->S_l, xa, nullptr, nullptr, b->maxrel, b->st));
+    return RT_OK;
+}
+
+// Ng of the line: S_l joins the four-iterate history; once four have
+// accumulated since the last extrapolation, S_l is replaced by the order-2 Ng
+// combination (when its 2x2 system is regular).
+int line_ng(rt_batch *b)
+{
+    const size_t n = b->lnvox;
+    if (b->nh == 4) {
+        const int t = b->hs[0];
+        b->hs[0] = b->hs[1];
+        b->hs[1] = b->hs[2];
+        b->hs[2] = b->hs[3];
+        b->hs[3] = t;
+        b->nh = 3;
+    }
+    BCK(cudaMemcpyAsync(b->H + b->hs[b->nh] * n, b->S_l, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->st));
+    if (++b->nh < 4) return RT_OK;
+    BCK(ng_extrapolate(b->lnvox, b->H + b->hs[3] * n, b->H + b->hs[2] * n, b->H + b->hs[1] * n, b->H + b->hs[0] * n,
+                       nullptr, b->ng_part, b->ng_coef, b->S_l, b->st));
+    double applied = 0.0;
+    BCK(cudaMemcpyAsync(&applied, b->ng_coef + 2, sizeof(double), cudaMemcpyDeviceToHost, b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    if (applied != 0.0) b->nh = 0;
     return RT_OK;
 }
 
@@ -699,12 +727,13 @@ int rt_batch_autotune(rt_batch *b, int32_t *chunk_out, int32_t *grid_out, double
 
 // ---- two-level-atom line transfer (the members are the frequencies) ----
 
-int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, const double *wq, int use_lstar,
+int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, const double *wq, int use_lstar, int ng,
                    void *stream)
 {
     if (!out || !g || n_freq < 1 || !phi || !wq) return bfail(RT_EINVAL, "bad arguments");
     if (use_lstar != RT_LSTAR_DIAG && use_lstar != RT_LSTAR_NN)
         return bfail(RT_EINVAL, "use_lstar must be RT_LSTAR_DIAG or RT_LSTAR_NN");
+    if (ng != 0 && ng != 1) return bfail(RT_EINVAL, "ng must be 0 or 1");
     if (use_lstar == RT_LSTAR_NN && g->nphi < 3) return bfail(RT_EINVAL, "the nearest-neighbour Lambda* needs n_phi >= 3");
     double norm = 0.0;
     for (int k = 0; k < n_freq; ++k) {
@@ -719,6 +748,7 @@ int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, co
     BRCK(rt_batch_create(&b, gs, 1, n_freq, mg.data(), stream));
     b->line = 1;
     b->lstar = use_lstar;
+    b->ng = ng;
     b->nf = n_freq;
     b->lnvox = g->nvox;
     b->h_phi.assign(phi, phi + n_freq);
@@ -734,7 +764,10 @@ int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, co
         (use_lstar == RT_LSTAR_NN &&
          ((rc = balloc(b, &b->Lbar27, 27 * (size_t)n)) != RT_OK || (rc = balloc(b, &b->L27k, 27 * (size_t)n)) != RT_OK ||
           (rc = balloc(b, &b->nnx, 2 * (size_t)n)) != RT_OK || (rc = balloc(b, &b->nny, n)) != RT_OK ||
-          (rc = balloc(b, &b->nnmx, 2)) != RT_OK))) {
+          (rc = balloc(b, &b->nnmx, 2)) != RT_OK)) ||
+        (ng && ((rc = balloc(b, &b->H, 4 * (size_t)n)) != RT_OK ||
+                (rc = balloc(b, &b->ng_part, ng_partial_elems(n))) != RT_OK ||
+                (rc = balloc(b, &b->ng_coef, 4)) != RT_OK))) {
         std::string keep = rt_last_error();
         rt_batch_destroy(b);
         set_last_error(keep.c_str());
@@ -791,6 +824,17 @@ int rt_line_set(rt_batch *b, const double *chi_c, const double *chi_l, const dou
     BCK(cudaStreamSynchronize(b->st));
     b->line_ready = true;
     b->history.clear();
+    b->nh = 0;
+    return RT_OK;
+}
+
+// One line iteration; Ng follows unless the iterate has met tol.
+int line_iterate(rt_batch *b, double tol, double *rel_out)
+{
+    std::vector<double> rel(b->nm);
+    BRCK(step(b, rel.data()));
+    *rel_out = rel[0];
+    if (b->ng && !(rel[0] < tol)) BRCK(line_ng(b));
     return RT_OK;
 }
 
@@ -800,20 +844,24 @@ int rt_line_step(rt_batch *b, double *max_rel_dSl)
     if (!b->line) return bfail(RT_EINVAL, "not a line problem (rt_line_create)");
     if (!b->line_ready) return bfail(RT_EINVAL, "rt_line_set first");
     BCK(cudaSetDevice(b->device));
-    std::vector<double> rel(b->nm);
-    BRCK(step(b, rel.data()));
-    if (max_rel_dSl) *max_rel_dSl = rel[0];
+    double rel = 0.0;
+    BRCK(line_iterate(b, 0.0, &rel));
+    if (max_rel_dSl) *max_rel_dSl = rel;
     return RT_OK;
 }
 
 int rt_line_solve(rt_batch *b, double tol, int max_iter, int32_t *iters)
 {
     if (!b) return bfail(RT_EINVAL, "batch is NULL");
+    if (!b->line) return bfail(RT_EINVAL, "not a line problem (rt_line_create)");
+    if (!b->line_ready) return bfail(RT_EINVAL, "rt_line_set first");
     if (!(tol > 0.0) || max_iter < 1) return bfail(RT_EINVAL, "need tol > 0 and max_iter >= 1");
+    BCK(cudaSetDevice(b->device));
     if (iters) *iters = 0;
+    b->nh = 0;
     for (int it = 1; it <= max_iter; ++it) {
         double rel = 0.0;
-        BRCK(rt_line_step(b, &rel));
+        BRCK(line_iterate(b, tol, &rel));
         if (iters) *iters = it;
         if (rel < tol) return RT_OK;
     }

@@ -104,7 +104,7 @@ def load():
         "rt_get_timing": [_P, ctypes.POINTER(rt_timing)],
         "rt_adjoint": [_P, _P, _P, _P, ctypes.c_double, _I, _P, _P, _P, _I, ctypes.POINTER(_I)],
         "rt_get_Lstar_nn": [_P, _P, _I],
-        "rt_line_create": [ctypes.POINTER(_P), _P, _I, _P, _P, _I, _P],
+        "rt_line_create": [ctypes.POINTER(_P), _P, _I, _P, _P, _I, _I, _P],
         "rt_line_set": [_P, _P, _P, _P, _P, _I],
         "rt_line_step": [_P, _P],
         "rt_line_solve": [_P, ctypes.c_double, _I, ctypes.POINTER(ctypes.c_int32)],
@@ -419,14 +419,15 @@ class Batch:
         return rt_batch_autotune(self.h)
 
 
-def rt_line_create(grid_handle, phi, wq, use_lstar=RT_LSTAR_DIAG, stream=None):
+def rt_line_create(grid_handle, phi, wq, use_lstar=RT_LSTAR_DIAG, ng=False, stream=None):
     phi = np.ascontiguousarray(phi, dtype=np.float64)
     wq = np.ascontiguousarray(wq, dtype=np.float64)
     if phi.shape != wq.shape or phi.ndim != 1:
         raise ValueError("phi and wq: one value per frequency each")
     h = ctypes.c_void_p()
     _check(load().rt_line_create(ctypes.byref(h), grid_handle, int(phi.size), ctypes.c_void_p(phi.ctypes.data),
-                                 ctypes.c_void_p(wq.ctypes.data), int(use_lstar), stream if stream else None))
+                                 ctypes.c_void_p(wq.ctypes.data), int(use_lstar), int(ng),
+                                 stream if stream else None))
     return h
 
 
@@ -458,11 +459,11 @@ def rt_line_get(h, what, n_vox, out=None):
 class Line(Batch):
     """Two-level-atom line on one grid, one batch member per frequency (see rt_line_* in rt.h)."""
 
-    def __init__(self, grid, phi, wq, use_lstar=RT_LSTAR_DIAG, stream=None):
+    def __init__(self, grid, phi, wq, use_lstar=RT_LSTAR_DIAG, ng=False, stream=None):
         self.grids = [grid]
         self.member_grid = [0] * len(phi)
         self.h = None
-        self.h = rt_line_create(grid.h, phi, wq, use_lstar, stream)
+        self.h = rt_line_create(grid.h, phi, wq, use_lstar, ng, stream)
         self.nvox = [grid.nvox] * len(phi)
         self.n = grid.nvox
 

@@ -49,8 +49,8 @@ def _case(name):
     return p
 
 
-def _line(p, g, use_lstar=rt.RT_LSTAR_DIAG):
-    ln = rt.Line(g, p["phi"], p["wq"], use_lstar)
+def _line(p, g, use_lstar=rt.RT_LSTAR_DIAG, ng=False):
+    ln = rt.Line(g, p["phi"], p["wq"], use_lstar, ng)
     ln.set(p["chi_c"], p["chi_l"], p["eps_l"], p["B"])
     return ln
 
@@ -226,6 +226,24 @@ def test_nn_line_converges_faster_to_the_same_fixed_point():
     g.close()
 
 
+@pytest.mark.parametrize("lstar", [rt.RT_LSTAR_DIAG, rt.RT_LSTAR_NN])
+def test_line_with_ng_matches_oracle(lstar):
+    """Ng on S_l (every fourth iterate) step by step against the oracle's."""
+    p = _case("sph_core")
+    p["eps_l"] = np.full(p["nvox"], 0.02)
+    o = _oracle(p)
+    g = _grid(p)
+    ln = _line(p, g, lstar, ng=True)
+    steps = 10
+    rel = [ln.step() for _ in range(steps)]
+    S_o, _, h_o = OL.line_solve(o, p["chi_c"], p["chi_l"], p["eps_l"], p["B"], p["phi"], p["wq"], tol=0.0,
+                                max_iter=steps, use_lstar=2 if lstar == rt.RT_LSTAR_NN else 1, ng=True)
+    assert np.max(np.abs(ln.S_l() - S_o) / np.abs(S_o)) < 2e-5
+    assert np.allclose(rel[:4], h_o[:4], rtol=1e-3, atol=0)
+    ln.close()
+    g.close()
+
+
 def test_line_argument_checks():
     p = _case("sph_core")
     n = p["nvox"]
@@ -253,5 +271,8 @@ def test_line_argument_checks():
     ln.close()
     with pytest.raises(rt.RtError) as ei:
         rt.Line(g, p["phi"], p["wq"], use_lstar=rt.RT_LSTAR_NONE)
+    assert ei.value.code == rt.RT_EINVAL
+    with pytest.raises(rt.RtError) as ei:
+        rt.rt_line_create(g.h, p["phi"], p["wq"], rt.RT_LSTAR_DIAG, 2)
     assert ei.value.code == rt.RT_EINVAL
     g.close()
