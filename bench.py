@@ -388,7 +388,8 @@ def main():
                        "angle_block": info["angle_block"], "l2": "inputs larger than L2 (crossing lists %.1f GB "
                        "streamed per step)" % (info["n_segments"] * bytes_per_seg / 1e9),
                        "parallelism": "replicas" if world > 1 else "1 GPU",
-                       "geometry_ms": info["geometry_ms"], "device_gb": info["device_bytes"] / 1e9},
+                       "geometry_ms": info["geometry_ms"], "geometry_trace_ms": info["geometry_trace_ms"],
+                       "geometry_lists_ms": info["geometry_lists_ms"], "device_gb": info["device_bytes"] / 1e9},
             "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "steps": k64,
                      "mixed_over_fp64": value / value64,
                      "path": "FP64 march with FP64 weights streamed per chi (48 B per segment), FP64 gather",

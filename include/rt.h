@@ -106,6 +106,8 @@ typedef struct rt_info {
     int32_t lost_rays;      /* characteristics that could not be tracked (0 expected) */
     int32_t precision;
     double geometry_ms;     /* wall time of the characteristic geometry at create */
+    double geometry_trace_ms; /* of which: coverage, characteristics and crossing lists */
+    double geometry_lists_ms; /* of which: ownership lists, inverse path lengths, gather units */
 } rt_info;
 
 /* Thread-local message for the last failed call (never NULL). */

@@ -59,7 +59,7 @@ struct rt_grid {
     double *h_pin = nullptr;  // pinned scalars read back by the iteration control
     int *d_lost = nullptr;
     int lost = 0;
-    double geom_ms = 0.0;
+    double geom_ms = 0.0, geom_trace_ms = 0.0, geom_lists_ms = 0.0;
     int hs[4] = {0, 1, 2, 3};
     int nh = 0;
     std::vector<double> history;

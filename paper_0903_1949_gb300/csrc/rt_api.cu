@@ -323,6 +323,7 @@ int build_geometry(rt_grid *g)
                        cudaMemcpyDeviceToHost, g->st));
     CK(cudaMemcpyAsync(&g->lost, g->d_lost, sizeof(int), cudaMemcpyDeviceToHost, g->st));
     RCK(sync(g));
+    g->geom_trace_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     dfree(g, d_aro);
     // angle blocks sized so one block's per-segment results stay in L2
     double avg = (double)g->n_seg / n_ang;
@@ -394,6 +395,8 @@ int build_geometry(rt_grid *g)
         CK(cudaMemcpyAsync(&g->h_nunits[b], uf + nvox, sizeof(int64_t), cudaMemcpyDeviceToHost, g->st));
     }
     RCK(sync(g));
+    g->geom_lists_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() -
+                       g->geom_trace_ms;
     int64_t max_units = 0;
     for (int b = 0; b < g->nblk; ++b) {
         g->h_ubase[b + 1] = g->h_ubase[b] + g->h_nunits[b];
@@ -1291,6 +1294,8 @@ int rt_get_info(const rt_grid *g, rt_info *info)
     info->lost_rays = g->lost;
     info->precision = g->precision;
     info->geometry_ms = g->geom_ms;
+    info->geometry_trace_ms = g->geom_trace_ms;
+    info->geometry_lists_ms = g->geom_lists_ms;
     return RT_OK;
 }
 

@@ -46,7 +46,8 @@ class rt_info(ctypes.Structure):
     _fields_ = [("n_vox", ctypes.c_int64), ("n_angles", ctypes.c_int64), ("n_rays", ctypes.c_int64),
                 ("n_segments", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("n_blocks", ctypes.c_int32),
                 ("angle_block", ctypes.c_int32), ("lost_rays", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("geometry_ms", ctypes.c_double)]
+                ("geometry_ms", ctypes.c_double), ("geometry_trace_ms", ctypes.c_double),
+                ("geometry_lists_ms", ctypes.c_double)]
 
 
 class rt_timing(ctypes.Structure):

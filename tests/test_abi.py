@@ -81,9 +81,15 @@ def test_null_handles_rejected(lib):
     assert lib.rt_get_J(None, ctypes.c_void_p(out.ctypes.data), rt.RT_HOST) == rt.RT_EINVAL
     p = ctypes.c_void_p(out.ctypes.data)
     assert lib.rt_adjoint(None, None, None, None, 1e-8, 10, p, p, p, rt.RT_HOST, None) == rt.RT_EINVAL
+    h = ctypes.c_void_p()
+    assert lib.rt_line_create(ctypes.byref(h), None, 4, p, p, rt.RT_LSTAR_DIAG, 0, None) == rt.RT_EINVAL
+    assert lib.rt_line_set(None, p, p, p, p, rt.RT_HOST) == rt.RT_EINVAL
+    assert lib.rt_line_step(None, None) == rt.RT_EINVAL
+    assert lib.rt_line_solve(None, 1e-6, 10, None) == rt.RT_EINVAL
+    assert lib.rt_line_get(None, 0, p, rt.RT_HOST) == rt.RT_EINVAL
 
 
 def test_struct_layout_matches_header(lib):
     # rt_grid_desc / rt_info sizes as laid out by the C compiler for x86-64 and aarch64
     assert ctypes.sizeof(rt.rt_grid_desc) == 112
-    assert ctypes.sizeof(rt.rt_info) == 64
+    assert ctypes.sizeof(rt.rt_info) == 80
