@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-wavelength batch measurement")
     ap.add_argument("--no-convergence", action="store_true", help="skip the time-to-convergence comparison")
     ap.add_argument("--no-line", action="store_true", help="skip the two-level-atom line measurement")
+    ap.add_argument("--flux-max", type=int, default=64,
+                    help="largest n (n x n solid angles) of the outer-flux angle-resolution study; 0 skips it")
     return ap.parse_args()
 
 
@@ -369,6 +371,10 @@ def main():
     if not args.no_line and rank == 0:
         line_res = line_measure(g, args.workload, rt, I, torch)
 
+    flux_res = None
+    if args.flux_max > 0 and rank == 0:
+        flux_res = flux_resolution(args.workload, args.flux_max, rt, I)
+
     batch = None
     if not args.no_batch and rank == 0:
         g.close()
@@ -420,6 +426,8 @@ def main():
         line["convergence"] = conv
     if line_res is not None:
         line["line"] = line_res
+    if flux_res is not None:
+        line["flux_resolution"] = flux_res
     if rank == 0 and not args.no_cpu:
         try:
             line["cpu_baseline"] = cpu_oracle_sample(p, args.cpu_angles)
@@ -503,6 +511,38 @@ def line_measure(g, workload, rt, I, torch, eps_l=1e-4, tol=1e-4, max_iter=80):
             "last_max_rel_dS_l": hist[-1],
             "note": "the paper quotes 30 iterations at eps_l = 1e-4 with 256x256 solid angles (other machine, "
                     "context only)"}
+
+
+def flux_resolution(workload, n_max, rt, I, chunk=1024):
+    """Flux vectors of the outermost voxels against the solid-angle resolution
+    (Sect. 3.2.2): the line-centre opacity of the eps_l = 1 line (S = B) on the
+    workload grid without noise, so that only F_r should be non-zero.  Each set
+    of n x n solid angles is solved by rt_fs_sweep, `chunk` angles at a time
+    (geometry, parabola choices and an FP32 formal solution per chunk)."""
+    q = I.line_problem(workload, n_freq=32, ratio=1e6, eps_l=1.0, noise=0.0)
+    k = int(np.argmax(q["phi"]))
+    chi = q["chi_c"] + q["chi_l"] * q["phi"][k]
+    n1 = len(q["edges"][0]) - 1
+    rows = []
+    na = 8
+    while na <= n_max:
+        dirs, w = I.angle_set(na, na)
+        t0 = time.perf_counter()
+        J, F = rt.rt_fs_sweep(q["coord"], q["edges"], dirs, w, chi, q["B"], q["B"], chunk, inner_bc=q["inner_bc"])
+        dt = time.perf_counter() - t0
+        out = F.reshape(n1, -1, 3)[-1]
+        Fr = out[:, 0].mean()
+        rows.append({"n_angles": na * na, "max_abs_F_theta_over_F_r": float(np.abs(out[:, 1]).max() / Fr),
+                     "max_abs_F_phi_over_F_r": float(np.abs(out[:, 2]).max() / Fr),
+                     "F_r_max_over_min_minus_1": float(out[:, 0].max() / out[:, 0].min() - 1.0),
+                     "s": dt, "voxel_angles_per_s": chi.size * na * na / dt})
+        na *= 2
+    return {"workload": "%s grid, no noise, line-centre opacity of the eps_l = 1 line (chi_l/chi_c = 1e6), S = B; "
+                        "outermost shell, all (theta_c, phi_c); FP32 formal solutions, %d solid angles per chunk"
+                        % (workload, chunk),
+            "rows": rows,
+            "note": "the paper reports F_theta, F_phi errors of about 10%% at low resolution and below 1%% of F_r "
+                    "at 512^2 (other machine, context only)"}
 
 
 def convergence_measure(g, p, rt, torch, tol=1e-6, max_fs=400):

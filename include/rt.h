@@ -381,6 +381,23 @@ int rt_line_solve(rt_batch *b, double tol, int max_iter, int32_t *iters);
  * in the slot order of rt_get_Lstar_nn (RT_EINVAL on a diagonal line). */
 int rt_line_get(const rt_batch *b, int what, double *out, int where);
 
+/* ---- Formal solution over a large solid-angle set (angle-resolution study) ----
+ *
+ * J and the flux (local basis, as rt_get_flux) of the field (chi, S, B) for the
+ * grid and solid-angle set of d, processed angles_per_chunk solid angles at a
+ * time so that only one chunk's characteristics are held (Sect. 3.1-3.2: the
+ * flux vectors of the outermost voxels with up to 512^2 solid angles).  Each
+ * chunk is a temporary grid built from d (its weights renormalised to 1),
+ * solved with `precision` (RT_FP64: FP64 march and gather; RT_MIXED: FP32),
+ * and its J and flux are added with the chunk's share of the total weight;
+ * d->use_lstar, d->ng and d->refine_every are ignored.  chi, S, B: n_vox each
+ * (host arrays validated as by rt_set_opacity); J: n_vox, F: 3 n_vox, all on
+ * `where`.  Uses d->device and d->stream.  Chunk geometry dominates the time
+ * (larger chunks amortise it better, within device memory).  Errors of a
+ * chunk's grid are returned as they are; the outputs are written only on RT_OK. */
+int rt_fs_sweep(const rt_grid_desc *d, int angles_per_chunk, const double *chi, const double *S, const double *B,
+                int precision, double *J, double *F, int where);
+
 /* Device timing of the hot kernels.  rt_set_timing(g, 1) resets the counters
  * and brackets every ray-march and gather launch of later calls with CUDA
  * events on the stream each runs on; rt_set_timing(g, N) with N > 1 brackets

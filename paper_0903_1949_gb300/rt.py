@@ -110,6 +110,7 @@ def load():
         "rt_line_step": [_P, _P],
         "rt_line_solve": [_P, ctypes.c_double, _I, ctypes.POINTER(ctypes.c_int32)],
         "rt_line_get": [_P, _I, _P, _I],
+        "rt_fs_sweep": [ctypes.POINTER(rt_grid_desc), _I, _P, _P, _P, _I, _P, _P, _I],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -141,9 +142,9 @@ def rt_last_error():
     return load().rt_last_error().decode()
 
 
-def rt_grid_create(coord, edges, dirs, weights, inner_bc=RT_CORE_B, interp=RT_PARABOLIC, I_outer=0.0,
-                   precision=RT_FP64, use_lstar=True, ng=True, refine_every=0, angle_block=0, device=0, stream=None):
-    L = load()
+def _desc(coord, edges, dirs, weights, inner_bc=RT_CORE_B, interp=RT_PARABOLIC, I_outer=0.0, precision=RT_FP64,
+          use_lstar=True, ng=True, refine_every=0, angle_block=0, device=0, stream=None):
+    """(rt_grid_desc, arrays it points to)."""
     keep = [np.ascontiguousarray(e, dtype=np.float64) for e in edges]
     dirs = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 3))
     wts = np.ascontiguousarray(weights, dtype=np.float64)
@@ -160,9 +161,41 @@ def rt_grid_create(coord, edges, dirs, weights, inner_bc=RT_CORE_B, interp=RT_PA
     d.precision, d.use_lstar, d.ng = int(precision), lst, 1 if ng else 0
     d.refine_every, d.angle_block, d.device = int(refine_every), int(angle_block), int(device)
     d.stream = stream if stream else None
+    return d, (keep, dirs, wts)
+
+
+def rt_grid_create(coord, edges, dirs, weights, inner_bc=RT_CORE_B, interp=RT_PARABOLIC, I_outer=0.0,
+                   precision=RT_FP64, use_lstar=True, ng=True, refine_every=0, angle_block=0, device=0, stream=None):
+    L = load()
+    d, keep = _desc(coord, edges, dirs, weights, inner_bc, interp, I_outer, precision, use_lstar, ng, refine_every,
+                    angle_block, device, stream)
     h = ctypes.c_void_p()
     _check(L.rt_grid_create(ctypes.byref(h), ctypes.byref(d)))
     return h
+
+
+def rt_fs_sweep(coord, edges, dirs, weights, chi, S, B, angles_per_chunk, precision=RT_MIXED, inner_bc=RT_CORE_B,
+                interp=RT_PARABOLIC, I_outer=0.0, angle_block=0, device=0, stream=None):
+    """J (n_vox) and flux (n_vox, 3; local basis) of (chi, S, B) over the whole solid-angle set,
+    angles_per_chunk solid angles at a time (host arrays in and out)."""
+    d, keep = _desc(coord, edges, dirs, weights, inner_bc, interp, I_outer, precision, True, False, 0, angle_block,
+                    device, stream)
+    n = d.n[0] * d.n[1] * d.n[2]
+    c, pc = _host(chi, n)
+    Sv, pS = _host(S, n)
+    Bv, pB = _host(B, n)
+    J = np.empty(n)
+    F = np.empty((n, 3))
+    _check(load().rt_fs_sweep(ctypes.byref(d), int(angles_per_chunk), pc, pS, pB, int(precision),
+                              ctypes.c_void_p(J.ctypes.data), ctypes.c_void_p(F.ctypes.data), RT_HOST))
+    return J, F
+
+
+def _host(x, n):
+    a = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+    if a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a, ctypes.c_void_p(a.ctypes.data)
 
 
 def rt_grid_destroy(h):

@@ -98,3 +98,27 @@ def test_p11_flux_conservation_improves_with_resolution():
     s2, t2, p2 = _p11(16, 9, 17, 8)
     assert s2 < 0.5 * s1
     assert t2 < 0.5 * t1 and p2 < 0.5 * p1
+
+
+def test_p12_outer_flux_vectors_become_radial_with_solid_angles():
+    """Sect. 3.2.2 (flux vectors of the outermost voxels): in spherical symmetry
+    only F_r is non-zero; on a fixed grid the scatter of F_r over the outermost
+    shell and F_phi fall as the solid-angle set is refined; F_theta falls until the
+    9 theta cells of the grid, not the solid angles, set its error."""
+    edges, rm = _shell_problem(8, 9, 17)
+    per = 9 * 17
+    chi = np.repeat(2.0 / rm ** 2, per)
+    S = np.ones(8 * per)
+    scat, fth, fph = [], [], []
+    for n in (2, 4, 8, 16):
+        dirs, w = I.angle_set(n, n)
+        g = O.OracleGrid(I.SPHERICAL, edges, dirs, w, I.CORE_B)
+        _, _, F, _ = g.formal_solution(S, chi, S)
+        out = F.reshape(8, per, 3)[-1]
+        Fr = out[:, 0].mean()
+        scat.append(out[:, 0].max() / out[:, 0].min() - 1.0)
+        fth.append(np.abs(out[:, 1]).max() / Fr)
+        fph.append(np.abs(out[:, 2]).max() / Fr)
+    assert scat[0] > scat[1] > scat[2] > scat[3]
+    assert fph[0] > fph[1] > fph[2] > fph[3]
+    assert fth[0] > fth[1] and max(fth[2], fth[3]) < 0.6 * fth[1]
