@@ -82,62 +82,6 @@ __device__ __forceinline__ bool shell(const GeomDev &G, const Line &L, int m, do
     return roots2(L.a, L.b, L.p2 - rm * rm, lo, hi);
 }
 
-__device__ double next_cone(const GeomDev &G, const Line &L, int jc, double t)
-{
-    double c = G.ct[jc];
-    if (fabs(c) < 1e-12) {  // the cone at theta = pi/2 is the plane z = 0
-        if (L.dz == 0.0) return dinf();
-        double r = -(L.z / L.dz);
-        return (r > t) ? r : dinf();
-    }
-    double cc = c * c;
-    double A = L.dz * L.dz - cc * L.a;
-    double B = L.zd - cc * L.b;
-    double C = L.z2 - cc * L.p2;
-    double r0, r1;
-    int nr;
-    if (A == 0.0) {
-        if (B == 0.0) return dinf();
-        r0 = -(C / (2.0 * B));
-        r1 = r0;
-        nr = 1;
-    } else {
-        if (!roots2(A, B, C, r0, r1)) return dinf();
-        if (r0 == r1) return dinf();  // a tangent line stays in its cell
-        nr = 2;
-    }
-    for (int q = 0; q < nr; ++q) {
-        double r = (q == 0) ? r0 : r1;
-        if (!(r > t)) continue;
-        double zz = L.z + r * L.dz;
-        bool nappe = (c > 0.0) ? (zz > 0.0) : (zz < 0.0);
-        if (nappe) return r;
-    }
-    return dinf();
-}
-
-// Half-plane phi = phi_kp bounded by the z axis.
-__device__ __forceinline__ double next_halfplane(const GeomDev &G, const Line &L, int kp, double t)
-{
-    double c = G.cp[kp], s = G.sp[kp];
-    double den = c * L.dy - s * L.dx;
-    if (den == 0.0) return dinf();
-    double num = c * L.y - s * L.x;
-    double r = -(num / den);
-    if (!(r > t)) return dinf();
-    double xx = L.x + r * L.dx;
-    double yy = L.y + r * L.dy;
-    double h = c * xx + s * yy;
-    return (h > 0.0) ? r : dinf();
-}
-
-__device__ __forceinline__ double next_zplane(const GeomDev &G, const Line &L, int m, double t)
-{
-    if (L.dz == 0.0) return dinf();
-    double r = (G.e3[m] - L.z) / L.dz;
-    return (r > t) ? r : dinf();
-}
-
 // Angular cell at parameter t (after crossing a transparent hole).
 __device__ void locate(const GeomDev &G, const Line &L, double t, int &jo, int &ko)
 {
@@ -173,6 +117,115 @@ __device__ void locate(const GeomDev &G, const Line &L, double t, int &jo, int &
 
 __device__ __forceinline__ int max_steps(const GeomDev &G) { return 4 * (G.n1 + G.n2 + G.n3) + 16; }
 
+// Where a line crosses a given surface does not depend on the cell the walk is
+// in, so each surface's candidate parameters are evaluated once per walk (by
+// the same operations, in the same order, as a per-step evaluation) and kept
+// for the three most recently used surfaces of each axis.  Invalid candidates
+// are stored as NaN (shells) or +inf (cones, half-planes, planes).
+
+// Shell m: ordered roots (lo, hi), NaN when the line misses it.
+__device__ __forceinline__ void shell_roots(const GeomDev &G, const Line &L, int m, double &lo, double &hi)
+{
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    if (!shell(G, L, m, lo, hi)) {
+        lo = nan;
+        hi = nan;
+    }
+}
+
+// Cone jc: the roots on its own nappe, smaller first (+inf where none).
+__device__ void cone_roots(const GeomDev &G, const Line &L, int jc, double &ra, double &rb)
+{
+    const double INF = dinf();
+    ra = INF;
+    rb = INF;
+    double c = G.ct[jc];
+    if (fabs(c) < 1e-12) {  // the cone at theta = pi/2 is the plane z = 0
+        if (L.dz != 0.0) ra = -(L.z / L.dz);
+        return;
+    }
+    double cc = c * c;
+    double A = L.dz * L.dz - cc * L.a;
+    double B = L.zd - cc * L.b;
+    double C = L.z2 - cc * L.p2;
+    double r0, r1;
+    int nr;
+    if (A == 0.0) {
+        if (B == 0.0) return;
+        r0 = -(C / (2.0 * B));
+        r1 = r0;
+        nr = 1;
+    } else {
+        if (!roots2(A, B, C, r0, r1)) return;
+        if (r0 == r1) return;  // a tangent line stays in its cell
+        nr = 2;
+    }
+    for (int q = 0; q < nr; ++q) {
+        double r = (q == 0) ? r0 : r1;
+        double zz = L.z + r * L.dz;
+        bool nappe = (c > 0.0) ? (zz > 0.0) : (zz < 0.0);
+        if (nappe) {
+            if (q == 0) ra = r;
+            else rb = r;
+        }
+    }
+}
+
+// Half-plane phi = phi_kp bounded by the z axis: its crossing, +inf if none.
+__device__ __forceinline__ double halfplane_root(const GeomDev &G, const Line &L, int kp)
+{
+    double c = G.cp[kp], s = G.sp[kp];
+    double den = c * L.dy - s * L.dx;
+    if (den == 0.0) return dinf();
+    double num = c * L.y - s * L.x;
+    double r = -(num / den);
+    double xx = L.x + r * L.dx;
+    double yy = L.y + r * L.dy;
+    double h = c * xx + s * yy;
+    return (h > 0.0) ? r : dinf();
+}
+
+__device__ __forceinline__ double zplane_root(const GeomDev &G, const Line &L, int m)
+{
+    if (L.dz == 0.0) return dinf();
+    return (G.e3[m] - L.z) / L.dz;
+}
+
+// kind: 0 shell, 1 cone, 2 half-plane, 3 z-plane; three entries in scalars
+// (kept in registers), replaced in turn
+template <int KIND>
+struct SurfCache {
+    int i0, i1, i2, rr;
+    double a0, a1, a2, b0, b1, b2;
+    __device__ __forceinline__ void init()
+    {
+        i0 = i1 = i2 = -1;
+        rr = 0;
+        a0 = a1 = a2 = b0 = b1 = b2 = 0.0;
+    }
+    __device__ __forceinline__ void get(const GeomDev &G, const Line &L, int m, double &ra, double &rb)
+    {
+        if (i0 == m) { ra = a0; rb = b0; return; }
+        if (i1 == m) { ra = a1; rb = b1; return; }
+        if (i2 == m) { ra = a2; rb = b2; return; }
+        if (KIND == 0) shell_roots(G, L, m, ra, rb);
+        else if (KIND == 1) cone_roots(G, L, m, ra, rb);
+        else if (KIND == 2) { ra = halfplane_root(G, L, m); rb = ra; }
+        else { ra = zplane_root(G, L, m); rb = ra; }
+        if (rr == 0) { i0 = m; a0 = ra; b0 = rb; }
+        else if (rr == 1) { i1 = m; a1 = ra; b1 = rb; }
+        else { i2 = m; a2 = ra; b2 = rb; }
+        rr = (rr == 2) ? 0 : rr + 1;
+    }
+};
+
+// the first crossing after t among one or two candidates (+inf: none)
+__device__ __forceinline__ double after(double ra, double rb, double t)
+{
+    const double INF = dinf();
+    return fmin((ra > t) ? ra : INF, (rb > t) ? rb : INF);
+}
+
 // Walk from the centre of voxel (i,j,k) along (dx,dy,dz), reporting each
 // traversed cell to vis.cell(vox, t_in, t_out, after_hole).  Returns how the
 // characteristic ended: left the domain, met the opaque core, or lost.
@@ -183,6 +236,14 @@ __device__ int walk(const GeomDev &G, double x0, double y0, double z0, double dx
     const Line L = make_line(G, x0, y0, z0, dx, dy, dz);
     const double INF = dinf();
     const bool sph = (G.coord == RT_SPHERICAL);
+    SurfCache<0> csh;
+    SurfCache<1> ccone;
+    SurfCache<2> chp;
+    SurfCache<3> czp;
+    csh.init();
+    ccone.init();
+    chp.init();
+    czp.init();
     double t = 0.0;
     int hole = 0;
     const int nsteps = max_steps(G);
@@ -190,23 +251,42 @@ __device__ int walk(const GeomDev &G, double x0, double y0, double z0, double dx
         double c0 = INF, c1 = INF, c2 = INF, c3 = INF, c4 = INF, c5 = INF;
         double lo, hi;
         if (!(i == 0 && G.e1[0] == 0.0)) {
-            if (shell(G, L, i, lo, hi) && lo < hi && lo > t) c0 = lo;
+            csh.get(G, L, i, lo, hi);
+            if (lo < hi && lo > t) c0 = lo;
         }
-        if (shell(G, L, i + 1, lo, hi) && hi > t) c1 = hi;
+        csh.get(G, L, i + 1, lo, hi);
+        if (hi > t) c1 = hi;
+        double ra, rb;
         if (sph) {
-            if (j >= 1) c2 = next_cone(G, L, j, t);
-            if (j + 1 <= G.n2 - 1) c3 = next_cone(G, L, j + 1, t);
+            if (j >= 1) {
+                ccone.get(G, L, j, ra, rb);
+                c2 = after(ra, rb, t);
+            }
+            if (j + 1 <= G.n2 - 1) {
+                ccone.get(G, L, j + 1, ra, rb);
+                c3 = after(ra, rb, t);
+            }
             if (G.n3 > 1) {
-                c4 = next_halfplane(G, L, k, t);
-                c5 = next_halfplane(G, L, (k + 1 == G.n3) ? 0 : k + 1, t);
+                chp.get(G, L, k, ra, rb);
+                c4 = (ra > t) ? ra : INF;
+                chp.get(G, L, (k + 1 == G.n3) ? 0 : k + 1, ra, rb);
+                c5 = (ra > t) ? ra : INF;
             }
         } else {
             if (G.n2 > 1) {
-                c2 = next_halfplane(G, L, j, t);
-                c3 = next_halfplane(G, L, (j + 1 == G.n2) ? 0 : j + 1, t);
+                chp.get(G, L, j, ra, rb);
+                c2 = (ra > t) ? ra : INF;
+                chp.get(G, L, (j + 1 == G.n2) ? 0 : j + 1, ra, rb);
+                c3 = (ra > t) ? ra : INF;
             }
-            if (L.dz < 0.0) c4 = next_zplane(G, L, k, t);
-            if (L.dz > 0.0) c5 = next_zplane(G, L, k + 1, t);
+            if (L.dz < 0.0) {
+                czp.get(G, L, k, ra, rb);
+                c4 = (ra > t) ? ra : INF;
+            }
+            if (L.dz > 0.0) {
+                czp.get(G, L, k + 1, ra, rb);
+                c5 = (ra > t) ? ra : INF;
+            }
         }
         double best = fmin(fmin(fmin(c0, c1), fmin(c2, c3)), fmin(c4, c5));
         if (best == INF) return RTK_END_LOST;
