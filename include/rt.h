@@ -180,6 +180,11 @@ int rt_set_precision(rt_grid *g, int precision);
 /* RT_TUNE_MARCH64_COARSEN: segments per lane of the FP64 streamed-weight
  * march, 1 or 2 (default). */
 #define RT_TUNE_MARCH64_COARSEN 9
+/* RT_TUNE_MARCH_LOOKAHEAD (default 1): the register-prefetch FP32 march loads
+ * the voxel words two tiles ahead and issues the S lookups of the next tile
+ * while it marches the current one; 0 looks S up at the start of each tile.
+ * Both give bit-identical results. */
+#define RT_TUNE_MARCH_LOOKAHEAD 10
 int rt_tune(rt_grid *g, int knob, int value);
 
 /* Formal solution from the current S with the grid's precision: J, the

@@ -65,6 +65,26 @@ struct Sum64 {
 template <typename T> struct AccOf;
 template <> struct AccOf<float> { using type = Kahan; };
 template <> struct AccOf<double> { using type = Sum64; };
+// 16-byte vectors of a row and their entries added in order
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+    using type = float4;
+    template <typename A> __device__ __forceinline__ static void add_to(A &acc, const float4 &x)
+    {
+        acc.add(x.x);
+        acc.add(x.y);
+        acc.add(x.z);
+        acc.add(x.w);
+    }
+};
+template <> struct Vec16<double> {
+    using type = double2;
+    template <typename A> __device__ __forceinline__ static void add_to(A &acc, const double2 &x)
+    {
+        acc.add(x.x);
+        acc.add(x.y);
+    }
+};
 template <typename T> __device__ __forceinline__ const T *gbuf(const SwGather &t);
 template <> __device__ __forceinline__ const float *gbuf<float>(const SwGather &t) { return t.buf; }
 template <> __device__ __forceinline__ const double *gbuf<double>(const SwGather &t) { return t.buf64; }
@@ -104,7 +124,9 @@ __device__ __forceinline__ Wd4 ldw(const Wd4 *p)
     return Wd4{a.x, a.y, b.x, b.y};
 }
 
-template <typename M, int K>
+// SLA: the S lookups of tile t + 1 are issued while tile t is marched (its
+// words are loaded two tiles ahead), so no tile waits for its own lookups.
+template <typename M, int K, bool SLA>
 __device__ __forceinline__ void march_sw(const M &m, int64_t wg)
 {
     using T = typename M::T;
@@ -124,6 +146,7 @@ __device__ __forceinline__ void march_sw(const M &m, int64_t wg)
     uint32_t w[K];
     W c[K];
     T g[K];
+    int p[K];  // output positions (list order) when scattering
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         const int s = s_begin + K * lane + j;
@@ -131,6 +154,20 @@ __device__ __forceinline__ void march_sw(const M &m, int64_t wg)
         w[j] = ok ? __ldcs(vx + s) : 0u;
         c[j] = ok ? ldw(cf + s) : W{1, 0, 0, 0};
         g[j] = ok ? __ldcs(gw + s) : T(0);
+        p[j] = (ps && ok) ? __ldcs(ps + s) : 0;
+    }
+    uint32_t wA[K];  // SLA: words of the next tile
+    T Sc[K];         // SLA: S of this tile's segments
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        if constexpr (SLA) {
+            const int s = s_begin + 32 * K + K * lane + j;
+            wA[j] = s < s_end ? __ldcs(vx + s) : 0u;
+            Sc[j] = (s_begin + K * lane + j < s_end) ? m.S[w[j] & RTK_VOXMASK] : T(0);
+        } else {
+            wA[j] = 0u;
+            Sc[j] = T(0);
+        }
     }
     // The last segment of a tile may use S of the next tile's first segment
     // (gamma); its value is completed and stored at the start of the next tile,
@@ -143,20 +180,29 @@ __device__ __forceinline__ void march_sw(const M &m, int64_t wg)
         uint32_t wN[K];
         W cN[K];
         T gN[K];
+        int pN[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
+        for (int j = 0; j < K; ++j) {  // the next tile's streams, in flight while this one is marched
             const int s = base + 32 * K + K * lane + j;
             const bool ok = s < s_end;
-            wN[j] = ok ? __ldcs(vx + s) : 0u;
+            wN[j] = SLA ? wA[j] : (ok ? __ldcs(vx + s) : 0u);
             cN[j] = ok ? ldw(cf + s) : W{1, 0, 0, 0};
             gN[j] = ok ? __ldcs(gw + s) : T(0);
+            pN[j] = (ps && ok) ? __ldcs(ps + s) : 0;
         }
-        int pN[K];  // output positions of this tile (voxel order) when scattering
+        T S[K], SN[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) pN[j] = (ps && s0 + j < s_end) ? __ldcs(ps + s0 + j) : 0;
-        T S[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) S[j] = (s0 + j < s_end) ? m.S[w[j] & RTK_VOXMASK] : T(0);
+        for (int j = 0; j < K; ++j) {
+            if constexpr (SLA) {
+                S[j] = Sc[j];
+                const int s = base + 64 * K + K * lane + j;  // words two tiles ahead
+                wA[j] = s < s_end ? __ldcs(vx + s) : 0u;
+                SN[j] = (base + 32 * K + K * lane + j < s_end) ? m.S[wN[j] & RTK_VOXMASK] : T(0);
+            } else {
+                S[j] = (s0 + j < s_end) ? m.S[w[j] & RTK_VOXMASK] : T(0);
+                SN[j] = T(0);
+            }
+        }
         if (pend) {  // complete the previous tile's last segment
             const T Sf = __shfl_sync(FULL, S[0], 0);
             if (lane == 31) {
@@ -213,7 +259,7 @@ __device__ __forceinline__ void march_sw(const M &m, int64_t wg)
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             I = fma(A[j], I, b[j]);
-            const int oi = ps ? pN[j] : s0 + j;
+            const int oi = ps ? p[j] : s0 + j;
             if (j == K - 1 && lane == 31 && pend) {
                 pend_I = g[j] * I;
                 pend_gam = c[j].w;
@@ -231,6 +277,8 @@ __device__ __forceinline__ void march_sw(const M &m, int64_t wg)
             w[j] = wN[j];
             c[j] = cN[j];
             g[j] = gN[j];
+            p[j] = pN[j];
+            Sc[j] = SN[j];
         }
     }
 }
@@ -583,15 +631,28 @@ __global__ void __launch_bounds__(256) k_gather_rows_sw(SwGather t, int nvox, in
         if (v >= nvox) return;
         const int a = t.off[v], L = t.off[v + 1] - a;
         if (L > RTK_JSHORT) return;  // long list: chunk warps
+        // A row is one thread's: it is read through the read-only L1 path in
+        // 16-byte vectors from its first 16-byte boundary on (scalars before
+        // it and after the last whole vector); entries are added in row order.
         Acc acc;
-        for (int k = 0; k < L; k += 8) {
-            T val[8];
+        const T *row = buf + a;
+        constexpr int NV = 16 / sizeof(T);
+        int head = (int)(((16u - ((uint32_t)(uintptr_t)row & 15u)) & 15u) / sizeof(T));
+        if (head > L) head = L;
+        for (int k = 0; k < head; ++k) acc.add(__ldg(row + k));
+        using V = typename Vec16<T>::type;
+        const V *rv = reinterpret_cast<const V *>(row + head);
+        const int nvec = (L - head) / NV;
+        for (int q = 0; q < nvec; q += 4) {
+            V x[4];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) val[j] = (k + j < L) ? __ldcg(buf + a + k + j) : T(0);
+            for (int u = 0; u < 4; ++u)
+                if (q + u < nvec) x[u] = __ldg(rv + q + u);
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (k + j < L) acc.add(val[j]);
+            for (int u = 0; u < 4; ++u)
+                if (q + u < nvec) Vec16<T>::add_to(acc, x[u]);
         }
+        for (int k = head + nvec * NV; k < L; ++k) acc.add(__ldg(row + k));
         const double r = acc.value();
         t.J[v] = t.first ? r : t.J[v] + r;
         return;
@@ -634,10 +695,10 @@ __global__ void k_inv_perm(const int32_t *perm, int64_t n, int32_t *pos)
         pos[perm[e]] = (int32_t)e;
 }
 
-template <typename M, int K>
+template <typename M, int K, bool SLA>
 __global__ void __launch_bounds__(256) k_march_sw(M m)
 {
-    march_sw<M, K>(m, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    march_sw<M, K, SLA>(m, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
 }
 
 // FP64 weights of every segment for the current chi, rounded to FP32.
@@ -756,9 +817,15 @@ cudaError_t march_sw_launch(const SwMarch &m, int coarsen, cudaStream_t st)
     const int64_t grid = (m.nbundles + 7) / 8;
     if (grid <= 0) return cudaSuccess;
     if (m.stages >= 2) return m.bulk ? launch_ring_k<true>(m, coarsen, grid, st) : launch_ring_k<false>(m, coarsen, grid, st);
-    if (coarsen == 4) k_march_sw<SwMarch, 4><<<(unsigned)grid, 256, 0, st>>>(m);
-    else if (coarsen == 1) k_march_sw<SwMarch, 1><<<(unsigned)grid, 256, 0, st>>>(m);
-    else k_march_sw<SwMarch, 2><<<(unsigned)grid, 256, 0, st>>>(m);
+    if (m.lookahead) {
+        if (coarsen == 4) k_march_sw<SwMarch, 4, true><<<(unsigned)grid, 256, 0, st>>>(m);
+        else if (coarsen == 1) k_march_sw<SwMarch, 1, true><<<(unsigned)grid, 256, 0, st>>>(m);
+        else k_march_sw<SwMarch, 2, true><<<(unsigned)grid, 256, 0, st>>>(m);
+    } else {
+        if (coarsen == 4) k_march_sw<SwMarch, 4, false><<<(unsigned)grid, 256, 0, st>>>(m);
+        else if (coarsen == 1) k_march_sw<SwMarch, 1, false><<<(unsigned)grid, 256, 0, st>>>(m);
+        else k_march_sw<SwMarch, 2, false><<<(unsigned)grid, 256, 0, st>>>(m);
+    }
     return cudaGetLastError();
 }
 
@@ -792,8 +859,8 @@ cudaError_t march_sw64_launch(const SwMarch64 &m, int coarsen, cudaStream_t st)
 {
     const int64_t grid = (m.nbundles + 7) / 8;
     if (grid <= 0) return cudaSuccess;
-    if (coarsen == 2) k_march_sw<SwMarch64, 2><<<(unsigned)grid, 256, 0, st>>>(m);
-    else k_march_sw<SwMarch64, 1><<<(unsigned)grid, 256, 0, st>>>(m);
+    if (coarsen == 2) k_march_sw<SwMarch64, 2, false><<<(unsigned)grid, 256, 0, st>>>(m);
+    else k_march_sw<SwMarch64, 1, false><<<(unsigned)grid, 256, 0, st>>>(m);
     return cudaGetLastError();
 }
 

@@ -91,6 +91,7 @@ struct rt_grid {
     int sw_scatter = 1;       // march stores in ownership-list order (RT_TUNE_SCATTER)
     int sw_stages = 0;        // shared-memory ring depth of the streamed-weight march (RT_TUNE_MARCH_STAGES)
     int sw_bulk = 0;          // ring filled by bulk copies instead of cp.async (RT_TUNE_MARCH_BULK)
+    int sw_lookahead = 1;  // S lookups of the next tile issued during this one (register prefetch path)
     int *d_err = nullptr;     // raised by a bounded device wait that gave up
     int32_t *d_pos = nullptr; // list position of every segment within its block (NULL: not available)
     cudaStream_t st2 = nullptr;  // second stream of the overlapped gather (created on first use)

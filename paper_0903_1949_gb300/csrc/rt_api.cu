@@ -812,6 +812,7 @@ SwMarch sw_march(rt_grid *g, int b, int homog, float *out)
     m.pos = (g->sw_scatter && g->d_pos) ? g->d_pos : nullptr;
     m.stages = g->sw_stages;
     m.bulk = g->sw_bulk;
+    m.lookahead = g->sw_lookahead;
     m.err = g->d_err;
     m.seg_lo = g->h_ang_seg_off[w0];
     m.nbundles = g->h_bnd_off[b + 1] - g->h_bnd_off[b];
@@ -1388,6 +1389,11 @@ int rt_tune(rt_grid *g, int knob, int value)
     if (knob == RT_TUNE_MARCH_COARSEN) {
         if (value != 1 && value != 2 && value != 4) return fail(RT_EINVAL, "march coarsening must be 1, 2 or 4");
         g->sw_coarsen = value;
+        return RT_OK;
+    }
+    if (knob == RT_TUNE_MARCH_LOOKAHEAD) {
+        if (value != 0 && value != 1) return fail(RT_EINVAL, "march lookahead: 0 or 1");
+        g->sw_lookahead = value;
         return RT_OK;
     }
     return fail(RT_EINVAL, "unknown tuning knob %d", knob);

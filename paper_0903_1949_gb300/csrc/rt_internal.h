@@ -188,6 +188,7 @@ struct SwMarch {
     const int32_t *pos;    // NULL: out[s] in segment order; else out[pos[s]] (ownership-list order)
     int stages;            // 0: register prefetch of one tile; 2..4: shared-memory ring of that many tiles per warp
     int bulk;              // ring filled by bulk copies (1) or by per-lane 16-byte cp.async (0)
+    int lookahead;         // register prefetch: S lookups of the next tile issued during this one (1)
     int *err;              // raised when a bounded wait of the staged march gives up
     int64_t seg_lo, nbundles;
     const float *S;        // S per voxel, FP32
