@@ -185,6 +185,11 @@ int rt_set_precision(rt_grid *g, int precision);
  * while it marches the current one; 0 looks S up at the start of each tile.
  * Both give bit-identical results. */
 #define RT_TUNE_MARCH_LOOKAHEAD 10
+/* RT_TUNE_S_BLOCKED (default 1): the FP32 streamed-weight march looks S up in
+ * a copy ordered by 4 x 2 x 4 blocks of (i, j, k) voxels (one 128-byte line
+ * each) through words that carry the blocked slot; 0 uses the grid's voxel
+ * order.  Both give bit-identical results. */
+#define RT_TUNE_S_BLOCKED 11
 int rt_tune(rt_grid *g, int knob, int value);
 
 /* Formal solution from the current S with the grid's precision: J, the

@@ -771,6 +771,36 @@ __global__ void k_seg_weight(const uint32_t *__restrict__ vox, const double *__r
     }
 }
 
+
+// ---- S lookups of the FP32 march in a blocked voxel order ----
+//
+// The march looks S up once per segment; consecutive segments of a
+// characteristic are neighbouring voxels in any of the three index
+// directions.  In the grid's order (k fastest) a 128-byte line of FP32 S holds
+// 32 voxels of one (i, j) row, so most lookups touch a new line; in the blocked
+// order a line holds a 4 x 2 x 4 block of (i, j, k), and a characteristic
+// crossing it finds several of its voxels there.  vblk maps a voxel to its
+// blocked slot; the march reads words whose voxel field holds that slot.
+__global__ void k_make_voxb(const uint32_t *__restrict__ vox, int64_t nseg, const int32_t *__restrict__ vblk,
+                            uint32_t *__restrict__ voxb)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nseg; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = vox[s];
+        voxb[s] = (w & (RTK_RAYSTART | RTK_CORE | RTK_RESTART)) | (uint32_t)vblk[w & RTK_VOXMASK];
+    }
+}
+
+__global__ void k_blk_scatter(int nvox, const int32_t *__restrict__ vblk, const float *__restrict__ S,
+                              const float *__restrict__ B, float *__restrict__ Sb, float *__restrict__ Bb)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < nvox) {
+        const int q = vblk[v];
+        Sb[q] = S[v];
+        Bb[q] = B[v];
+    }
+}
+
 unsigned grid_cap(int64_t n)
 {
     int64_t b = (n + 255) / 256;
@@ -779,6 +809,20 @@ unsigned grid_cap(int64_t n)
 }
 
 }  // namespace
+
+cudaError_t make_voxb(const uint32_t *vox, int64_t nseg, const int32_t *vblk, uint32_t *voxb, cudaStream_t st)
+{
+    if (nseg <= 0) return cudaSuccess;
+    k_make_voxb<<<grid_cap(nseg), 256, 0, st>>>(vox, nseg, vblk, voxb);
+    return cudaGetLastError();
+}
+
+cudaError_t blk_scatter(int nvox, const int32_t *vblk, const float *S, const float *B, float *Sb, float *Bb,
+                        cudaStream_t st)
+{
+    k_blk_scatter<<<(nvox + 255) / 256, 256, 0, st>>>(nvox, vblk, S, B, Sb, Bb);
+    return cudaGetLastError();
+}
 
 cudaError_t sw_bundles(const int64_t *ray_off, int64_t r_lo, int64_t r_hi, int64_t seg_lo, int64_t nseg, int chunk,
                        int2 *bnd, cudaStream_t st)

@@ -91,7 +91,12 @@ struct rt_grid {
     int sw_scatter = 1;       // march stores in ownership-list order (RT_TUNE_SCATTER)
     int sw_stages = 0;        // shared-memory ring depth of the streamed-weight march (RT_TUNE_MARCH_STAGES)
     int sw_bulk = 0;          // ring filled by bulk copies instead of cp.async (RT_TUNE_MARCH_BULK)
-    int sw_lookahead = 1;  // S lookups of the next tile issued during this one (register prefetch path)
+    int sw_lookahead = 1;
+    // blocked voxel order of the FP32 streamed-weight march's S lookups (RT_TUNE_S_BLOCKED)
+    int sblk = 1, sblk_state = 0;
+    int32_t *d_vblk = nullptr;
+    uint32_t *d_voxb = nullptr;
+    float *d_S32b = nullptr, *d_B32b = nullptr;  // S lookups of the next tile issued during this one (register prefetch path)
     int *d_err = nullptr;     // raised by a bounded device wait that gave up
     int32_t *d_pos = nullptr; // list position of every segment within its block (NULL: not available)
     cudaStream_t st2 = nullptr;  // second stream of the overlapped gather (created on first use)

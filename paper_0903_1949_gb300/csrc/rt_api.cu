@@ -800,6 +800,52 @@ bool use_sw64(rt_grid *g)
     return sw_common(g);
 }
 
+// Blocked voxel order for the FP32 march's S lookups (once per grid): slots of
+// 4 x 2 x 4 index blocks, 32 voxels (one 128-byte line of FP32 S) each.
+bool build_sblk(rt_grid *g)
+{
+    if (g->sblk_state != 0) return g->sblk_state > 0;
+    g->sblk_state = -1;
+    const int n1 = g->n1, n2 = g->n2, n3 = g->n3;
+    const int nbj = (n2 + 1) / 2, nbk = (n3 + 3) / 4, nbi = (n1 + 3) / 4;
+    const int64_t nslot = (int64_t)nbi * nbj * nbk * 32;
+    if (nslot > (int64_t)RTK_VOXMASK) return false;
+    std::vector<int32_t> h(g->nvox);
+    for (int i = 0; i < n1; ++i)
+        for (int j = 0; j < n2; ++j)
+            for (int k = 0; k < n3; ++k) {
+                const int64_t blk = ((int64_t)(i / 4) * nbj + j / 2) * nbk + k / 4;
+                h[((int64_t)i * n2 + j) * n3 + k] = (int32_t)(blk * 32 + ((i % 4) * 2 + j % 2) * 4 + k % 4);
+            }
+    void *a = nullptr, *b = nullptr, *c = nullptr, *d = nullptr;
+    auto al = [&](void **q, size_t bytes) {
+        if (cudaMalloc(q, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            *q = nullptr;
+            return false;
+        }
+        g->allocs.push_back(*q);
+        g->bytes += (int64_t)bytes;
+        return true;
+    };
+    if (!al(&a, sizeof(int32_t) * g->nvox) || !al(&b, sizeof(uint32_t) * (size_t)(g->n_seg + 4)) ||
+        !al(&c, sizeof(float) * (size_t)nslot) || !al(&d, sizeof(float) * (size_t)nslot))
+        return false;
+    g->d_vblk = (int32_t *)a;
+    g->d_voxb = (uint32_t *)b;
+    g->d_S32b = (float *)c;
+    g->d_B32b = (float *)d;
+    if (cudaMemsetAsync(g->d_S32b, 0, sizeof(float) * nslot, g->st) != cudaSuccess ||
+        cudaMemsetAsync(g->d_B32b, 0, sizeof(float) * nslot, g->st) != cudaSuccess ||
+        cudaMemcpyAsync(g->d_vblk, h.data(), sizeof(int32_t) * g->nvox, cudaMemcpyHostToDevice, g->st) != cudaSuccess ||
+        make_voxb(g->d_vox, g->n_seg, g->d_vblk, g->d_voxb, g->st) != cudaSuccess ||
+        cudaStreamSynchronize(g->st) != cudaSuccess)  // h goes out of scope
+        return false;
+    g->launches++;
+    g->sblk_state = 1;
+    return true;
+}
+
 SwMarch sw_march(rt_grid *g, int b, int homog, float *out)
 {
     SwMarch m{};
@@ -818,6 +864,11 @@ SwMarch sw_march(rt_grid *g, int b, int homog, float *out)
     m.nbundles = g->h_bnd_off[b + 1] - g->h_bnd_off[b];
     m.S = g->d_S32;
     m.B = g->d_B32;
+    if (g->sblk && g->sblk_state == 1) {  // S lookups in the blocked order
+        m.vox = g->d_voxb;
+        m.S = g->d_S32b;
+        m.B = g->d_B32b;
+    }
     m.I_outer = (float)g->I_outer;
     m.homog = homog;
     m.out = out;
@@ -884,6 +935,10 @@ int run_fs_J_sw(rt_grid *g, int prec, int homog, const double *S_src, double *J)
     auto segs = [&](int b) -> int64_t {
         return g->h_ang_seg_off[g->blk_w0[b] + g->blk_nw[b]] - g->h_ang_seg_off[g->blk_w0[b]];
     };
+    if (!f64 && g->sblk && build_sblk(g)) {  // this step's FP32 S and B in the blocked order
+        CK(blk_scatter(g->nvox, g->d_vblk, g->d_S32, g->d_B32, g->d_S32b, g->d_B32b, g->st));
+        g->launches++;
+    }
     auto march = [&](int b, int q, cudaStream_t st) -> cudaError_t {
         if (!f64) return march_sw_launch(sw_march(g, b, homog, b32[q]), g->sw_coarsen, st);
         SwMarch64 m = sw_march64(g, b, homog, b64[q]);
@@ -1389,6 +1444,11 @@ int rt_tune(rt_grid *g, int knob, int value)
     if (knob == RT_TUNE_MARCH_COARSEN) {
         if (value != 1 && value != 2 && value != 4) return fail(RT_EINVAL, "march coarsening must be 1, 2 or 4");
         g->sw_coarsen = value;
+        return RT_OK;
+    }
+    if (knob == RT_TUNE_S_BLOCKED) {
+        if (value != 0 && value != 1) return fail(RT_EINVAL, "blocked S order: 0 or 1");
+        g->sblk = value;
         return RT_OK;
     }
     if (knob == RT_TUNE_MARCH_LOOKAHEAD) {

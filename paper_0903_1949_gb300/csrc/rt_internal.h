@@ -228,6 +228,12 @@ struct SwGather {
     int64_t nshort, nchunks, nbs;
     int nlong, first;
 };
+// Blocked voxel order of the FP32 march's S lookups: words with the voxel field
+// replaced by its blocked slot vblk[v] (flags RAYSTART, CORE, RESTART kept),
+// and S, B scattered to their slots.
+cudaError_t make_voxb(const uint32_t *vox, int64_t nseg, const int32_t *vblk, uint32_t *voxb, cudaStream_t st);
+cudaError_t blk_scatter(int nvox, const int32_t *vblk, const float *S, const float *B, float *Sb, float *Bb,
+                        cudaStream_t st);
 cudaError_t sw_bundles(const int64_t *ray_off, int64_t r_lo, int64_t r_hi, int64_t seg_lo, int64_t nseg, int chunk,
                        int2 *bnd, cudaStream_t st);
 cudaError_t march_sw_launch(const SwMarch &m, int coarsen, cudaStream_t st);

@@ -47,9 +47,12 @@ def _iterate(p, interp, knobs, precision=rt.RT_MIXED):
 
 T = rt
 BASE = {T.RT_TUNE_STREAMED_WEIGHTS: 1, T.RT_TUNE_MARCH_COARSEN: 2, T.RT_TUNE_MARCH_CHUNK: 512, T.RT_TUNE_SCATTER: 1,
-        T.RT_TUNE_OVERLAP: 1, T.RT_TUNE_MARCH_STAGES: 0, T.RT_TUNE_MARCH_BULK: 0, T.RT_TUNE_MARCH_LOOKAHEAD: 1}
+        T.RT_TUNE_OVERLAP: 1, T.RT_TUNE_MARCH_STAGES: 0, T.RT_TUNE_MARCH_BULK: 0, T.RT_TUNE_MARCH_LOOKAHEAD: 1,
+        T.RT_TUNE_S_BLOCKED: 1}
 # same arithmetic in the same order, data moved differently: bit-identical
 SAME = [
+    {T.RT_TUNE_S_BLOCKED: 0},
+    {T.RT_TUNE_S_BLOCKED: 0, T.RT_TUNE_MARCH_STAGES: 3},
     {T.RT_TUNE_MARCH_LOOKAHEAD: 0},
     {T.RT_TUNE_MARCH_LOOKAHEAD: 0, T.RT_TUNE_SCATTER: 0},
     {T.RT_TUNE_SCATTER: 0},
@@ -107,7 +110,7 @@ def test_tune_rejects_bad_values():
     for knob, bad in ((T.RT_TUNE_MARCH_CHUNK, 32), (T.RT_TUNE_MARCH_COARSEN, 3), (T.RT_TUNE_MARCH_STAGES, 1),
                       (T.RT_TUNE_MARCH_STAGES, 5), (T.RT_TUNE_MARCH_BULK, 2), (T.RT_TUNE_SCATTER, -1),
                       (T.RT_TUNE_OVERLAP, 7), (T.RT_TUNE_STREAMED_WEIGHTS, 3), (T.RT_TUNE_MARCH_LOOKAHEAD, 2),
-                      (99, 1)):
+                      (T.RT_TUNE_S_BLOCKED, 2), (99, 1)):
         with pytest.raises(rt.RtError) as ei:
             g.tune(knob, bad)
         assert ei.value.code == rt.RT_EINVAL
