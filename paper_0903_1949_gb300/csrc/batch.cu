@@ -131,8 +131,8 @@ __global__ void k_line_update(int nvox, int nf, const double *J, const double *p
     if ((threadIdx.x & 31) == 0) atomicMax(maxrel, (unsigned long long)__double_as_longlong(rel));
 }
 
-// Nearest-neighbour line operator, frequency k's share:
-// Lbar27[v][q] (+)= w_k phi_k L27_k[v][q] (chi_l phi_k / chi_k) at the voxel u in slot q.
+// Nearest-neighbour line operator, frequency k's share (slot planes, [q nvox + v]):
+// Lbar27[q][v] (+)= w_k phi_k L27_k[q][v] (chi_l phi_k / chi_k) at the voxel u in slot q.
 __global__ void k_line_lbar_nn(int nvox, int sph, int n1, int n2, int n3, const double *L27k, const double *chi_c,
                                const double *chi_l, double phik, double wphi, double *Lbar27, int first)
 {
@@ -148,7 +148,7 @@ __global__ void k_line_lbar_nn(int nvox, int sph, int n1, int n2, int n3, const 
             const int u = (i * n2 + j) * n3 + k;
             f = chi_l[u] * phik / fma(chi_l[u], phik, chi_c[u]);
         }
-        const int64_t e = 27 * (int64_t)v + q;
+        const int64_t e = (int64_t)q * nvox + v;  // slot planes
         const double add = wphi * L27k[e] * f;
         Lbar27[e] = first ? add : Lbar27[e] + add;
     }
@@ -335,7 +335,7 @@ int capture(rt_batch *b)
 
 // Nearest-neighbour OS step of the line: (I - (1 - eps_l) Lbar27) dS_l = y by
 // Jacobi sweeps from dS_l = 0 until a sweep changes dS_l by <= 1e-14 max |dS_l|
-// (checked after 4 sweeps, then every 16), then S_l += dS_l and the max rel dS_l.
+// (checked on the 4th sweep, then every 16th), then S_l += dS_l and the max rel dS_l.
 int line_nn_os(rt_batch *b)
 {
     const rt_grid *g = b->grids[0];
@@ -348,7 +348,7 @@ int line_nn_os(rt_batch *b)
         const int batch = m < 16 ? 4 : 16;
         for (int q = 0; q < batch; ++q) {
             BCK(nn_jacobi(n, g->coord == RT_SPHERICAL, g->n1, g->n2, g->n3, b->Lbar27, b->eps_l, b->nny, xa, xb,
-                          b->nnmx, b->st));
+                          q == batch - 1 ? b->nnmx : nullptr, b->st));
             std::swap(xa, xb);
             ++m;
         }
@@ -876,6 +876,10 @@ int rt_line_get(const rt_batch *b, int what, double *out, int where)
     const double *src = what == 0 ? b->S_l : what == 1 ? b->Jbar : what == 2 ? b->Lbar : what == 3 ? b->Lbar27 : nullptr;
     if (!src) return bfail(RT_EINVAL, "what must be 0 (S_l), 1 (Jbar), 2 (Lbar*) or 3 (Lbar*_NN of a NN line)");
     BCK(cudaSetDevice(b->device));
+    if (what == 3) {  // slot planes to rows of 27, through L27k as scratch
+        BCK(nn_rows(b->lnvox, b->Lbar27, b->L27k, b->st));
+        src = b->L27k;
+    }
     BCK(cudaMemcpyAsync(out, src, sizeof(double) * b->lnvox * (what == 3 ? 27 : 1),
                         where == RT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, b->st));
     BCK(cudaStreamSynchronize(b->st));

@@ -1,9 +1,9 @@
 // nn.cu -- nearest-neighbour approximate Lambda operator (3^3 neighbour voxels
 // built exactly, Sect. 2 and 3.2.1) and its operator-splitting step.
 //
-// L27[27 v + q] = dJ_v / dS_u for the voxel u at offset (q/9 - 1, (q/3)%3 - 1,
+// L27[q nvox + v] = dJ_v / dS_u for the voxel u at offset (q/9 - 1, (q/3)%3 - 1,
 // q%3 - 1) of v in (i, j, k), the phi index periodic (axis 3 spherical, axis 2
-// cylindrical).  Along a characteristic I_s = E_s I_{s-1} + alpha_s S_prev +
+// cylindrical); 27 planes of n_vox, so that the sweeps read them coalesced.  Along a characteristic I_s = E_s I_{s-1} + alpha_s S_prev +
 // beta_s S_{v_s} + gamma_s S_{v_{s+1}}, so the derivatives d_u = dI_s/dS_u obey
 // d_u <- E_s d_u + (the weight of S_u in segment s's increment).  One thread
 // per characteristic carries d_u for the NNW most recently touched voxels (the
@@ -161,15 +161,17 @@ __global__ void __launch_bounds__(128) k_nn_gather(int nvox, const int32_t *off,
             if (q >= 0) acc[q][threadIdx.x] += val[o + k];
         }
     }
-    double *row = L27 + 27 * (int64_t)v;
 #pragma unroll
-    for (int q = 0; q < 27; ++q) row[q] = first ? acc[q][threadIdx.x] : row[q] + acc[q][threadIdx.x];
+    for (int q = 0; q < 27; ++q) {
+        double *e = L27 + (int64_t)q * nvox + v;  // slot planes: coalesced over v
+        *e = first ? acc[q][threadIdx.x] : *e + acc[q][threadIdx.x];
+    }
 }
 
 __global__ void k_nn_diag(int nvox, const double *L27, double *L)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < nvox) L[v] = L27[27 * (int64_t)v + 13];
+    if (v < nvox) L[v] = L27[13 * (int64_t)nvox + v];
 }
 
 __device__ __forceinline__ void max_to(double x, unsigned long long *dst)
@@ -178,33 +180,64 @@ __device__ __forceinline__ void max_to(double x, unsigned long long *dst)
     if ((threadIdx.x & 31) == 0) atomicMax(dst, (unsigned long long)__double_as_longlong(x));
 }
 
+// rows[27 v + q] = planes[q nvox + v]
+__global__ void k_nn_rows(int nvox, const double *planes, double *rows)
+{
+    const int64_t n = 27 * (int64_t)nvox;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = e / 27, q = e - 27 * v;
+        rows[e] = planes[q * nvox + v];
+    }
+}
+
+// max over the block, then one atomic per block (bits of non-negative doubles)
+__device__ __forceinline__ void block_max_to(double x, unsigned long long *dst)
+{
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();  // red may hold the previous call's values
+    if ((threadIdx.x & 31) == 0) red[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = red[0];
+        for (int q = 1; q < nw; ++q) m = fmax(m, red[q]);
+        atomicMax(dst, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
 // One Jacobi sweep of (I - (1-eps) L*) x = y: xo = (y + (1-eps) sum_{q != 13} L*_q xi[u_q]) / (1 - (1-eps) L*_13).
-__global__ void k_nn_jacobi(int nvox, int sph, int n1, int n2, int n3, const double *L27, const double *eps,
-                            const double *y, const double *xi, double *xo, unsigned long long *mx)
+// TRACK: also mx[0] <- max |xo - xi|, mx[1] <- max |xo| (the sweep that a convergence check reads).
+template <bool TRACK>
+__global__ void __launch_bounds__(256) k_nn_jacobi(int nvox, int sph, int n1, int n2, int n3, const double *L27,
+                                                   const double *eps, const double *y, const double *xi, double *xo,
+                                                   unsigned long long *mx)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     double dd = 0.0, xa = 0.0;
     if (v < nvox) {
         const Ijk c = decode(v, n2, n3);
-        const double *L = L27 + 27 * (int64_t)v;
+        const double *L = L27 + v;  // slot q at L[q * nvox]
         double off = 0.0;
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
             if (q == 13) continue;
             int i = c.i + q / 9 - 1, j = c.j + (q / 3) % 3 - 1, k = c.k + q % 3 - 1;
-            if (sph) k = (k + n3) % n3;
-            else j = (j + n2) % n2;
+            if (sph) k = (k < 0) ? k + n3 : ((k >= n3) ? k - n3 : k);  // phi periodic (offsets are +-1)
+            else j = (j < 0) ? j + n2 : ((j >= n2) ? j - n2 : j);
             if (i < 0 || i >= n1 || j < 0 || j >= n2 || k < 0 || k >= n3) continue;
-            off += L[q] * xi[(i * n2 + j) * n3 + k];
+            off += L[(int64_t)q * nvox] * xi[(i * n2 + j) * n3 + k];
         }
         const double e = 1.0 - eps[v];
-        const double xn = (y[v] + e * off) / (1.0 - e * L[13]);
+        const double xn = (y[v] + e * off) / (1.0 - e * L[13 * (int64_t)nvox]);
         dd = fabs(xn - xi[v]);
         xa = fabs(xn);
         xo[v] = xn;
     }
-    max_to(dd, mx);
-    max_to(xa, mx + 1);
+    if (TRACK) {
+        block_max_to(dd, mx);
+        block_max_to(xa, mx + 1);
+    }
 }
 
 // y = (1-eps) J + eps B - S   (ALI step, and the residual of the refinement)
@@ -265,10 +298,17 @@ cudaError_t nn_diag(int nvox, const double *L27, double *L, cudaStream_t st)
     return cudaGetLastError();
 }
 
+cudaError_t nn_rows(int nvox, const double *planes, double *rows, cudaStream_t st)
+{
+    k_nn_rows<<<152 * 8, 256, 0, st>>>(nvox, planes, rows);
+    return cudaGetLastError();
+}
+
 cudaError_t nn_jacobi(int nvox, int sph, int n1, int n2, int n3, const double *L27, const double *eps, const double *y,
                       const double *xi, double *xo, unsigned long long *mx, cudaStream_t st)
 {
-    k_nn_jacobi<<<nb(nvox, 256), 256, 0, st>>>(nvox, sph, n1, n2, n3, L27, eps, y, xi, xo, mx);
+    if (mx) k_nn_jacobi<true><<<nb(nvox, 256), 256, 0, st>>>(nvox, sph, n1, n2, n3, L27, eps, y, xi, xo, mx);
+    else k_nn_jacobi<false><<<nb(nvox, 256), 256, 0, st>>>(nvox, sph, n1, n2, n3, L27, eps, y, xi, xo, nullptr);
     return cudaGetLastError();
 }
 

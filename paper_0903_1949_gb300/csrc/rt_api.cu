@@ -1162,9 +1162,9 @@ int build_nn(rt_grid *g)
     return RT_OK;
 }
 
-// x = (I - (1-eps) L*_NN)^-1 y by Jacobi sweeps from x = 0 until the sweep
-// change is <= nn_jtol max |x| (checked after 4 sweeps, then every 16; the max
-// covers the sweeps since the last check); returns the result's buffer in *x_out.
+// x = (I - (1-eps) L*_NN)^-1 y by Jacobi sweeps from x = 0 until a sweep
+// changes x by <= nn_jtol max |x| (checked on the 4th sweep, then every 16th);
+// returns the result's buffer in *x_out.
 int nn_solve(rt_grid *g, const double *y, double **x_out)
 {
     const int n = g->nvox;
@@ -1173,11 +1173,12 @@ int nn_solve(rt_grid *g, const double *y, double **x_out)
     int m = 0;
     for (;;) {
         CK(cudaMemsetAsync(g->d_nnmx, 0, 2 * sizeof(unsigned long long), g->st));
-        // sweeps between convergence checks: few at first, then more (each check syncs the host)
+        // sweeps between convergence checks: few at first, then more (each check syncs the host);
+        // the last sweep of a batch measures its change
         const int batch = m < 16 ? 4 : 16;
         for (int q = 0; q < batch; ++q) {
-            CK(nn_jacobi(n, g->coord == RT_SPHERICAL, g->n1, g->n2, g->n3, g->d_L27, g->d_eps, y, xa, xb, g->d_nnmx,
-                         g->st));
+            CK(nn_jacobi(n, g->coord == RT_SPHERICAL, g->n1, g->n2, g->n3, g->d_L27, g->d_eps, y, xa, xb,
+                         q == batch - 1 ? g->d_nnmx : nullptr, g->st));
             std::swap(xa, xb);
             ++m;
         }
@@ -1600,7 +1601,25 @@ int rt_get_Lstar_nn(rt_grid *g, double *out27, int where)
     RCK(check_lost(g));
     CK(cudaSetDevice(g->device));
     RCK(build_nn(g));
-    return copy_out(g, g->d_L27, out27, 27 * (size_t)g->nvox, where);
+    if (!out27) return fail(RT_EINVAL, "out is NULL");
+    if (where == RT_DEVICE) {  // slot planes to rows of 27
+        CK(nn_rows(g->nvox, g->d_L27, out27, g->st));
+        RCK(sync(g));
+        return RT_OK;
+    }
+    if (where != RT_HOST) return fail(RT_EINVAL, "where must be RT_HOST or RT_DEVICE");
+    double *tmp = nullptr;
+    if (cudaMalloc(&tmp, sizeof(double) * 27 * (size_t)g->nvox) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RT_ENOMEM, "no device memory for the row layout of the NN Lambda*");
+    }
+    cudaError_t e = nn_rows(g->nvox, g->d_L27, tmp, g->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out27, tmp, sizeof(double) * 27 * (size_t)g->nvox, cudaMemcpyDeviceToHost, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+    cudaFree(tmp);
+    CK(e);
+    return RT_OK;
 }
 
 int rt_get_flux(const rt_grid *g, double *out3, int where)

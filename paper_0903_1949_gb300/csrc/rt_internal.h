@@ -297,7 +297,10 @@ cudaError_t nn_walk(const NnWalk &a, cudaStream_t st);
 cudaError_t nn_gather(int nvox, const int32_t *off, const int32_t *perm, const int8_t *slot, const double *val,
                       double *L27, int first, cudaStream_t st);
 cudaError_t nn_diag(int nvox, const double *L27, double *L, cudaStream_t st);
-// One Jacobi sweep of (I - (1-eps) L*) x = y; mx[0] <- max |xo - xi|, mx[1] <- max |xo| (bits of doubles)
+// The operator's 27 slot planes (L27[q nvox + v]) as rows: rows[27 v + q].
+cudaError_t nn_rows(int nvox, const double *planes, double *rows, cudaStream_t st);
+// One Jacobi sweep of (I - (1-eps) L*) x = y; with mx (may be NULL): mx[0] <- max |xo - xi|,
+// mx[1] <- max |xo| (atomic max of the bits of non-negative doubles)
 cudaError_t nn_jacobi(int nvox, int sph, int n1, int n2, int n3, const double *L27, const double *eps, const double *y,
                       const double *xi, double *xo, unsigned long long *mx, cudaStream_t st);
 cudaError_t nn_rhs(int n, const double *S, const double *J, const double *eps, const double *B, double *y,
