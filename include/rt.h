@@ -190,6 +190,12 @@ int rt_set_precision(rt_grid *g, int precision);
  * each) through words that carry the blocked slot; 0 uses the grid's voxel
  * order.  Both give bit-identical results. */
 #define RT_TUNE_S_BLOCKED 11
+/* RT_TUNE_NN_KRYLOV (default 1): the OS step of the nearest-neighbour Lambda*
+ * first runs BiCGSTAB on the Jacobi-preconditioned system until its
+ * preconditioned residual (the change a Jacobi sweep would make) is below the
+ * RT_TUNE_NN_JTOL bound, then Jacobi sweeps confirm that bound; 0 runs the
+ * Jacobi sweeps alone.  Both stop on the same criterion. */
+#define RT_TUNE_NN_KRYLOV 12
 int rt_tune(rt_grid *g, int knob, int value);
 
 /* Formal solution from the current S with the grid's precision: J, the

@@ -334,36 +334,33 @@ int capture(rt_batch *b)
 }
 
 // Nearest-neighbour OS step of the line: (I - (1 - eps_l) Lbar27) dS_l = y by
-// Jacobi sweeps from dS_l = 0 until a sweep changes dS_l by <= 1e-14 max |dS_l|
-// (checked on the 4th sweep, then every 16th), then S_l += dS_l and the max rel dS_l.
+// BiCGSTAB on the Jacobi-preconditioned system and Jacobi sweeps until one
+// changes dS_l by <= 1e-14 max |dS_l|, then S_l += dS_l and the max rel dS_l.
 int line_nn_os(rt_batch *b)
 {
     const rt_grid *g = b->grids[0];
-    const int n = b->lnvox;
-    double *xa = b->nnx, *xb = b->nnx + n;
-    BCK(cudaMemsetAsync(xa, 0, sizeof(double) * n, b->st));
-    int m = 0;
-    for (;;) {
-        BCK(cudaMemsetAsync(b->nnmx, 0, 2 * sizeof(unsigned long long), b->st));
-        const int batch = m < 16 ? 4 : 16;
-        for (int q = 0; q < batch; ++q) {
-            BCK(nn_jacobi(n, g->coord == RT_SPHERICAL, g->n1, g->n2, g->n3, b->Lbar27, b->eps_l, b->nny, xa, xb,
-                          q == batch - 1 ? b->nnmx : nullptr, b->st));
-            std::swap(xa, xb);
-            ++m;
-        }
-        unsigned long long h[2];
-        BCK(cudaMemcpyAsync(h, b->nnmx, sizeof(h), cudaMemcpyDeviceToHost, b->st));
-        BCK(cudaStreamSynchronize(b->st));
-        double dmax, xmax;
-        std::memcpy(&dmax, &h[0], sizeof(double));
-        std::memcpy(&xmax, &h[1], sizeof(double));
-        if (!std::isfinite(dmax) || !std::isfinite(xmax)) return bfail(RT_EDEVICE, "line NN OS step diverged");
-        if (!(dmax > 1e-14 * xmax)) break;
-        if (m >= 100000) return bfail(RT_ENOTCONVERGED, "line NN OS step: no convergence in 100000 sweeps");
-    }
-    b->nn_sweeps = m;
-    BCK(nn_apply(n, b->S_l, xa, nullptr, nullptr, b->maxrel, b->st));
+    NnOs o{};
+    o.nvox = b->lnvox;
+    o.sph = g->coord == RT_SPHERICAL;
+    o.n1 = g->n1;
+    o.n2 = g->n2;
+    o.n3 = g->n3;
+    o.L27 = b->Lbar27;
+    o.eps = b->eps_l;
+    o.y = b->nny;
+    o.work = b->nnx;
+    o.mx = b->nnmx;
+    o.jtol = 1e-14;
+    o.jmax = 100000;
+    o.krylov = 1;
+    o.kmax = 1000;
+    double *x = nullptr;
+    int its = 0, sweeps = 0, status = 0;
+    BCK(nn_os_solve(o, b->st, &x, &its, &sweeps, &status));
+    if (status == 2) return bfail(RT_EDEVICE, "line NN OS step diverged");
+    if (status == 1) return bfail(RT_ENOTCONVERGED, "line NN OS step: no convergence in 100000 sweeps");
+    b->nn_sweeps = sweeps;
+    BCK(nn_apply(b->lnvox, b->S_l, x, nullptr, nullptr, b->maxrel, b->st));
     return RT_OK;
 }
 
@@ -763,7 +760,7 @@ int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, co
         (rc = balloc(b, &b->tmp, n)) != RT_OK ||
         (use_lstar == RT_LSTAR_NN &&
          ((rc = balloc(b, &b->Lbar27, 27 * (size_t)n)) != RT_OK || (rc = balloc(b, &b->L27k, 27 * (size_t)n)) != RT_OK ||
-          (rc = balloc(b, &b->nnx, 2 * (size_t)n)) != RT_OK || (rc = balloc(b, &b->nny, n)) != RT_OK ||
+          (rc = balloc(b, &b->nnx, (size_t)nn_os_work_elems(n))) != RT_OK || (rc = balloc(b, &b->nny, n)) != RT_OK ||
           (rc = balloc(b, &b->nnmx, 2)) != RT_OK)) ||
         (ng && ((rc = balloc(b, &b->H, 4 * (size_t)n)) != RT_OK ||
                 (rc = balloc(b, &b->ng_part, ng_partial_elems(n))) != RT_OK ||

@@ -110,6 +110,7 @@ struct rt_grid {
     int nn_sweeps = 0;                  // Jacobi sweeps of the last OS step
     double nn_jtol = 1e-14;
     int nn_jmax = 100000;
+    int nn_krylov = 1, nn_krylov_its = 0;  // BiCGSTAB before the Jacobi sweeps of the OS step
     std::vector<int64_t> h_bnd_off;
     int bnd_chunk = 0;
 };

@@ -576,7 +576,7 @@ int alloc_fields(rt_grid *g)
     RCK(dalloc(g, &g->d_cs32, n));
     if (g->use_lstar == RT_LSTAR_NN) {
         RCK(dalloc(g, &g->d_L27, 27 * (size_t)n));
-        RCK(dalloc(g, &g->d_nnx, 2 * (size_t)n));
+        RCK(dalloc(g, &g->d_nnx, (size_t)nn_os_work_elems(n)));  // OS-step solve work space
         RCK(dalloc(g, &g->d_nny, n));
         RCK(dalloc(g, &g->d_nnmx, 2));
     }
@@ -1162,40 +1162,34 @@ int build_nn(rt_grid *g)
     return RT_OK;
 }
 
-// x = (I - (1-eps) L*_NN)^-1 y by Jacobi sweeps from x = 0 until a sweep
-// changes x by <= nn_jtol max |x| (checked on the 4th sweep, then every 16th);
-// returns the result's buffer in *x_out.
+// x = (I - (1-eps) L*_NN)^-1 y: BiCGSTAB on the Jacobi-preconditioned system
+// (unless RT_TUNE_NN_KRYLOV is 0), then Jacobi sweeps until one changes x by
+// <= nn_jtol max |x| (checked on the last sweep of each batch); returns the
+// result's buffer in *x_out.
 int nn_solve(rt_grid *g, const double *y, double **x_out)
 {
-    const int n = g->nvox;
-    double *xa = g->d_nnx, *xb = g->d_nnx + n;
-    CK(cudaMemsetAsync(xa, 0, sizeof(double) * n, g->st));
-    int m = 0;
-    for (;;) {
-        CK(cudaMemsetAsync(g->d_nnmx, 0, 2 * sizeof(unsigned long long), g->st));
-        // sweeps between convergence checks: few at first, then more (each check syncs the host);
-        // the last sweep of a batch measures its change
-        const int batch = m < 16 ? 4 : 16;
-        for (int q = 0; q < batch; ++q) {
-            CK(nn_jacobi(n, g->coord == RT_SPHERICAL, g->n1, g->n2, g->n3, g->d_L27, g->d_eps, y, xa, xb,
-                         q == batch - 1 ? g->d_nnmx : nullptr, g->st));
-            std::swap(xa, xb);
-            ++m;
-        }
-        g->launches += batch;
-        unsigned long long h[2];
-        CK(cudaMemcpyAsync(g->h_pin + 4, g->d_nnmx, sizeof(h), cudaMemcpyDeviceToHost, g->st));
-        RCK(sync(g));
-        std::memcpy(h, g->h_pin + 4, sizeof(h));
-        double dmax, xmax;
-        std::memcpy(&dmax, &h[0], sizeof(double));
-        std::memcpy(&xmax, &h[1], sizeof(double));
-        if (!std::isfinite(dmax) || !std::isfinite(xmax)) return fail(RT_EDEVICE, "NN Lambda* OS step diverged");
-        if (!(dmax > g->nn_jtol * xmax)) break;
-        if (m >= g->nn_jmax) return fail(RT_ENOTCONVERGED, "NN Lambda* OS step: no convergence in %d sweeps", m);
-    }
-    g->nn_sweeps = m;
-    *x_out = xa;
+    NnOs o{};
+    o.nvox = g->nvox;
+    o.sph = g->coord == RT_SPHERICAL;
+    o.n1 = g->n1;
+    o.n2 = g->n2;
+    o.n3 = g->n3;
+    o.L27 = g->d_L27;
+    o.eps = g->d_eps;
+    o.y = y;
+    o.work = g->d_nnx;
+    o.mx = g->d_nnmx;
+    o.jtol = g->nn_jtol;
+    o.jmax = g->nn_jmax;
+    o.krylov = g->nn_krylov;
+    o.kmax = 1000;
+    int its = 0, sweeps = 0, status = 0;
+    CK(nn_os_solve(o, g->st, x_out, &its, &sweeps, &status));
+    g->launches += 8 * its + sweeps;
+    g->nn_sweeps = sweeps;
+    g->nn_krylov_its = its;
+    if (status == 2) return fail(RT_EDEVICE, "NN Lambda* OS step diverged");
+    if (status == 1) return fail(RT_ENOTCONVERGED, "NN Lambda* OS step: no convergence in %d sweeps", sweeps);
     return RT_OK;
 }
 
@@ -1445,6 +1439,11 @@ int rt_tune(rt_grid *g, int knob, int value)
     if (knob == RT_TUNE_MARCH_COARSEN) {
         if (value != 1 && value != 2 && value != 4) return fail(RT_EINVAL, "march coarsening must be 1, 2 or 4");
         g->sw_coarsen = value;
+        return RT_OK;
+    }
+    if (knob == RT_TUNE_NN_KRYLOV) {
+        if (value != 0 && value != 1) return fail(RT_EINVAL, "NN Krylov OS solve: 0 or 1");
+        g->nn_krylov = value;
         return RT_OK;
     }
     if (knob == RT_TUNE_S_BLOCKED) {

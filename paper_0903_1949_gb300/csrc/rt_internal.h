@@ -297,6 +297,22 @@ cudaError_t nn_walk(const NnWalk &a, cudaStream_t st);
 cudaError_t nn_gather(int nvox, const int32_t *off, const int32_t *perm, const int8_t *slot, const double *val,
                       double *L27, int first, cudaStream_t st);
 cudaError_t nn_diag(int nvox, const double *L27, double *L, cudaStream_t st);
+// Operator-splitting step (I - (1-eps) L*) x = y of the nearest-neighbour
+// Lambda* (slot planes): BiCGSTAB on the Jacobi-preconditioned system (krylov
+// != 0, at most kmax iterations) to a preconditioned residual <= jtol max |x|,
+// then Jacobi sweeps until one changes x by <= jtol max |x| (at most jmax).
+// work: nn_os_work_elems(nvox) doubles; mx: 2 words.  *status: 0 converged,
+// 1 not within jmax sweeps, 2 non-finite; *x_out: the solution's buffer (in work).
+struct NnOs {
+    int nvox, sph, n1, n2, n3;
+    const double *L27, *eps, *y;
+    double *work;
+    unsigned long long *mx;
+    double jtol;
+    int jmax, krylov, kmax;
+};
+int64_t nn_os_work_elems(int nvox);
+cudaError_t nn_os_solve(const NnOs &o, cudaStream_t st, double **x_out, int *krylov_its, int *sweeps, int *status);
 // The operator's 27 slot planes (L27[q nvox + v]) as rows: rows[27 v + q].
 cudaError_t nn_rows(int nvox, const double *planes, double *rows, cudaStream_t st);
 // One Jacobi sweep of (I - (1-eps) L*) x = y; with mx (may be NULL): mx[0] <- max |xo - xi|,
