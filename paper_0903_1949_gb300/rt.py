@@ -178,19 +178,29 @@ def rt_grid_create(coord, edges, dirs, weights, inner_bc=RT_CORE_B, interp=RT_PA
 
 
 def rt_fs_sweep(coord, edges, dirs, weights, chi, S, B, angles_per_chunk, precision=RT_MIXED, inner_bc=RT_CORE_B,
-                interp=RT_PARABOLIC, I_outer=0.0, angle_block=0, device=0, stream=None):
+                interp=RT_PARABOLIC, I_outer=0.0, angle_block=0, device=0, stream=None, J=None, F=None):
     """J (n_vox) and flux (n_vox, 3; local basis) of (chi, S, B) over the whole solid-angle set,
-    angles_per_chunk solid angles at a time (host arrays in and out)."""
+    angles_per_chunk solid angles at a time.  Host arrays in and out, or CUDA float64 tensors
+    for chi, S, B with J and F given as CUDA tensors (written in place)."""
     d, keep = _desc(coord, edges, dirs, weights, inner_bc, interp, I_outer, precision, True, False, 0, angle_block,
                     device, stream)
     n = d.n[0] * d.n[1] * d.n[2]
-    c, pc = _host(chi, n)
-    Sv, pS = _host(S, n)
-    Bv, pB = _host(B, n)
-    J = np.empty(n)
-    F = np.empty((n, 3))
-    _check(load().rt_fs_sweep(ctypes.byref(d), int(angles_per_chunk), pc, pS, pB, int(precision),
-                              ctypes.c_void_p(J.ctypes.data), ctypes.c_void_p(F.ctypes.data), RT_HOST))
+    ins = [_ptr(a) for a in (chi, S, B)]
+    where = ins[0][1]
+    if any(w != where for _, w, _ in ins):
+        raise TypeError("chi, S and B must live in the same memory space")
+    if where == RT_HOST:
+        for a in (chi, S, B):
+            _host(a, n)  # size check
+        J, F = np.empty(n), np.empty((n, 3))
+    elif J is None or F is None:
+        raise TypeError("device inputs need device outputs J (n_vox) and F (n_vox, 3)")
+    pj, wj, _ = _ptr(J)
+    pf, wf, _ = _ptr(F)
+    if wj != where or wf != where:
+        raise TypeError("J and F must live where the inputs do")
+    _check(load().rt_fs_sweep(ctypes.byref(d), int(angles_per_chunk), ins[0][0], ins[1][0], ins[2][0], int(precision),
+                              pj, pf, where))
     return J, F
 
 

@@ -52,6 +52,21 @@ def test_sweep_matches_one_grid_and_oracle(coord, bc):
     assert _rel(J, J_o) < 1e-5 and _rel(F, F_o) < 1e-5
 
 
+def test_sweep_device_buffers():
+    """CUDA tensors in and out give the host path's numbers."""
+    torch = pytest.importorskip("torch")
+    p = tiny_problem(I.SPHERICAL, (9, 6, 8), 6, 6, I.CORE_B, seed=63)
+    S = p["B"] * np.random.default_rng(4).uniform(0.5, 2.0, p["nvox"])
+    J_h, F_h = _sweep(p, S, 7, rt.RT_FP64)
+    dev = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (p["chi"], S, p["B"])]
+    J_d = torch.empty(p["nvox"], dtype=torch.float64, device="cuda")
+    F_d = torch.empty((p["nvox"], 3), dtype=torch.float64, device="cuda")
+    rt.rt_fs_sweep(p["coord"], p["edges"], p["dirs"], p["weights"], *dev, 7, precision=rt.RT_FP64,
+                   inner_bc=p["inner_bc"], J=J_d, F=F_d)
+    torch.cuda.synchronize()
+    assert np.array_equal(J_d.cpu().numpy(), J_h) and np.array_equal(F_d.cpu().numpy(), F_h)
+
+
 def test_sweep_argument_checks():
     p = tiny_problem(I.SPHERICAL, (5, 4, 6), 4, 4, I.CORE_B, seed=62)
     for kw in (dict(chunk=0), dict(precision=7)):
