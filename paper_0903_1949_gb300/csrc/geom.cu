@@ -471,13 +471,17 @@ __device__ __forceinline__ uint32_t read_word(uint32_t *p) { return atomicOr(p, 
 // parallel, then accepts them in voxel order: candidate m is kept only if no
 // accepted characteristic of a lower voxel has hit it, exactly as a serial
 // pass in increasing voxel index would decide.
-__global__ void __launch_bounds__(128) k_complete(GeomDev G, const double *dirs, int w0, int nw, uint32_t *hit,
+// One warp per CTA: the CTAs, one per solid angle, spread over every SM (the
+// walks are FP64-bound, so SMs with more solid angles than others finish last).
+constexpr int CPL_WARPS = 1;
+
+__global__ void __launch_bounds__(32 * CPL_WARPS) k_complete(GeomDev G, const double *dirs, int w0, int nw, uint32_t *hit,
                                                   uint32_t *comp, int words, int32_t *scratch, int cap, int *lost)
 {
-    __shared__ int cand_s[4][32];
+    __shared__ int cand_s[CPL_WARPS][32];
     const int wib = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int wl = blockIdx.x * 4 + wib;
+    const int wl = blockIdx.x * CPL_WARPS + wib;
     if (wl >= nw) return;
     const int w = w0 + wl;
     const double dx = dirs[3 * w], dy = dirs[3 * w + 1], dz = dirs[3 * w + 2];
@@ -698,7 +702,8 @@ cudaError_t geom_mark_boundary(const GeomDev &G, const double *dirs, int w0, int
 cudaError_t geom_complete(const GeomDev &G, const double *dirs, int w0, int nw, uint32_t *hit, uint32_t *comp,
                           int words, int32_t *scratch, int cap, int *lost, cudaStream_t st)
 {
-    k_complete<<<(nw + 3) / 4, 128, 0, st>>>(G, dirs, w0, nw, hit, comp, words, scratch, cap, lost);
+    k_complete<<<(nw + CPL_WARPS - 1) / CPL_WARPS, 32 * CPL_WARPS, 0, st>>>(G, dirs, w0, nw, hit, comp, words, scratch,
+                                                                           cap, lost);
     return cudaGetLastError();
 }
 
