@@ -237,8 +237,10 @@ int rt_get_Lstar(const rt_grid *g, double *out, int where);
  * (q/9 - 1, (q/3)%3 - 1, q%3 - 1) of v in (i, j, k), the phi index periodic;
  * 0 where that offset leaves the grid.  n_vox x 27 doubles, caller-owned.
  * With RT_LSTAR_NN the ALI step solves (I - (1-eps) L*) dS = (1-eps) J +
- * eps B - S by Jacobi sweeps to max |sweep change| <= 1e-14 max |dS|, and
- * rt_get_Lstar returns the diagonal. */
+ * eps B - S until a Jacobi sweep would change dS by at most 1e-14 max |dS|
+ * (BiCGSTAB on the Jacobi-preconditioned system, then confirming sweeps; see
+ * RT_TUNE_NN_KRYLOV and RT_TUNE_NN_JTOL), and rt_get_Lstar returns the
+ * diagonal. */
 int rt_get_Lstar_nn(rt_grid *g, double *out27, int where);
 int rt_get_flux(const rt_grid *g, double *out3, int where);
 
@@ -367,8 +369,9 @@ int rt_batch_autotune(rt_batch *b, int32_t *chunk_out, int32_t *grid_out, double
  *     Lbar*_vu = sum_k wq_k phi_k Lambda*_NN,k,vu (chi_l phi_k / chi_k)_u,
  * built once per rt_line_set from each frequency's exact nearest-neighbour
  * Lambda* (as rt_get_Lstar_nn), and each iteration solves
- * (I - (1 - eps_l) Lbar*) dS_l = (1 - eps_l) Jbar + eps_l B - S_l by Jacobi
- * sweeps to a sweep change <= 1e-14 max |dS_l| after the graph.  use_lstar
+ * (I - (1 - eps_l) Lbar*) dS_l = (1 - eps_l) Jbar + eps_l B - S_l after the
+ * graph, until a Jacobi sweep would change dS_l by at most 1e-14 max |dS_l|
+ * (BiCGSTAB, then confirming sweeps, as rt_ali_step).  use_lstar
  * other than RT_LSTAR_DIAG / RT_LSTAR_NN is RT_EINVAL.  ng = 1 applies order-2
  * Ng extrapolation to S_l whenever four iterates have accumulated since the
  * last one (as rt_ali_step; rt_line_solve skips it once tol is met); ng other
