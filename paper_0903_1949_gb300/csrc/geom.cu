@@ -364,8 +364,21 @@ __device__ __forceinline__ bool core_launch(const GeomDev &G, int i, int j, int 
 
 struct MarkVisit {
     uint32_t *H;
-    __device__ void cell(int v, double, double, int) { atomicOr(H + (v >> 5), 1u << (v & 31)); }
+    int n;
+    __device__ void cell(int v, double, double, int)
+    {
+        atomicOr(H + (v >> 5), 1u << (v & 31));
+        n++;
+    }
 };
+
+// cells of the backward and forward walk of a launched characteristic, packed
+// for the segment counts (1 and 1 when a walk was lost, as the counting rule)
+__device__ __forceinline__ uint32_t pack_counts(int nb, int nf, bool lost)
+{
+    if (lost) nb = nf = 1;
+    return ((uint32_t)nb << 16) | (uint32_t)nf;
+}
 
 struct ListVisit {
     int32_t *list;
@@ -443,7 +456,8 @@ struct FwdWrite {
     }
 };
 
-__global__ void k_mark_boundary(GeomDev G, const double *dirs, int w0, int nw, uint32_t *hit, int words, int *lost)
+__global__ void k_mark_boundary(GeomDev G, const double *dirs, int w0, int nw, uint32_t *hit, int words, int *lost,
+                                uint32_t *cnt)
 {
     int64_t total = (int64_t)nw * G.nvox;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -457,10 +471,13 @@ __global__ void k_mark_boundary(GeomDev G, const double *dirs, int w0, int nw, u
         if (!outer_launch(G, i, j, k, dx, dy, dz) && !core_launch(G, i, j, k, dx, dy, dz)) continue;
         double x, y, z;
         centre_of(G, i, j, k, x, y, z);
-        MarkVisit mv{hit + (int64_t)wl * words};
+        MarkVisit mv{hit + (int64_t)wl * words, 0};
         int eb = walk(G, x, y, z, -dx, -dy, -dz, i, j, k, mv);
+        const int nb = mv.n;
         int ef = walk(G, x, y, z, dx, dy, dz, i, j, k, mv);
-        if (eb == RTK_END_LOST || ef == RTK_END_LOST) atomicAdd(lost, 1);
+        const bool bad = eb == RTK_END_LOST || ef == RTK_END_LOST;
+        if (bad) atomicAdd(lost, 1);
+        cnt[(int64_t)w * G.nvox + v] = pack_counts(nb, mv.n - nb, bad);
     }
 }
 
@@ -476,7 +493,8 @@ __device__ __forceinline__ uint32_t read_word(uint32_t *p) { return atomicOr(p, 
 constexpr int CPL_WARPS = 1;
 
 __global__ void __launch_bounds__(32 * CPL_WARPS) k_complete(GeomDev G, const double *dirs, int w0, int nw, uint32_t *hit,
-                                                  uint32_t *comp, int words, int32_t *scratch, int cap, int *lost)
+                                                  uint32_t *comp, int words, int32_t *scratch, int cap, int *lost,
+                                                  uint32_t *cnt)
 {
     __shared__ int cand_s[CPL_WARPS][32];
     const int wib = threadIdx.x >> 5;
@@ -527,6 +545,7 @@ __global__ void __launch_bounds__(32 * CPL_WARPS) k_complete(GeomDev G, const do
         pos = scan;
         // trace the candidates
         int nl = 0, bad = 0;
+        uint32_t pc = 0;  // packed walk counts of this lane's candidate
         if (lane < ncand) {
             int v = cand[lane];
             int i, j, k;
@@ -535,9 +554,11 @@ __global__ void __launch_bounds__(32 * CPL_WARPS) k_complete(GeomDev G, const do
             centre_of(G, i, j, k, x, y, z);
             ListVisit lv{mylist, cap, 0};
             int eb = walk(G, x, y, z, -dx, -dy, -dz, i, j, k, lv);
+            const int nbk = lv.n;
             int ef = walk(G, x, y, z, dx, dy, dz, i, j, k, lv);
             nl = lv.n < cap ? lv.n : cap;
             bad = (eb == RTK_END_LOST || ef == RTK_END_LOST || lv.n > cap) ? 1 : 0;
+            pc = pack_counts(nbk, lv.n - nbk, eb == RTK_END_LOST || ef == RTK_END_LOST);
         }
         __syncwarp();
         // accept in voxel order
@@ -545,6 +566,7 @@ __global__ void __launch_bounds__(32 * CPL_WARPS) k_complete(GeomDev G, const do
             int v = cand[m];
             int n_m = __shfl_sync(0xffffffffu, nl, m);
             int bad_m = __shfl_sync(0xffffffffu, bad, m);
+            const uint32_t pc_m = __shfl_sync(0xffffffffu, pc, m);
             uint32_t word = 0;
             if (lane == 0) word = read_word(H + (v >> 5));
             word = __shfl_sync(0xffffffffu, word, 0);
@@ -555,7 +577,10 @@ __global__ void __launch_bounds__(32 * CPL_WARPS) k_complete(GeomDev G, const do
                         atomicAdd(lost, 1);
                     }
                 } else {
-                    if (lane == 0) atomicOr(C + (v >> 5), 1u << (v & 31));
+                    if (lane == 0) {
+                        atomicOr(C + (v >> 5), 1u << (v & 31));
+                        cnt[(int64_t)w * G.nvox + v] = pc_m;
+                    }
                     const int32_t *lst = scratch + ((int64_t)wl * 32 + m) * cap;
                     for (int e = lane; e < n_m; e += 32) {
                         int u = lst[e];
@@ -653,6 +678,18 @@ __global__ void k_count_segs(GeomDev G, const double *dirs, int64_t n_rays, cons
     }
 }
 
+// Segment counts of every characteristic from the walks of the launch-set pass.
+__global__ void k_gather_counts(int nvox, int64_t n_rays, const int32_t *ray_origin, const int32_t *ray_angle,
+                                const uint32_t *cnt, int32_t *nseg, int32_t *nback)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = cnt[(int64_t)ray_angle[r] * nvox + ray_origin[r]];
+        const int nb = (int)(c >> 16), nf = (int)(c & 0xffffu);
+        nseg[r] = nb + nf - 1;
+        nback[r] = nb;
+    }
+}
+
 __global__ void k_write_segs(GeomDev G, const double *dirs, int64_t n_rays, const int32_t *ray_origin,
                              const int32_t *ray_angle, const int64_t *ray_off, const int32_t *nback, uint32_t *vox,
                              double *len64, float *len32, int *lost)
@@ -692,18 +729,18 @@ int blocks_for(int64_t n, int threads)
 int geom_scratch_cap(const GeomDev &G) { return 2 * (4 * (G.n1 + G.n2 + G.n3) + 16) + 8; }
 
 cudaError_t geom_mark_boundary(const GeomDev &G, const double *dirs, int w0, int nw, uint32_t *hit, int words,
-                               int *lost, cudaStream_t st)
+                               int *lost, uint32_t *cnt, cudaStream_t st)
 {
     int64_t total = (int64_t)nw * G.nvox;
-    k_mark_boundary<<<blocks_for(total, 256), 256, 0, st>>>(G, dirs, w0, nw, hit, words, lost);
+    k_mark_boundary<<<blocks_for(total, 256), 256, 0, st>>>(G, dirs, w0, nw, hit, words, lost, cnt);
     return cudaGetLastError();
 }
 
 cudaError_t geom_complete(const GeomDev &G, const double *dirs, int w0, int nw, uint32_t *hit, uint32_t *comp,
-                          int words, int32_t *scratch, int cap, int *lost, cudaStream_t st)
+                          int words, int32_t *scratch, int cap, int *lost, uint32_t *cnt, cudaStream_t st)
 {
     k_complete<<<(nw + CPL_WARPS - 1) / CPL_WARPS, 32 * CPL_WARPS, 0, st>>>(G, dirs, w0, nw, hit, comp, words, scratch,
-                                                                           cap, lost);
+                                                                           cap, lost, cnt);
     return cudaGetLastError();
 }
 
@@ -718,6 +755,13 @@ cudaError_t geom_list_rays(const GeomDev &G, const double *dirs, int n_ang, cons
                            const int64_t *ang_ray_off, int32_t *ray_origin, int32_t *ray_angle, cudaStream_t st)
 {
     k_list_rays<<<n_ang, 256, 0, st>>>(G, dirs, comp, words, ang_ray_off, ray_origin, ray_angle);
+    return cudaGetLastError();
+}
+
+cudaError_t geom_gather_counts(int nvox, int64_t n_rays, const int32_t *ray_origin, const int32_t *ray_angle,
+                               const uint32_t *cnt, int32_t *nseg, int32_t *nback, cudaStream_t st)
+{
+    k_gather_counts<<<blocks_for(n_rays, 256), 256, 0, st>>>(nvox, n_rays, ray_origin, ray_angle, cnt, nseg, nback);
     return cudaGetLastError();
 }
 

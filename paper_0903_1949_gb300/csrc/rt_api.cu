@@ -268,12 +268,15 @@ int build_geometry(rt_grid *g)
     int32_t *scratch = nullptr;
     RCK(dalloc(g, &hit, (size_t)chunk * words));
     RCK(dalloc(g, &scratch, (size_t)chunk * 32 * cap));
+    // walk counts of every launched characteristic (n_ang x n_vox), recorded by the launch-set passes
+    uint32_t *wcnt = nullptr;
+    RCK(dalloc(g, &wcnt, (size_t)n_ang * nvox));
     for (int w0 = 0; w0 < n_ang; w0 += chunk) {
         int nw = std::min(chunk, n_ang - w0);
         CK(cudaMemsetAsync(hit, 0, sizeof(uint32_t) * (size_t)nw * words, g->st));
-        CK(geom_mark_boundary(g->G, g->d_dirs, w0, nw, hit, words, g->d_lost, g->st));
+        CK(geom_mark_boundary(g->G, g->d_dirs, w0, nw, hit, words, g->d_lost, wcnt, g->st));
         CK(geom_complete(g->G, g->d_dirs, w0, nw, hit, comp + (size_t)w0 * words, words, scratch, cap, g->d_lost,
-                         g->st));
+                         wcnt, g->st));
     }
     dfree(g, hit);
     dfree(g, scratch);
@@ -299,7 +302,8 @@ int build_geometry(rt_grid *g)
     int32_t *nseg = nullptr, *nback = nullptr;
     RCK(dalloc(g, &nseg, g->n_rays));
     RCK(dalloc(g, &nback, g->n_rays));
-    CK(geom_count_segs(g->G, g->d_dirs, g->n_rays, g->d_ray_origin, g->d_ray_angle, nseg, nback, g->d_lost, g->st));
+    CK(geom_gather_counts(nvox, g->n_rays, g->d_ray_origin, g->d_ray_angle, wcnt, nseg, nback, g->st));
+    dfree(g, wcnt);
     RCK(dalloc(g, &g->d_ray_off, g->n_rays + 1));
     int64_t *tmp = nullptr;
     RCK(dalloc(g, &tmp, scan_tmp_elems(g->n_rays)));

@@ -43,10 +43,15 @@ struct GeomDev {
 // ---- geometry (geom.cu, compiled without FMA contraction) ----
 // Marks every voxel hit by the characteristics of the boundary and core voxels.
 cudaError_t geom_mark_boundary(const GeomDev &G, const double *dirs, int w0, int nw, uint32_t *hit, int words,
-                               int *lost, cudaStream_t st);
+                               int *lost, uint32_t *cnt, cudaStream_t st);
 // Coverage completion in increasing voxel order, one warp per solid angle.
 cudaError_t geom_complete(const GeomDev &G, const double *dirs, int w0, int nw, uint32_t *hit, uint32_t *comp,
-                          int words, int32_t *scratch, int cap, int *lost, cudaStream_t st);
+                          int words, int32_t *scratch, int cap, int *lost, uint32_t *cnt, cudaStream_t st);
+// cnt[w n_vox + v]: cells of the backward (high 16 bits) and forward walk of the
+// characteristic launched at voxel v for solid angle w, recorded by the two
+// launch-set passes; the segment counts then need no walk of their own.
+cudaError_t geom_gather_counts(int nvox, int64_t n_rays, const int32_t *ray_origin, const int32_t *ray_angle,
+                               const uint32_t *cnt, int32_t *nseg, int32_t *nback, cudaStream_t st);
 cudaError_t geom_count_rays(const GeomDev &G, const double *dirs, int n_ang, const uint32_t *comp, int words,
                             int32_t *counts, cudaStream_t st);
 cudaError_t geom_list_rays(const GeomDev &G, const double *dirs, int n_ang, const uint32_t *comp, int words,
