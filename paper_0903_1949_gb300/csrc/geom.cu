@@ -390,11 +390,6 @@ struct ListVisit {
     }
 };
 
-struct CountVisit {
-    int n;
-    __device__ void cell(int, double, double, int) { n++; }
-};
-
 // Writes the upstream half in reverse: cell q of the backward walk goes to
 // position base - q; the hole flag of cell q belongs to the cell written
 // just before it (the next one downstream).
@@ -655,29 +650,6 @@ __global__ void __launch_bounds__(256) k_list_rays(GeomDev G, const double *dirs
     }
 }
 
-__global__ void k_count_segs(GeomDev G, const double *dirs, int64_t n_rays, const int32_t *ray_origin,
-                             const int32_t *ray_angle, int32_t *nseg, int32_t *nback, int *lost)
-{
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
-        int v = ray_origin[r], w = ray_angle[r];
-        double dx = dirs[3 * w], dy = dirs[3 * w + 1], dz = dirs[3 * w + 2];
-        int i, j, k;
-        ijk_of(G, v, i, j, k);
-        double x, y, z;
-        centre_of(G, i, j, k, x, y, z);
-        CountVisit cb{0}, cf{0};
-        int eb = walk(G, x, y, z, -dx, -dy, -dz, i, j, k, cb);
-        int ef = walk(G, x, y, z, dx, dy, dz, i, j, k, cf);
-        if (eb == RTK_END_LOST || ef == RTK_END_LOST) {
-            atomicAdd(lost, 1);
-            cb.n = 1;
-            cf.n = 1;
-        }
-        nseg[r] = cb.n + cf.n - 1;
-        nback[r] = cb.n;
-    }
-}
-
 // Segment counts of every characteristic from the walks of the launch-set pass.
 __global__ void k_gather_counts(int nvox, int64_t n_rays, const int32_t *ray_origin, const int32_t *ray_angle,
                                 const uint32_t *cnt, int32_t *nseg, int32_t *nback)
@@ -762,13 +734,6 @@ cudaError_t geom_gather_counts(int nvox, int64_t n_rays, const int32_t *ray_orig
                                const uint32_t *cnt, int32_t *nseg, int32_t *nback, cudaStream_t st)
 {
     k_gather_counts<<<blocks_for(n_rays, 256), 256, 0, st>>>(nvox, n_rays, ray_origin, ray_angle, cnt, nseg, nback);
-    return cudaGetLastError();
-}
-
-cudaError_t geom_count_segs(const GeomDev &G, const double *dirs, int64_t n_rays, const int32_t *ray_origin,
-                            const int32_t *ray_angle, int32_t *nseg, int32_t *nback, int *lost, cudaStream_t st)
-{
-    k_count_segs<<<blocks_for(n_rays, 128), 128, 0, st>>>(G, dirs, n_rays, ray_origin, ray_angle, nseg, nback, lost);
     return cudaGetLastError();
 }
 

@@ -56,8 +56,6 @@ cudaError_t geom_count_rays(const GeomDev &G, const double *dirs, int n_ang, con
                             int32_t *counts, cudaStream_t st);
 cudaError_t geom_list_rays(const GeomDev &G, const double *dirs, int n_ang, const uint32_t *comp, int words,
                            const int64_t *ang_ray_off, int32_t *ray_origin, int32_t *ray_angle, cudaStream_t st);
-cudaError_t geom_count_segs(const GeomDev &G, const double *dirs, int64_t n_rays, const int32_t *ray_origin,
-                            const int32_t *ray_angle, int32_t *nseg, int32_t *nback, int *lost, cudaStream_t st);
 cudaError_t geom_write_segs(const GeomDev &G, const double *dirs, int64_t n_rays, const int32_t *ray_origin,
                             const int32_t *ray_angle, const int64_t *ray_off, const int32_t *nback, uint32_t *vox,
                             double *len64, float *len32, int *lost, cudaStream_t st);
