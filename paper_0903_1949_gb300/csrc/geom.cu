@@ -121,15 +121,14 @@ __device__ __forceinline__ int max_steps(const GeomDev &G) { return 4 * (G.n1 + 
 // in, so each surface's candidate parameters are evaluated once per walk (by
 // the same operations, in the same order, as a per-step evaluation) and kept
 // for the three most recently used surfaces of each axis.  Invalid candidates
-// are stored as NaN (shells) or +inf (cones, half-planes, planes).
+// are stored as +inf.
 
 // Shell m: ordered roots (lo, hi), NaN when the line misses it.
 __device__ __forceinline__ void shell_roots(const GeomDev &G, const Line &L, int m, double &lo, double &hi)
 {
-    const double nan = __longlong_as_double(0x7ff8000000000000LL);
-    if (!shell(G, L, m, lo, hi)) {
-        lo = nan;
-        hi = nan;
+    if (!shell(G, L, m, lo, hi)) {  // no crossing: neither candidate is taken
+        lo = dinf();
+        hi = dinf();
     }
 }
 
@@ -220,10 +219,17 @@ struct SurfCache {
 };
 
 // the first crossing after t among one or two candidates (+inf: none)
-__device__ __forceinline__ double after(double ra, double rb, double t)
+// The step rule compares crossing parameters only with t >= 0 and among
+// candidates greater than t, i.e. among positive doubles (or +inf), whose order
+// is that of their bit patterns as signed 64-bit integers: the selection runs on
+// the integer pipe, the values are the doubles themselves.
+__device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
+
+// the first crossing after t among one or two candidates (+inf: none), as bits
+__device__ __forceinline__ long long after(double ra, double rb, long long tb, long long infb)
 {
-    const double INF = dinf();
-    return fmin((ra > t) ? ra : INF, (rb > t) ? rb : INF);
+    const long long a = bits(ra), b = bits(rb);
+    return min(a > tb ? a : infb, b > tb ? b : infb);
 }
 
 // Walk from the centre of voxel (i,j,k) along (dx,dy,dz), reporting each
@@ -247,50 +253,54 @@ __device__ int walk(const GeomDev &G, double x0, double y0, double z0, double dx
     double t = 0.0;
     int hole = 0;
     const int nsteps = max_steps(G);
+    const long long INFB = bits(INF);
     for (int step = 0; step < nsteps; ++step) {
-        double c0 = INF, c1 = INF, c2 = INF, c3 = INF, c4 = INF, c5 = INF;
+        const long long tb = bits(t);
+        long long c0 = INFB, c1 = INFB, c2 = INFB, c3 = INFB, c4 = INFB, c5 = INFB;
         double lo, hi;
         if (!(i == 0 && G.e1[0] == 0.0)) {
             csh.get(G, L, i, lo, hi);
-            if (lo < hi && lo > t) c0 = lo;
+            // lo > t >= 0 makes lo and hi >= lo positive, so the bit order is theirs
+            if (bits(lo) > tb && bits(lo) < bits(hi)) c0 = bits(lo);
         }
         csh.get(G, L, i + 1, lo, hi);
-        if (hi > t) c1 = hi;
+        if (bits(hi) > tb) c1 = bits(hi);
         double ra, rb;
         if (sph) {
             if (j >= 1) {
                 ccone.get(G, L, j, ra, rb);
-                c2 = after(ra, rb, t);
+                c2 = after(ra, rb, tb, INFB);
             }
             if (j + 1 <= G.n2 - 1) {
                 ccone.get(G, L, j + 1, ra, rb);
-                c3 = after(ra, rb, t);
+                c3 = after(ra, rb, tb, INFB);
             }
             if (G.n3 > 1) {
                 chp.get(G, L, k, ra, rb);
-                c4 = (ra > t) ? ra : INF;
+                c4 = bits(ra) > tb ? bits(ra) : INFB;
                 chp.get(G, L, (k + 1 == G.n3) ? 0 : k + 1, ra, rb);
-                c5 = (ra > t) ? ra : INF;
+                c5 = bits(ra) > tb ? bits(ra) : INFB;
             }
         } else {
             if (G.n2 > 1) {
                 chp.get(G, L, j, ra, rb);
-                c2 = (ra > t) ? ra : INF;
+                c2 = bits(ra) > tb ? bits(ra) : INFB;
                 chp.get(G, L, (j + 1 == G.n2) ? 0 : j + 1, ra, rb);
-                c3 = (ra > t) ? ra : INF;
+                c3 = bits(ra) > tb ? bits(ra) : INFB;
             }
             if (L.dz < 0.0) {
                 czp.get(G, L, k, ra, rb);
-                c4 = (ra > t) ? ra : INF;
+                c4 = bits(ra) > tb ? bits(ra) : INFB;
             }
             if (L.dz > 0.0) {
                 czp.get(G, L, k + 1, ra, rb);
-                c5 = (ra > t) ? ra : INF;
+                c5 = bits(ra) > tb ? bits(ra) : INFB;
             }
         }
-        double best = fmin(fmin(fmin(c0, c1), fmin(c2, c3)), fmin(c4, c5));
-        if (best == INF) return RTK_END_LOST;
-        vis.cell(vid(G, i, j, k), t, best, hole);
+        const long long best = min(min(min(c0, c1), min(c2, c3)), min(c4, c5));
+        if (best == INFB) return RTK_END_LOST;
+        const double bestd = __longlong_as_double(best);
+        vis.cell(vid(G, i, j, k), t, bestd, hole);
         int ni = i, nj = j, nk = k;
         bool ex = false, core = false;
         if (c0 == best) { if (i == 0) core = true; else ni = i - 1; }
@@ -307,7 +317,7 @@ __device__ int walk(const GeomDev &G, double x0, double y0, double z0, double dx
             if (c5 == best) { if (k == G.n3 - 1) ex = true; else nk = k + 1; }
         }
         if (ex) return RTK_END_EXIT;
-        double tn = best;
+        double tn = bestd;
         hole = 0;
         if (core) {
             if (G.inner_bc == RT_CORE_B) return RTK_END_CORE;
