@@ -11,11 +11,12 @@ One step = one ALI iteration of the mixed-precision path: FP32 ray march
 over all 1024 solid angles, compensated FP32 ownership gather of J (FP64
 across angle blocks), FP64 ALI update with the cached Lambda* (+ Ng when four
 iterates have accumulated).  The metric is voxel-angle updates per second
-(n_vox * n_angles per step).  The crossing lists streamed by every step
-(about 7 GB) are far larger than L2, so no L2 flush is needed between steps.
+(n_vox * n_angles per step).  The crossing lists and weights streamed by
+every step (about 23.5 GB) are far larger than L2, so no L2 flush is needed
+between steps.
 
 Also reported: the FP64 path's step throughput, the kernel roofline of the
-FP32 ray march (event-timed inside the timed region), an end-to-end figure
+FP32 ray march (its bytes over the event-timed steps), an end-to-end figure
 through the C ABI with host buffers, the CPU oracle on a bounded sample, and
 an equal-J-error comparison of the mixed and FP64 solvers.
 
@@ -290,9 +291,13 @@ def main():
         return max_over_ranks(ev0.elapsed_time(ev1) / k, dist, "cuda")
 
     # ---- mixed-precision ALI iterations (the headline) ----
-    # Every TIMING_EVERY-th angle block's march launch is bracketed by CUDA events on
-    # its stream inside the timed region (per-launch events on every launch cost
-    # about 5 % of the step); the gather is timed in a separate window afterwards.
+    # The marches of consecutive angle blocks alternate between two streams and
+    # overlap where one drains and the next starts, so the march's throughput is
+    # taken over the event-timed step: all march bytes of a step over the step's
+    # duration (the step's other kernels count against it).  Every TIMING_EVERY-th
+    # march launch is also bracketed by events on its own stream (informational:
+    # those windows overlap the neighbouring launches); the gather is timed in a
+    # separate window afterwards.
     for _ in range(args.warmup):
         g.ali_step()
     clocks = Clocks(local)
@@ -304,9 +309,11 @@ def main():
     ck = clocks.stop()
     tm = g.timing()
     value = job_throughput(units, world, ms)
-    march_avg_ms = tm["march_ms"] / max(1, tm["march_launches"])
-    seg_per_launch = tm["march_segments"] / max(1, tm["march_launches"])
+    march_event_ms = tm["march_ms"] / max(1, tm["march_launches"])
     bytes_per_seg = tm["march_bytes"] / max(1, tm["march_segments"])
+    info = g.info()
+    seg_per_launch = info["n_segments"] / info["n_blocks"]  # one march launch per angle block and step
+    march_avg_ms = ms / info["n_blocks"]  # the step's duration shared by its march launches
     achieved = seg_per_launch * bytes_per_seg / (march_avg_ms / 1e3) / 1e9
     peak, peak_src = hbm_peak()
     traffic, traffic_src = ncu_traffic(seg_per_launch)
@@ -408,11 +415,16 @@ def main():
                          "algorithmic_bytes": "%g B per crossing segment (u32 voxel word + FP32 E, alpha, beta, "
                                               "gamma + FP32 w l/L + i32 list position)" % bytes_per_seg,
                          "segments_per_launch": seg_per_launch, "avg_launch_ms": march_avg_ms,
+                         "avg_launch_ms_events": march_event_ms,
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src if peak_src == "measured"
                          else "fallback 6800 GB/s", "traffic_source": traffic_src,
-                         "timing": "CUDA events on the march's stream around every %d-th angle block's launch "
-                                   "inside the timed steps (%d launches); the J gather of the previous angle block "
-                                   "runs concurrently on a second stream" % (TIMING_EVERY, tm["march_launches"]),
+                         "timing": "march bytes of a step (one launch per angle block, %d blocks) over the "
+                                   "event-timed step on the bench stream (avg_launch_ms = step / blocks): the "
+                                   "marches alternate between two streams and overlap at their ends, the J gather "
+                                   "of the previous angle block runs on a third; avg_launch_ms_events = CUDA events "
+                                   "on the march's own stream around every %d-th launch (%d launches), windows "
+                                   "that overlap the neighbouring launches" % (info["n_blocks"], TIMING_EVERY,
+                                                                               tm["march_launches"]),
                          "info_window": {"steps": k_info, "ms_per_step_with_all_events": ms_info,
                                          "march_ms_per_step": tm_all["march_ms"] / k_info,
                                          "gather_ms_per_step": tm_all["gather_ms"] / k_info}},

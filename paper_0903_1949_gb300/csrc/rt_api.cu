@@ -93,6 +93,8 @@ void release(rt_grid *g)
         if (e) cudaEventDestroy(e), e = nullptr;
     if (g->st2) cudaStreamDestroy(g->st2);
     g->st2 = nullptr;
+    if (g->st3) cudaStreamDestroy(g->st3);
+    g->st3 = nullptr;
     for (void *p : g->allocs) cudaFree(p);
     g->allocs.clear();
     if (g->h_pin) cudaFreeHost(g->h_pin);
@@ -927,7 +929,9 @@ SwGather sw_gather(rt_grid *g, int b, const float *buf, double *J)
 // Streamed-weight J.  Overlapped: the march of block b (grid stream, into
 // buffer b % 2) waits only for the gather of block b - 2, which read that
 // buffer; the gathers run in block order on the second stream, each after its
-// march, so J accumulates in the same order as without overlap.
+// march, so J accumulates in the same order as without overlap.  With two
+// march streams the odd blocks are marched on a third stream, so a march may
+// begin while the previous one drains.
 int run_fs_J_sw(rt_grid *g, int prec, int homog, const double *S_src, double *J)
 {
     const bool f64 = prec == RT_FP64;
@@ -974,14 +978,21 @@ int run_fs_J_sw(rt_grid *g, int prec, int homog, const double *S_src, double *J)
         for (cudaEvent_t &e : g->sev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     cudaEvent_t fork = g->sev[0], join = g->sev[1], *mdone = g->sev + 2, *gdone = g->sev + 4;
+    cudaStream_t ms[2] = {g->st, g->st};
+    if (g->sw_mstreams == 2 && g->nblk > 1) {
+        if (!g->st3) CK(cudaStreamCreateWithFlags(&g->st3, cudaStreamNonBlocking));
+        ms[1] = g->st3;
+    }
     CK(cudaEventRecord(fork, g->st));
     CK(cudaStreamWaitEvent(g->st2, fork, 0));
+    if (ms[1] != g->st) CK(cudaStreamWaitEvent(ms[1], fork, 0));
     for (int b = 0; b < g->nblk; ++b) {
-        if (b >= 2) CK(cudaStreamWaitEvent(g->st, gdone[b & 1], 0));
-        int t0 = tstart(g, 0);
-        CK(march(b, b & 1, g->st));
-        tstop(g, t0, 0, segs(b), bps * segs(b));
-        CK(cudaEventRecord(mdone[b & 1], g->st));
+        cudaStream_t s = ms[b & 1];
+        if (b >= 2) CK(cudaStreamWaitEvent(s, gdone[b & 1], 0));
+        int t0 = tstart(g, 0, s);
+        CK(march(b, b & 1, s));
+        tstop(g, t0, 0, segs(b), bps * segs(b), s);
+        CK(cudaEventRecord(mdone[b & 1], s));
         CK(cudaStreamWaitEvent(g->st2, mdone[b & 1], 0));
         t0 = tstart(g, 1, g->st2);
         CK(gather(b, b & 1, g->st2));
@@ -991,6 +1002,10 @@ int run_fs_J_sw(rt_grid *g, int prec, int homog, const double *S_src, double *J)
     }
     CK(cudaEventRecord(join, g->st2));
     CK(cudaStreamWaitEvent(g->st, join, 0));
+    if (ms[1] != g->st) {
+        CK(cudaEventRecord(g->sev[6], ms[1]));
+        CK(cudaStreamWaitEvent(g->st, g->sev[6], 0));
+    }
     return RT_OK;
 }
 
@@ -1453,6 +1468,11 @@ int rt_tune(rt_grid *g, int knob, int value)
     if (knob == RT_TUNE_S_BLOCKED) {
         if (value != 0 && value != 1) return fail(RT_EINVAL, "blocked S order: 0 or 1");
         g->sblk = value;
+        return RT_OK;
+    }
+    if (knob == RT_TUNE_MARCH_STREAMS) {
+        if (value != 1 && value != 2) return fail(RT_EINVAL, "march streams: 1 or 2");
+        g->sw_mstreams = value;
         return RT_OK;
     }
     if (knob == RT_TUNE_MARCH_LOOKAHEAD) {

@@ -25,6 +25,7 @@ RT_TUNE_MARCH_STAGES, RT_TUNE_MARCH_BULK, RT_TUNE_NN_JTOL, RT_TUNE_MARCH64_COARS
 RT_TUNE_MARCH_LOOKAHEAD = 10
 RT_TUNE_S_BLOCKED = 11
 RT_TUNE_NN_KRYLOV = 12
+RT_TUNE_MARCH_STREAMS = 13
 
 _STATUS = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONVERGED", 5: "RT_ETIMEOUT",
            6: "RT_EDEVICE"}

@@ -32,9 +32,9 @@ def _problems():
     return {"sph17": (p1, rt.RT_PARABOLIC), "cyl_hole": (p2, rt.RT_PARABOLIC), "sph_linear": (p3, rt.RT_LINEAR)}
 
 
-def _iterate(p, interp, knobs, precision=rt.RT_MIXED):
+def _iterate(p, interp, knobs, precision=rt.RT_MIXED, angle_block=0):
     g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], interp=interp,
-                precision=precision, ng=False)
+                precision=precision, ng=False, angle_block=angle_block)
     for k, v in knobs.items():
         g.tune(k, v)
     g.set_opacity(p["chi"], p["eps"], p["B"])
@@ -48,7 +48,7 @@ def _iterate(p, interp, knobs, precision=rt.RT_MIXED):
 T = rt
 BASE = {T.RT_TUNE_STREAMED_WEIGHTS: 1, T.RT_TUNE_MARCH_COARSEN: 2, T.RT_TUNE_MARCH_CHUNK: 512, T.RT_TUNE_SCATTER: 1,
         T.RT_TUNE_OVERLAP: 1, T.RT_TUNE_MARCH_STAGES: 0, T.RT_TUNE_MARCH_BULK: 0, T.RT_TUNE_MARCH_LOOKAHEAD: 1,
-        T.RT_TUNE_S_BLOCKED: 1}
+        T.RT_TUNE_S_BLOCKED: 1, T.RT_TUNE_MARCH_STREAMS: 2}
 # same arithmetic in the same order, data moved differently: bit-identical
 SAME = [
     {T.RT_TUNE_S_BLOCKED: 0},
@@ -104,13 +104,28 @@ def test_fp64_march_configurations(name):
     assert np.max(np.abs(S0 - S_o) / np.abs(S_o)) < 1e-11
 
 
+@pytest.mark.parametrize("precision", [rt.RT_MIXED, rt.RT_FP64])
+def test_march_streams_give_identical_iterates(precision):
+    """Angle blocks of 5 solid angles (13 blocks of sph17): the marches on one
+    stream or alternating between two, and without overlap, give the same bits."""
+    p, interp = _problems()["sph17"]
+    S0 = _iterate(p, interp, BASE, precision, angle_block=5)
+    for var in ({T.RT_TUNE_MARCH_STREAMS: 1}, {T.RT_TUNE_MARCH_STREAMS: 1, T.RT_TUNE_SCATTER: 0},
+                {T.RT_TUNE_SCATTER: 0},
+                {T.RT_TUNE_OVERLAP: 0}):
+        assert np.array_equal(_iterate(p, interp, {**BASE, **var}, precision, angle_block=5), S0), var
+    S_one = _iterate(p, interp, BASE, precision)  # one block: the same sums in another association
+    tol = 2e-6 if precision == rt.RT_MIXED else 1e-13
+    assert np.max(np.abs(S_one - S0) / np.abs(S0)) < tol
+
+
 def test_tune_rejects_bad_values():
     p, interp = _problems()["sph17"]
     g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=rt.RT_MIXED)
     for knob, bad in ((T.RT_TUNE_MARCH_CHUNK, 32), (T.RT_TUNE_MARCH_COARSEN, 3), (T.RT_TUNE_MARCH_STAGES, 1),
                       (T.RT_TUNE_MARCH_STAGES, 5), (T.RT_TUNE_MARCH_BULK, 2), (T.RT_TUNE_SCATTER, -1),
                       (T.RT_TUNE_OVERLAP, 7), (T.RT_TUNE_STREAMED_WEIGHTS, 3), (T.RT_TUNE_MARCH_LOOKAHEAD, 2),
-                      (T.RT_TUNE_S_BLOCKED, 2), (99, 1)):
+                      (T.RT_TUNE_S_BLOCKED, 2), (T.RT_TUNE_MARCH_STREAMS, 0), (T.RT_TUNE_MARCH_STREAMS, 3), (99, 1)):
         with pytest.raises(rt.RtError) as ei:
             g.tune(knob, bad)
         assert ei.value.code == rt.RT_EINVAL
