@@ -291,7 +291,7 @@ def main():
         return max_over_ranks(ev0.elapsed_time(ev1) / k, dist, "cuda")
 
     # ---- mixed-precision ALI iterations (the headline) ----
-    # The marches of consecutive angle blocks alternate between two streams and
+    # The marches of consecutive angle blocks alternate between three streams and
     # overlap where one drains and the next starts, so the march's throughput is
     # taken over the event-timed step: all march bytes of a step over the step's
     # duration (the step's other kernels count against it).  Every TIMING_EVERY-th
@@ -420,8 +420,8 @@ def main():
                          else "fallback 6800 GB/s", "traffic_source": traffic_src,
                          "timing": "march bytes of a step (one launch per angle block, %d blocks) over the "
                                    "event-timed step on the bench stream (avg_launch_ms = step / blocks): the "
-                                   "marches alternate between two streams and overlap at their ends, the J gather "
-                                   "of the previous angle block runs on a third; avg_launch_ms_events = CUDA events "
+                                   "marches alternate between three streams and overlap at their ends, the J gathers "
+                                   "run in block order on a fourth; avg_launch_ms_events = CUDA events "
                                    "on the march's own stream around every %d-th launch (%d launches), windows "
                                    "that overlap the neighbouring launches" % (info["n_blocks"], TIMING_EVERY,
                                                                                tm["march_launches"]),

@@ -196,11 +196,12 @@ int rt_set_precision(rt_grid *g, int precision);
  * RT_TUNE_NN_JTOL bound, then Jacobi sweeps confirm that bound; 0 runs the
  * Jacobi sweeps alone.  Both stop on the same criterion. */
 #define RT_TUNE_NN_KRYLOV 12
-/* RT_TUNE_MARCH_STREAMS (default 2): with RT_TUNE_OVERLAP, the marches of
- * consecutive angle blocks alternate between 1 or 2 streams, so that the next
- * block's march can start while the last CTAs of the previous one finish.  The
- * gathers still run in block order on their own stream: both give bit-identical
- * J. */
+/* RT_TUNE_MARCH_STREAMS (default 3): with RT_TUNE_OVERLAP, the marches of
+ * consecutive angle blocks alternate between 1, 2 or 3 streams (the FP64 march
+ * uses at most 2), so that the next block's march can start while the last CTAs
+ * of the previous one finish; with 3 the FP32 per-segment values are triple
+ * buffered.  The gathers still run in block order on their own stream: all give
+ * bit-identical J. */
 #define RT_TUNE_MARCH_STREAMS 13
 int rt_tune(rt_grid *g, int knob, int value);
 

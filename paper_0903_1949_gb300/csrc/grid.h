@@ -100,9 +100,10 @@ struct rt_grid {
     int *d_err = nullptr;     // raised by a bounded device wait that gave up
     int32_t *d_pos = nullptr; // list position of every segment within its block (NULL: not available)
     cudaStream_t st2 = nullptr;  // second stream of the overlapped gather (created on first use)
-    cudaStream_t st3 = nullptr;  // second march stream (RT_TUNE_MARCH_STREAMS 2; created on first use)
-    int sw_mstreams = 2;         // march streams of the overlapped J-only formal solution (RT_TUNE_MARCH_STREAMS)
-    cudaEvent_t sev[7] = {};     // fork, join, march done x2, gather done x2, join of st3
+    cudaStream_t st3 = nullptr;  // second and third march streams (RT_TUNE_MARCH_STREAMS; created on first use)
+    cudaStream_t st4 = nullptr;
+    int sw_mstreams = 3;         // march streams of the overlapped J-only formal solution (RT_TUNE_MARCH_STREAMS)
+    cudaEvent_t sev[10] = {};    // fork, join, march done x3, gather done x3, joins of st3 and st4
     int2 *d_bnd = nullptr;    // bundle bounds of every block for bnd_chunk
     // nearest-neighbour Lambda* (use_lstar = 2)
     double *d_L27 = nullptr;            // 27 per voxel

@@ -95,6 +95,8 @@ void release(rt_grid *g)
     g->st2 = nullptr;
     if (g->st3) cudaStreamDestroy(g->st3);
     g->st3 = nullptr;
+    if (g->st4) cudaStreamDestroy(g->st4);
+    g->st4 = nullptr;
     for (void *p : g->allocs) cudaFree(p);
     g->allocs.clear();
     if (g->h_pin) cudaFreeHost(g->h_pin);
@@ -936,8 +938,10 @@ int run_fs_J_sw(rt_grid *g, int prec, int homog, const double *S_src, double *J)
 {
     const bool f64 = prec == RT_FP64;
     const bool scatter = g->sw_scatter && g->d_pos;
-    // double buffer of per-segment values: FP32 or FP64 (the segment buffer holds 16 bytes per segment)
-    float *b32[2] = {(float *)g->d_segbuf, (float *)g->d_segbuf + g->max_blk_seg};
+    // double (FP64) or up to triple (FP32) buffer of per-segment values: the
+    // segment buffer holds 16 bytes per segment of the largest block
+    float *b32[3] = {(float *)g->d_segbuf, (float *)g->d_segbuf + g->max_blk_seg,
+                     (float *)g->d_segbuf + 2 * g->max_blk_seg};
     double *b64[2] = {(double *)g->d_segbuf, (double *)g->d_segbuf + g->max_blk_seg};
     const int64_t bps = f64 ? (scatter ? 48 : 44) : (scatter ? 28 : 24);  // streamed bytes per segment
     auto segs = [&](int b) -> int64_t {
@@ -977,34 +981,39 @@ int run_fs_J_sw(rt_grid *g, int prec, int homog, const double *S_src, double *J)
         CK(cudaStreamCreateWithFlags(&g->st2, cudaStreamNonBlocking));
         for (cudaEvent_t &e : g->sev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    cudaEvent_t fork = g->sev[0], join = g->sev[1], *mdone = g->sev + 2, *gdone = g->sev + 4;
-    cudaStream_t ms[2] = {g->st, g->st};
-    if (g->sw_mstreams == 2 && g->nblk > 1) {
-        if (!g->st3) CK(cudaStreamCreateWithFlags(&g->st3, cudaStreamNonBlocking));
-        ms[1] = g->st3;
+    // events: fork, join, march done and gather done per buffer, join of each extra march stream
+    cudaEvent_t fork = g->sev[0], join = g->sev[1], *mdone = g->sev + 2, *gdone = g->sev + 5, *mjoin = g->sev + 8;
+    const int nms = std::min(g->nblk, f64 ? std::min(g->sw_mstreams, 2) : g->sw_mstreams);
+    const int nbuf = std::max(2, nms);  // a buffer per march that may run at once
+    cudaStream_t ms[3] = {g->st, g->st3, g->st4};
+    for (int q = 1; q < nms; ++q) {
+        cudaStream_t &sq = q == 1 ? g->st3 : g->st4;
+        if (!sq) CK(cudaStreamCreateWithFlags(&sq, cudaStreamNonBlocking));
+        ms[q] = sq;
     }
     CK(cudaEventRecord(fork, g->st));
     CK(cudaStreamWaitEvent(g->st2, fork, 0));
-    if (ms[1] != g->st) CK(cudaStreamWaitEvent(ms[1], fork, 0));
+    for (int q = 1; q < nms; ++q) CK(cudaStreamWaitEvent(ms[q], fork, 0));
     for (int b = 0; b < g->nblk; ++b) {
-        cudaStream_t s = ms[b & 1];
-        if (b >= 2) CK(cudaStreamWaitEvent(s, gdone[b & 1], 0));
+        const int q = b % nbuf;
+        cudaStream_t s = ms[b % nms];
+        if (b >= nbuf) CK(cudaStreamWaitEvent(s, gdone[q], 0));  // the gather that read buffer q
         int t0 = tstart(g, 0, s);
-        CK(march(b, b & 1, s));
+        CK(march(b, q, s));
         tstop(g, t0, 0, segs(b), bps * segs(b), s);
-        CK(cudaEventRecord(mdone[b & 1], s));
-        CK(cudaStreamWaitEvent(g->st2, mdone[b & 1], 0));
+        CK(cudaEventRecord(mdone[q], s));
+        CK(cudaStreamWaitEvent(g->st2, mdone[q], 0));
         t0 = tstart(g, 1, g->st2);
-        CK(gather(b, b & 1, g->st2));
+        CK(gather(b, q, g->st2));
         tstop(g, t0, 1, segs(b), 0, g->st2);
-        CK(cudaEventRecord(gdone[b & 1], g->st2));
+        CK(cudaEventRecord(gdone[q], g->st2));
         g->launches += 2;
     }
     CK(cudaEventRecord(join, g->st2));
     CK(cudaStreamWaitEvent(g->st, join, 0));
-    if (ms[1] != g->st) {
-        CK(cudaEventRecord(g->sev[6], ms[1]));
-        CK(cudaStreamWaitEvent(g->st, g->sev[6], 0));
+    for (int q = 1; q < nms; ++q) {
+        CK(cudaEventRecord(mjoin[q - 1], ms[q]));
+        CK(cudaStreamWaitEvent(g->st, mjoin[q - 1], 0));
     }
     return RT_OK;
 }
@@ -1471,7 +1480,7 @@ int rt_tune(rt_grid *g, int knob, int value)
         return RT_OK;
     }
     if (knob == RT_TUNE_MARCH_STREAMS) {
-        if (value != 1 && value != 2) return fail(RT_EINVAL, "march streams: 1 or 2");
+        if (value < 1 || value > 3) return fail(RT_EINVAL, "march streams: 1, 2 or 3");
         g->sw_mstreams = value;
         return RT_OK;
     }
