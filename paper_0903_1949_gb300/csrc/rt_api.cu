@@ -928,12 +928,13 @@ SwGather sw_gather(rt_grid *g, int b, const float *buf, double *J)
     return t;
 }
 
-// Streamed-weight J.  Overlapped: the march of block b (grid stream, into
-// buffer b % 2) waits only for the gather of block b - 2, which read that
-// buffer; the gathers run in block order on the second stream, each after its
-// march, so J accumulates in the same order as without overlap.  With two
-// march streams the odd blocks are marched on a third stream, so a march may
-// begin while the previous one drains.
+// Streamed-weight J.  Overlapped: the march of block b writes buffer
+// b % nbuf (nbuf = max(2, march streams)) and waits only for the gather of
+// block b - nbuf, which read that buffer; the gathers run in block order on
+// the second stream, each after its march, so J accumulates in the same order
+// as without overlap.  With several march streams block b is marched on
+// stream b % nms (the grid's stream first), so a march may begin while the
+// previous one drains.
 int run_fs_J_sw(rt_grid *g, int prec, int homog, const double *S_src, double *J)
 {
     const bool f64 = prec == RT_FP64;
