@@ -60,3 +60,36 @@ def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
 
     bench.run_reference(Args())
     assert capsys.readouterr().out == ""
+
+
+def test_traffic_is_taken_only_from_a_capture_of_the_current_source(tmp_path, monkeypatch):
+    """roofline.traffic scales the committed DRAM bytes per segment to a launch,
+    and is withheld ("stale") once the march source differs from the one captured."""
+    import hashlib
+    import json
+
+    import bench
+
+    d = json.load(open(os.path.join(bench.ROOT, "profiles", "march_sw_traffic.json")))
+    src = open(bench.MARCH_SRC, "rb").read()
+    value, why = bench.ncu_traffic(1.0e6)
+    if d["source_sha256"] == hashlib.sha256(src).hexdigest():
+        assert value == pytest.approx(d["dram_bytes_per_segment"] * 1.0e6)
+        assert why == d["capture"]
+    else:
+        assert (value, why) == (None, "stale")
+    edited = tmp_path / "fs_sw.cu"
+    edited.write_bytes(src + b"\n// edited\n")
+    monkeypatch.setattr(bench, "MARCH_SRC", str(edited))
+    assert bench.ncu_traffic(1.0e6) == (None, "stale")
+
+
+def test_peak_falls_back_without_measured_peaks(tmp_path, monkeypatch):
+    import json
+
+    import bench
+
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.hbm_peak() == (bench.DEFAULT_HBM_FALLBACK, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6500.0}))
+    assert bench.hbm_peak() == (6500.0, "measured")
