@@ -203,6 +203,12 @@ int rt_set_precision(rt_grid *g, int precision);
  * buffered.  The gathers still run in block order on their own stream: all give
  * bit-identical J. */
 #define RT_TUNE_MARCH_STREAMS 13
+/* RT_TUNE_GRAPH (default 1): the overlapped J-only formal solution of the
+ * iteration is captured as one CUDA graph at its second call with the same
+ * precision, S and J, and replayed from then on (any rt_tune or
+ * rt_set_opacity drops it; not used while rt_set_timing is on).  Bit-identical
+ * J. */
+#define RT_TUNE_GRAPH 15
 int rt_tune(rt_grid *g, int knob, int value);
 
 /* Formal solution from the current S with the grid's precision: J, the

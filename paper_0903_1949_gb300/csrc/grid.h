@@ -103,6 +103,20 @@ struct rt_grid {
     cudaStream_t st3 = nullptr;  // second and third march streams (RT_TUNE_MARCH_STREAMS; created on first use)
     cudaStream_t st4 = nullptr;
     int sw_mstreams = 3;         // march streams of the overlapped J-only formal solution (RT_TUNE_MARCH_STREAMS)
+    // the overlapped J-only formal solution as one CUDA graph (RT_TUNE_GRAPH): captured on
+    // a private stream at the second call with the same arguments, replayed on st; two
+    // argument sets are kept (the FP64 residual and the FP32 corrections of rt_solve)
+    struct FsGraph {
+        cudaGraphExec_t exec = nullptr;
+        int prec = -1, homog = -1, calls = 0;
+        const void *S = nullptr, *J = nullptr;
+        int64_t launches = 0;    // kernel launches of one replay
+        uint64_t used = 0;
+    };
+    int sw_graph = 1;
+    cudaStream_t stc = nullptr;
+    FsGraph fsg[2];
+    uint64_t fsg_tick = 0;
     cudaEvent_t sev[10] = {};    // fork, join, march done x3, gather done x3, joins of st3 and st4
     int2 *d_bnd = nullptr;    // bundle bounds of every block for bnd_chunk
     // nearest-neighbour Lambda* (use_lstar = 2)

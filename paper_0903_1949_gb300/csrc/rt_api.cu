@@ -85,8 +85,21 @@ void dfree(rt_grid *g, void *p)
     }
 }
 
+// Forget the captured J-only formal solution (its arguments, knobs or the
+// arrays it reads may have changed).
+void drop_graph(rt_grid *g)
+{
+    for (rt_grid::FsGraph &f : g->fsg) {
+        if (f.exec) cudaGraphExecDestroy(f.exec);
+        f = rt_grid::FsGraph{};
+    }
+}
+
 void release(rt_grid *g)
 {
+    drop_graph(g);
+    if (g->stc) cudaStreamDestroy(g->stc);
+    g->stc = nullptr;
     for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
     g->ev.clear();
     for (cudaEvent_t &e : g->sev)
@@ -935,6 +948,8 @@ SwGather sw_gather(rt_grid *g, int b, const float *buf, double *J)
 // as without overlap.  With several march streams block b is marched on
 // stream b % nms (the grid's stream first), so a march may begin while the
 // previous one drains.
+int run_fs_J_sw_streams(rt_grid *g, int prec, int homog, const double *S_src, double *J, cudaStream_t base);
+
 int run_fs_J_sw(rt_grid *g, int prec, int homog, const double *S_src, double *J)
 {
     const bool f64 = prec == RT_FP64;
@@ -948,8 +963,102 @@ int run_fs_J_sw(rt_grid *g, int prec, int homog, const double *S_src, double *J)
     auto segs = [&](int b) -> int64_t {
         return g->h_ang_seg_off[g->blk_w0[b] + g->blk_nw[b]] - g->h_ang_seg_off[g->blk_w0[b]];
     };
+    auto march = [&](int b, int q, cudaStream_t st) -> cudaError_t {
+        if (!f64) return march_sw_launch(sw_march(g, b, homog, b32[q]), g->sw_coarsen, st);
+        SwMarch64 m = sw_march64(g, b, homog, b64[q]);
+        m.S = S_src;
+        return march_sw64_launch(m, g->sw64_coarsen, st);
+    };
+    auto gather = [&](int b, int q, cudaStream_t st) -> cudaError_t {
+        SwGather t = sw_gather(g, b, b32[q], J);
+        if (f64) {
+            t.buf = nullptr;
+            t.buf64 = b64[q];
+        }
+        return scatter ? gather_rows_sw_launch(t, g->nvox, st) : gather_sw_launch(t, st);
+    };
+    if (!g->sw_overlap) {
+        if (!f64 && g->sblk && build_sblk(g)) {  // this step's FP32 S and B in the blocked order
+            CK(blk_scatter(g->nvox, g->d_vblk, g->d_S32, g->d_B32, g->d_S32b, g->d_B32b, g->st));
+            g->launches++;
+        }
+        for (int b = 0; b < g->nblk; ++b) {
+            int t0 = tstart(g, 0);
+            CK(march(b, 0, g->st));
+            tstop(g, t0, 0, segs(b), bps * segs(b));
+            t0 = tstart(g, 1);
+            CK(gather(b, 0, g->st));
+            tstop(g, t0, 1, segs(b));
+            g->launches += 2;
+        }
+        return RT_OK;
+    }
+    if (!g->st2) {
+        CK(cudaStreamCreateWithFlags(&g->st2, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : g->sev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    if (g->sw_graph && !g->timing) {
+        rt_grid::FsGraph *f = nullptr;
+        for (rt_grid::FsGraph &c : g->fsg)
+            if (c.prec == prec && c.homog == homog && c.S == (const void *)S_src && c.J == (const void *)J) f = &c;
+        if (!f) {  // take the least recently used entry for these arguments
+            f = g->fsg[0].used <= g->fsg[1].used ? &g->fsg[0] : &g->fsg[1];
+            if (f->exec) cudaGraphExecDestroy(f->exec);
+            *f = rt_grid::FsGraph{};
+            f->prec = prec;
+            f->homog = homog;
+            f->S = S_src;
+            f->J = J;
+        }
+        f->used = ++g->fsg_tick;
+        if (!f->exec && f->calls >= 1) {  // the first call ran directly: lazy set-up is done
+            if (!g->stc) CK(cudaStreamCreateWithFlags(&g->stc, cudaStreamNonBlocking));
+            const int64_t l0 = g->launches;
+            cudaError_t ec = cudaStreamBeginCapture(g->stc, cudaStreamCaptureModeRelaxed);
+            if (ec == cudaSuccess) {
+                const int rc = run_fs_J_sw_streams(g, prec, homog, S_src, J, g->stc);
+                cudaGraph_t graph = nullptr;
+                ec = cudaStreamEndCapture(g->stc, &graph);
+                f->launches = g->launches - l0;
+                g->launches = l0;
+                if (rc != RT_OK) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return rc;
+                }
+                if (ec == cudaSuccess) ec = cudaGraphInstantiate(&f->exec, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+            }
+            if (ec != cudaSuccess) {  // no graph on this grid: the same launches, one by one
+                cudaGetLastError();
+                f->exec = nullptr;
+                g->sw_graph = 0;
+            }
+        }
+        f->calls++;
+        if (f->exec) {
+            CK(cudaGraphLaunch(f->exec, g->st));
+            g->launches += f->launches;
+            return RT_OK;
+        }
+    }
+    return run_fs_J_sw_streams(g, prec, homog, S_src, J, g->st);
+}
+
+// The overlapped streamed-weight J on base stream `base` (the grid's stream, or
+// the private stream the graph is captured on).
+int run_fs_J_sw_streams(rt_grid *g, int prec, int homog, const double *S_src, double *J, cudaStream_t base)
+{
+    const bool f64 = prec == RT_FP64;
+    const bool scatter = g->sw_scatter && g->d_pos;
+    float *b32[3] = {(float *)g->d_segbuf, (float *)g->d_segbuf + g->max_blk_seg,
+                     (float *)g->d_segbuf + 2 * g->max_blk_seg};
+    double *b64[2] = {(double *)g->d_segbuf, (double *)g->d_segbuf + g->max_blk_seg};
+    const int64_t bps = f64 ? (scatter ? 48 : 44) : (scatter ? 28 : 24);  // streamed bytes per segment
+    auto segs = [&](int b) -> int64_t {
+        return g->h_ang_seg_off[g->blk_w0[b] + g->blk_nw[b]] - g->h_ang_seg_off[g->blk_w0[b]];
+    };
     if (!f64 && g->sblk && build_sblk(g)) {  // this step's FP32 S and B in the blocked order
-        CK(blk_scatter(g->nvox, g->d_vblk, g->d_S32, g->d_B32, g->d_S32b, g->d_B32b, g->st));
+        CK(blk_scatter(g->nvox, g->d_vblk, g->d_S32, g->d_B32, g->d_S32b, g->d_B32b, base));
         g->launches++;
     }
     auto march = [&](int b, int q, cudaStream_t st) -> cudaError_t {
@@ -966,33 +1075,17 @@ int run_fs_J_sw(rt_grid *g, int prec, int homog, const double *S_src, double *J)
         }
         return scatter ? gather_rows_sw_launch(t, g->nvox, st) : gather_sw_launch(t, st);
     };
-    if (!g->sw_overlap) {
-        for (int b = 0; b < g->nblk; ++b) {
-            int t0 = tstart(g, 0);
-            CK(march(b, 0, g->st));
-            tstop(g, t0, 0, segs(b), bps * segs(b));
-            t0 = tstart(g, 1);
-            CK(gather(b, 0, g->st));
-            tstop(g, t0, 1, segs(b));
-            g->launches += 2;
-        }
-        return RT_OK;
-    }
-    if (!g->st2) {
-        CK(cudaStreamCreateWithFlags(&g->st2, cudaStreamNonBlocking));
-        for (cudaEvent_t &e : g->sev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    }
     // events: fork, join, march done and gather done per buffer, join of each extra march stream
     cudaEvent_t fork = g->sev[0], join = g->sev[1], *mdone = g->sev + 2, *gdone = g->sev + 5, *mjoin = g->sev + 8;
     const int nms = std::min(g->nblk, f64 ? std::min(g->sw_mstreams, 2) : g->sw_mstreams);
     const int nbuf = std::max(2, nms);  // a buffer per march that may run at once
-    cudaStream_t ms[3] = {g->st, g->st3, g->st4};
+    cudaStream_t ms[3] = {base, g->st3, g->st4};
     for (int q = 1; q < nms; ++q) {
         cudaStream_t &sq = q == 1 ? g->st3 : g->st4;
         if (!sq) CK(cudaStreamCreateWithFlags(&sq, cudaStreamNonBlocking));
         ms[q] = sq;
     }
-    CK(cudaEventRecord(fork, g->st));
+    CK(cudaEventRecord(fork, base));
     CK(cudaStreamWaitEvent(g->st2, fork, 0));
     for (int q = 1; q < nms; ++q) CK(cudaStreamWaitEvent(ms[q], fork, 0));
     for (int b = 0; b < g->nblk; ++b) {
@@ -1011,10 +1104,10 @@ int run_fs_J_sw(rt_grid *g, int prec, int homog, const double *S_src, double *J)
         g->launches += 2;
     }
     CK(cudaEventRecord(join, g->st2));
-    CK(cudaStreamWaitEvent(g->st, join, 0));
+    CK(cudaStreamWaitEvent(base, join, 0));
     for (int q = 1; q < nms; ++q) {
         CK(cudaEventRecord(mjoin[q - 1], ms[q]));
-        CK(cudaStreamWaitEvent(g->st, mjoin[q - 1], 0));
+        CK(cudaStreamWaitEvent(base, mjoin[q - 1], 0));
     }
     return RT_OK;
 }
@@ -1384,6 +1477,7 @@ int rt_set_opacity(rt_grid *g, const double *chi, const double *eps, const doubl
     if (!g || !chi || !eps || !B) return fail(RT_EINVAL, "NULL argument");
     if (where != RT_HOST && where != RT_DEVICE) return fail(RT_EINVAL, "where must be RT_HOST or RT_DEVICE");
     CK(cudaSetDevice(g->device));
+    drop_graph(g);
     const size_t n = g->nvox;
     if (where == RT_HOST) {
         for (size_t v = 0; v < n; ++v) {
@@ -1425,6 +1519,12 @@ int rt_set_S(rt_grid *g, const double *S, int where)
 int rt_tune(rt_grid *g, int knob, int value)
 {
     if (!g) return fail(RT_EINVAL, "grid is NULL");
+    drop_graph(g);  // a captured formal solution holds the old settings
+    if (knob == RT_TUNE_GRAPH) {
+        if (value != 0 && value != 1) return fail(RT_EINVAL, "graph: 0 or 1");
+        g->sw_graph = value;
+        return RT_OK;
+    }
     if (knob == RT_TUNE_MARCH_CHUNK) {
         if (value < 64 || value > 16384) return fail(RT_EINVAL, "march chunk must be in [64, 16384]");
         g->march_chunk = value;

@@ -48,7 +48,7 @@ def _iterate(p, interp, knobs, precision=rt.RT_MIXED, angle_block=0):
 T = rt
 BASE = {T.RT_TUNE_STREAMED_WEIGHTS: 1, T.RT_TUNE_MARCH_COARSEN: 2, T.RT_TUNE_MARCH_CHUNK: 512, T.RT_TUNE_SCATTER: 1,
         T.RT_TUNE_OVERLAP: 1, T.RT_TUNE_MARCH_STAGES: 0, T.RT_TUNE_MARCH_BULK: 0, T.RT_TUNE_MARCH_LOOKAHEAD: 1,
-        T.RT_TUNE_S_BLOCKED: 1, T.RT_TUNE_MARCH_STREAMS: 3}
+        T.RT_TUNE_S_BLOCKED: 1, T.RT_TUNE_MARCH_STREAMS: 3, T.RT_TUNE_GRAPH: 1}
 # same arithmetic in the same order, data moved differently: bit-identical
 SAME = [
     {T.RT_TUNE_S_BLOCKED: 0},
@@ -107,12 +107,13 @@ def test_fp64_march_configurations(name):
 @pytest.mark.parametrize("precision", [rt.RT_MIXED, rt.RT_FP64])
 def test_march_streams_give_identical_iterates(precision):
     """Angle blocks of 5 solid angles (13 blocks of sph17): the marches on one
-    stream or alternating between two or three, and without overlap, give the
-    same bits."""
+    stream or alternating between two or three, replayed as a CUDA graph or
+    launched one by one, and without overlap, give the same bits."""
     p, interp = _problems()["sph17"]
     S0 = _iterate(p, interp, BASE, precision, angle_block=5)
     for var in ({T.RT_TUNE_MARCH_STREAMS: 1}, {T.RT_TUNE_MARCH_STREAMS: 1, T.RT_TUNE_SCATTER: 0},
                 {T.RT_TUNE_MARCH_STREAMS: 2}, {T.RT_TUNE_MARCH_STREAMS: 2, T.RT_TUNE_SCATTER: 0},
+                {T.RT_TUNE_GRAPH: 0}, {T.RT_TUNE_GRAPH: 0, T.RT_TUNE_MARCH_STREAMS: 1},
                 {T.RT_TUNE_SCATTER: 0},
                 {T.RT_TUNE_OVERLAP: 0}):
         assert np.array_equal(_iterate(p, interp, {**BASE, **var}, precision, angle_block=5), S0), var
@@ -127,7 +128,7 @@ def test_tune_rejects_bad_values():
     for knob, bad in ((T.RT_TUNE_MARCH_CHUNK, 32), (T.RT_TUNE_MARCH_COARSEN, 3), (T.RT_TUNE_MARCH_STAGES, 1),
                       (T.RT_TUNE_MARCH_STAGES, 5), (T.RT_TUNE_MARCH_BULK, 2), (T.RT_TUNE_SCATTER, -1),
                       (T.RT_TUNE_OVERLAP, 7), (T.RT_TUNE_STREAMED_WEIGHTS, 3), (T.RT_TUNE_MARCH_LOOKAHEAD, 2),
-                      (T.RT_TUNE_S_BLOCKED, 2), (T.RT_TUNE_MARCH_STREAMS, 0), (T.RT_TUNE_MARCH_STREAMS, 4), (99, 1)):
+                      (T.RT_TUNE_S_BLOCKED, 2), (T.RT_TUNE_MARCH_STREAMS, 0), (T.RT_TUNE_MARCH_STREAMS, 4), (T.RT_TUNE_GRAPH, 2), (99, 1)):
         with pytest.raises(rt.RtError) as ei:
             g.tune(knob, bad)
         assert ei.value.code == rt.RT_EINVAL
