@@ -209,6 +209,13 @@ int rt_set_precision(rt_grid *g, int precision);
  * rt_set_opacity drops it; not used while rt_set_timing is on).  Bit-identical
  * J. */
 #define RT_TUNE_GRAPH 15
+/* RT_TUNE_GEOM_PREDICT (default 0), set with g = NULL for the grids created
+ * afterwards: the coverage completion of the launch set walks each candidate
+ * voxel's characteristic in float first and traces exactly (FP64) only
+ * candidates that no earlier chosen candidate's guessed line crosses; the
+ * decisions stay the exact serial ones, so the launch set and the crossing
+ * lists are the same as with 0.  Other knobs need a grid. */
+#define RT_TUNE_GEOM_PREDICT 16
 int rt_tune(rt_grid *g, int knob, int value);
 
 /* Formal solution from the current S with the grid's precision: J, the

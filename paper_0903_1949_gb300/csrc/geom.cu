@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "geom_pred.cuh"
 #include "rt_internal.h"
 
 namespace rtk {
@@ -598,6 +599,190 @@ __global__ void __launch_bounds__(32 * CPL_WARPS) k_complete(GeomDev G, const do
     }
 }
 
+// Candidates the predictor may hold back in one round of k_complete_pred.
+constexpr int PRED_PREFIX = 256;
+
+struct PredVisit {
+    int32_t *list;
+    int cap, n;
+    __device__ void cell(int v)
+    {
+        if (n < cap) list[n] = v;
+        n++;
+    }
+};
+
+// The coverage completion of k_complete with a guess of which candidates will
+// be hit.  A round looks at the unhit voxels in increasing order, 32 at a time:
+// each is walked in float (pwalk) and, in voxel order, either held back (an
+// earlier chosen candidate's guessed line crosses it: stamp[v] == round) or
+// chosen, up to 32 chosen; the chosen ones are traced exactly (FP64 walk) and
+// then every voxel of the round is decided in voxel order as the serial rule
+// does: a voxel hit by then is skipped, a chosen unhit one is launched, and a
+// held-back unhit one ends the round (it is the next round's first candidate,
+// which is always chosen, so every round launches at least one characteristic).
+__global__ void __launch_bounds__(32) k_complete_pred(GeomDev G, GeomF F, const double *dirs, int w0, int nw,
+                                                      uint32_t *hit, uint32_t *comp, int words, int32_t *scratch,
+                                                      int32_t *pscr, int32_t *stamp, int cap, int *lost,
+                                                      uint32_t *cnt)
+{
+    __shared__ int cand[32];
+    __shared__ int prefv[PRED_PREFIX];
+    __shared__ uint32_t prefsel[PRED_PREFIX / 32];
+    __shared__ int selv[32];
+    const int lane = threadIdx.x & 31;
+    const int wl = blockIdx.x;
+    if (wl >= nw) return;
+    const int w = w0 + wl;
+    const double dx = dirs[3 * w], dy = dirs[3 * w + 1], dz = dirs[3 * w + 2];
+    const float fdx = (float)dx, fdy = (float)dy, fdz = (float)dz;
+    uint32_t *H = hit + (int64_t)wl * words;
+    uint32_t *C = comp + (int64_t)wl * words;
+    int32_t *mylist = scratch + ((int64_t)wl * 32 + lane) * cap;
+    int32_t *myplist = pscr + ((int64_t)wl * 32 + lane) * cap;
+    volatile int32_t *ST = stamp + (int64_t)wl * G.nvox;
+    int pos = 0, round = 0;
+    while (pos < G.nvox) {
+        ++round;
+        if (lane < PRED_PREFIX / 32) prefsel[lane] = 0u;
+        int npref = 0, nsel = 0, scan = pos;
+        bool full = false;
+        __syncwarp();
+        while (!full && npref < PRED_PREFIX && scan < G.nvox) {
+            // the next unhit voxels, in increasing order
+            const int want = min(32, PRED_PREFIX - npref);
+            int ncand = 0, cscan = scan;
+            while (ncand < want && cscan < G.nvox) {
+                uint32_t w0w = 0, w1w = 0;
+                if (lane == 0) {
+                    w0w = read_word(H + (cscan >> 5));
+                    if ((cscan >> 5) + 1 < words) w1w = read_word(H + (cscan >> 5) + 1);
+                }
+                w0w = __shfl_sync(0xffffffffu, w0w, 0);
+                w1w = __shfl_sync(0xffffffffu, w1w, 0);
+                const int v = cscan + lane;
+                const uint32_t word = ((v >> 5) == (cscan >> 5)) ? w0w : w1w;
+                const bool unhit = (v < G.nvox) && !((word >> (v & 31)) & 1u);
+                uint32_t m = __ballot_sync(0xffffffffu, unhit);
+                const int need = want - ncand;
+                const int cntm = __popc(m);
+                int last_taken_lane = 31;
+                if (cntm > need) {
+                    uint32_t mm = m;
+                    for (int q = 0; q < need; ++q) mm &= mm - 1;
+                    m &= ~mm;
+                    last_taken_lane = 31 - __clz(m);
+                }
+                if (unhit && ((m >> lane) & 1u)) cand[ncand + __popc(m & ((1u << lane) - 1u))] = v;
+                ncand += __popc(m);
+                cscan += (cntm > need) ? last_taken_lane + 1 : 32;
+                __syncwarp();
+            }
+            // guessed lines of this batch
+            int pn = 0;
+            if (lane < ncand) {
+                const int v = cand[lane];
+                int i, j, k;
+                ijk_of(G, v, i, j, k);
+                float x, y, z;
+                pcentre(F, i, j, k, x, y, z);
+                PredVisit pv{myplist, cap, 0};
+                pwalk(F, x, y, z, -fdx, -fdy, -fdz, i, j, k, pv);
+                pwalk(F, x, y, z, fdx, fdy, fdz, i, j, k, pv);
+                pn = pv.n < cap ? pv.n : cap;
+            }
+            __syncwarp();
+            // choose in voxel order
+            int m = 0;
+            for (; m < ncand; ++m) {
+                const int v = cand[m];
+                int sv = 0;
+                if (lane == 0) sv = ST[v];
+                sv = __shfl_sync(0xffffffffu, sv, 0);
+                if (sv == round && nsel > 0) {  // held back (the round's first candidate never is)
+                    if (lane == 0) prefv[npref] = v;
+                    npref++;
+                    continue;
+                }
+                if (nsel == 32) break;  // round full: v starts the next one
+                if (lane == 0) {
+                    prefv[npref] = v;
+                    prefsel[npref >> 5] |= 1u << (npref & 31);
+                    selv[nsel] = v;
+                }
+                npref++;
+                nsel++;
+                const int n_m = __shfl_sync(0xffffffffu, pn, m);
+                const int32_t *pl = pscr + ((int64_t)wl * 32 + m) * cap;
+                for (int e = lane; e < n_m; e += 32) ST[pl[e]] = round;
+                __syncwarp();
+            }
+            if (m < ncand) {
+                scan = cand[m];
+                full = true;
+            } else {
+                scan = cscan;
+            }
+            __syncwarp();
+        }
+        // exact traces of the chosen candidates
+        int nl = 0, bad = 0;
+        uint32_t pc = 0;
+        if (lane < nsel) {
+            const int v = selv[lane];
+            int i, j, k;
+            ijk_of(G, v, i, j, k);
+            double x, y, z;
+            centre_of(G, i, j, k, x, y, z);
+            ListVisit lv{mylist, cap, 0};
+            const int eb = walk(G, x, y, z, -dx, -dy, -dz, i, j, k, lv);
+            const int nbk = lv.n;
+            const int ef = walk(G, x, y, z, dx, dy, dz, i, j, k, lv);
+            nl = lv.n < cap ? lv.n : cap;
+            bad = (eb == RTK_END_LOST || ef == RTK_END_LOST || lv.n > cap) ? 1 : 0;
+            pc = pack_counts(nbk, lv.n - nbk, eb == RTK_END_LOST || ef == RTK_END_LOST);
+        }
+        __syncwarp();
+        // decide in voxel order
+        int next = scan, si = 0;
+        for (int e = 0; e < npref; ++e) {
+            const int v = prefv[e];
+            const bool sel = (prefsel[e >> 5] >> (e & 31)) & 1u;
+            const int m = si;
+            if (sel) si++;
+            uint32_t word = 0;
+            if (lane == 0) word = read_word(H + (v >> 5));
+            word = __shfl_sync(0xffffffffu, word, 0);
+            if ((word >> (v & 31)) & 1u) continue;  // hit by then: no launch, as in the serial rule
+            if (!sel) {  // unhit but not traced: the next round starts here
+                next = v;
+                break;
+            }
+            const int n_m = __shfl_sync(0xffffffffu, nl, m);
+            const int bad_m = __shfl_sync(0xffffffffu, bad, m);
+            const uint32_t pc_m = __shfl_sync(0xffffffffu, pc, m);
+            if (bad_m) {
+                if (lane == 0) {
+                    atomicOr(H + (v >> 5), 1u << (v & 31));
+                    atomicAdd(lost, 1);
+                }
+            } else {
+                if (lane == 0) {
+                    atomicOr(C + (v >> 5), 1u << (v & 31));
+                    cnt[(int64_t)w * G.nvox + v] = pc_m;
+                }
+                const int32_t *lst = scratch + ((int64_t)wl * 32 + m) * cap;
+                for (int q = lane; q < n_m; q += 32) {
+                    const int u = lst[q];
+                    atomicOr(H + (u >> 5), 1u << (u & 31));
+                }
+            }
+            __syncwarp();
+        }
+        pos = next;
+    }
+}
+
 __device__ __forceinline__ int ray_kind(const GeomDev &G, int pass, int v, double dx, double dy, double dz,
                                         const uint32_t *C)
 {
@@ -723,6 +908,14 @@ cudaError_t geom_complete(const GeomDev &G, const double *dirs, int w0, int nw, 
 {
     k_complete<<<(nw + CPL_WARPS - 1) / CPL_WARPS, 32 * CPL_WARPS, 0, st>>>(G, dirs, w0, nw, hit, comp, words, scratch,
                                                                            cap, lost, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t geom_complete_pred(const GeomDev &G, const GeomF &F, const double *dirs, int w0, int nw, uint32_t *hit,
+                               uint32_t *comp, int words, int32_t *scratch, int32_t *pscr, int32_t *stamp, int cap,
+                               int *lost, uint32_t *cnt, cudaStream_t st)
+{
+    k_complete_pred<<<nw, 32, 0, st>>>(G, F, dirs, w0, nw, hit, comp, words, scratch, pscr, stamp, cap, lost, cnt);
     return cudaGetLastError();
 }
 

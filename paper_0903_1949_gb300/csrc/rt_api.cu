@@ -15,6 +15,7 @@
 #include <string>
 #include <vector>
 
+#include "geom_pred.cuh"
 #include "rt_internal.h"
 
 using namespace rtk;
@@ -267,6 +268,64 @@ int upload_tables(rt_grid *g)
 }
 
 // Launch set, crossing lists and ownership lists of every solid angle.
+// Library-wide: grids created from now on complete their launch sets with the
+// float-guided completion (RT_TUNE_GEOM_PREDICT on a NULL grid).
+int g_geom_predict = 0;
+
+// Float copies of the geometry tables for the guided completion, on the device
+// (freed by the caller through dfree).
+int upload_tables_f(rt_grid *g, GeomF &F, std::vector<void *> &owned)
+{
+    const bool sph = g->coord == RT_SPHERICAL;
+    const std::vector<double> &pe = sph ? g->h_e[2] : g->h_e[1];
+    const int nphi = g->nphi;
+    std::vector<float> cp(nphi), sp(nphi), cpm(nphi), spm(nphi), ct(1, 0.0f), ctm(1, 0.0f), stm(1, 0.0f);
+    for (int k = 0; k < nphi; ++k) {
+        const double pm = 0.5 * (pe[k] + pe[k + 1]);
+        cp[k] = (float)std::cos(pe[k]);
+        sp[k] = (float)std::sin(pe[k]);
+        cpm[k] = (float)std::cos(pm);
+        spm[k] = (float)std::sin(pm);
+    }
+    if (sph) {
+        ct.resize(g->n2 + 1);
+        ctm.resize(g->n2);
+        stm.resize(g->n2);
+        for (int j = 0; j <= g->n2; ++j) ct[j] = (float)std::cos(g->h_e[1][j]);
+        for (int j = 0; j < g->n2; ++j) {
+            const double tm = 0.5 * (g->h_e[1][j] + g->h_e[1][j + 1]);
+            ctm[j] = (float)std::cos(tm);
+            stm[j] = (float)std::sin(tm);
+        }
+    }
+    std::vector<float> e1(g->h_e[0].begin(), g->h_e[0].end()), e3(g->h_e[2].begin(), g->h_e[2].end());
+    auto up = [&](const std::vector<float> &h, const float **out) -> int {
+        float *p = nullptr;
+        RCK(dalloc(g, &p, h.size()));
+        owned.push_back(p);
+        CK(cudaMemcpyAsync(p, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, g->st));
+        *out = p;
+        return RT_OK;
+    };
+    RCK(up(e1, &F.e1));
+    RCK(up(e3, &F.e3));
+    RCK(up(ct, &F.ct));
+    RCK(up(ctm, &F.ctm));
+    RCK(up(stm, &F.stm));
+    RCK(up(cp, &F.cp));
+    RCK(up(sp, &F.sp));
+    RCK(up(cpm, &F.cpm));
+    RCK(up(spm, &F.spm));
+    F.coord = g->coord;
+    F.n1 = g->n1;
+    F.n2 = g->n2;
+    F.n3 = g->n3;
+    F.nphi = g->nphi;
+    F.inner_bc = g->inner_bc;
+    F.nvox = g->nvox;
+    return RT_OK;
+}
+
 int build_geometry(rt_grid *g)
 {
     auto t0 = std::chrono::steady_clock::now();
@@ -279,12 +338,21 @@ int build_geometry(rt_grid *g)
     CK(cudaMemsetAsync(comp, 0, sizeof(uint32_t) * (size_t)n_ang * words, g->st));
     // launch set: boundary marks, then serial-order coverage completion, in angle chunks
     const int cap = geom_scratch_cap(g->G);
-    const int64_t per_angle = (int64_t)words * 4 + (int64_t)32 * cap * 4;
+    const bool guided = g_geom_predict != 0;
+    const int64_t per_angle =
+        (int64_t)words * 4 + (int64_t)32 * cap * 4 + (guided ? (int64_t)32 * cap * 4 + (int64_t)nvox * 4 : 0);
     int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(n_ang, ((int64_t)1 << 31) / per_angle));
     uint32_t *hit = nullptr;
-    int32_t *scratch = nullptr;
+    int32_t *scratch = nullptr, *pscr = nullptr, *stamp = nullptr;
     RCK(dalloc(g, &hit, (size_t)chunk * words));
     RCK(dalloc(g, &scratch, (size_t)chunk * 32 * cap));
+    GeomF F{};
+    std::vector<void *> ftab;
+    if (guided) {
+        RCK(dalloc(g, &pscr, (size_t)chunk * 32 * cap));
+        RCK(dalloc(g, &stamp, (size_t)chunk * nvox));
+        RCK(upload_tables_f(g, F, ftab));
+    }
     // walk counts of every launched characteristic (n_ang x n_vox), recorded by the launch-set passes
     uint32_t *wcnt = nullptr;
     RCK(dalloc(g, &wcnt, (size_t)n_ang * nvox));
@@ -292,11 +360,20 @@ int build_geometry(rt_grid *g)
         int nw = std::min(chunk, n_ang - w0);
         CK(cudaMemsetAsync(hit, 0, sizeof(uint32_t) * (size_t)nw * words, g->st));
         CK(geom_mark_boundary(g->G, g->d_dirs, w0, nw, hit, words, g->d_lost, wcnt, g->st));
-        CK(geom_complete(g->G, g->d_dirs, w0, nw, hit, comp + (size_t)w0 * words, words, scratch, cap, g->d_lost,
-                         wcnt, g->st));
+        if (guided) {
+            CK(cudaMemsetAsync(stamp, 0, sizeof(int32_t) * (size_t)nw * nvox, g->st));
+            CK(geom_complete_pred(g->G, F, g->d_dirs, w0, nw, hit, comp + (size_t)w0 * words, words, scratch, pscr,
+                                  stamp, cap, g->d_lost, wcnt, g->st));
+        } else {
+            CK(geom_complete(g->G, g->d_dirs, w0, nw, hit, comp + (size_t)w0 * words, words, scratch, cap, g->d_lost,
+                             wcnt, g->st));
+        }
     }
     dfree(g, hit);
     dfree(g, scratch);
+    dfree(g, pscr);
+    dfree(g, stamp);
+    for (void *p : ftab) dfree(g, p);
     // ordered ray lists
     int32_t *counts = nullptr;
     RCK(dalloc(g, &counts, n_ang));
@@ -1518,7 +1595,13 @@ int rt_set_S(rt_grid *g, const double *S, int where)
 
 int rt_tune(rt_grid *g, int knob, int value)
 {
+    if (!g && knob == RT_TUNE_GEOM_PREDICT) {  // library-wide, for grids created afterwards
+        if (value != 0 && value != 1) return fail(RT_EINVAL, "guided completion: 0 or 1");
+        g_geom_predict = value;
+        return RT_OK;
+    }
     if (!g) return fail(RT_EINVAL, "grid is NULL");
+    if (knob == RT_TUNE_GEOM_PREDICT) return fail(RT_EINVAL, "RT_TUNE_GEOM_PREDICT is set on the library (grid NULL)");
     drop_graph(g);  // a captured formal solution holds the old settings
     if (knob == RT_TUNE_GRAPH) {
         if (value != 0 && value != 1) return fail(RT_EINVAL, "graph: 0 or 1");

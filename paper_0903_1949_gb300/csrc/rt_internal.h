@@ -60,6 +60,13 @@ cudaError_t geom_write_segs(const GeomDev &G, const double *dirs, int64_t n_rays
                             const int32_t *ray_angle, const int64_t *ray_off, const int32_t *nback, uint32_t *vox,
                             double *len64, float *len32, int *lost, cudaStream_t st);
 int geom_scratch_cap(const GeomDev &G);
+struct GeomF;
+// Coverage completion guided by a float guess of each candidate's line (same
+// launch set as geom_complete); pscr: 32 lists of cap per solid angle, stamp:
+// n_vox per solid angle, zeroed before the call.
+cudaError_t geom_complete_pred(const GeomDev &G, const GeomF &F, const double *dirs, int w0, int nw, uint32_t *hit,
+                               uint32_t *comp, int words, int32_t *scratch, int32_t *pscr, int32_t *stamp, int cap,
+                               int *lost, uint32_t *cnt, cudaStream_t st);
 
 // ---- scans and small helpers (scan.cu) ----
 // out[0] = 0, out[i+1] = out[i] + in[i]  (n + 1 outputs); tmp holds >= scan_tmp_elems(n) int64.

@@ -89,6 +89,13 @@ def test_null_handles_rejected(lib):
     assert lib.rt_line_get(None, 0, p, rt.RT_HOST) == rt.RT_EINVAL
 
 
+def test_library_wide_knob_takes_a_null_grid(lib):
+    assert lib.rt_tune(None, rt.RT_TUNE_GEOM_PREDICT, 2) == rt.RT_EINVAL
+    assert lib.rt_tune(None, rt.RT_TUNE_GEOM_PREDICT, 1) == rt.RT_OK
+    assert lib.rt_tune(None, rt.RT_TUNE_GEOM_PREDICT, 0) == rt.RT_OK
+    assert lib.rt_tune(None, rt.RT_TUNE_GRAPH, 1) == rt.RT_EINVAL  # the other knobs need a grid
+
+
 def test_struct_layout_matches_header(lib):
     # rt_grid_desc / rt_info sizes as laid out by the C compiler for x86-64 and aarch64
     assert ctypes.sizeof(rt.rt_grid_desc) == 112

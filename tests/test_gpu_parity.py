@@ -233,6 +233,45 @@ def test_full_size_sph65_sampled_crossings(sph65):
         o.free_angle(w)
 
 
+def _guided(p):
+    """A grid whose launch set comes from the float-guided coverage completion
+    (RT_TUNE_GEOM_PREDICT, set on the library for the grids created meanwhile)."""
+    rt.rt_tune(None, rt.RT_TUNE_GEOM_PREDICT, 1)
+    try:
+        return rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"])
+    finally:
+        rt.rt_tune(None, rt.RT_TUNE_GEOM_PREDICT, 0)
+
+
+@pytest.mark.parametrize("name", sorted(GEOMS) + ["sph17"])
+def test_guided_completion_gives_the_same_crossings(name):
+    """The guided completion decides every launch by the serial rule, so the
+    crossing lists equal the oracle's bit for bit."""
+    p = GEOMS[name]() if name in GEOMS else I.make_problem(name)
+    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"])
+    g = _guided(p)
+    assert g.info()["lost_rays"] == 0
+    for w in range(p["n_ang"]):
+        _same_crossings(o, g, w)
+    g.close()
+
+
+def test_full_size_guided_completion(sph65):
+    """65x33x65 voxels, 32x32 solid angles: the same characteristics and
+    segments as the plain completion, sampled crossing lists equal to the
+    oracle's."""
+    p, g = sph65
+    gg = _guided(p)
+    a, b = g.info(), gg.info()
+    assert (b["n_rays"], b["n_segments"], b["lost_rays"]) == (a["n_rays"], a["n_segments"], 0)
+    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"])
+    for w in (0, 341, 512):
+        _same_crossings(o, gg, w)
+        o.free_angle(w)
+    print("geometry trace ms: plain %.0f, guided %.0f" % (a["geometry_trace_ms"], b["geometry_trace_ms"]))
+    gg.close()
+
+
 def test_full_size_sph65_sampled_angle_intensities(sph65):
     p, g = sph65
     rng = np.random.default_rng(5)
