@@ -30,6 +30,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -93,7 +94,9 @@ class Clocks:
         self.gpu = gpu_index
         self.proc = None
         self.marks = []
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        # the raw samples (RT_BENCH_CLOCKS_DIR, default the temporary directory)
+        out = os.environ.get("RT_BENCH_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out, "clocks_bench_%d.csv" % os.getpid())
 
     def start(self):
         """Start sampling every 50 ms and wait (up to 5 s) for the first sample."""
