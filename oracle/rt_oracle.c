@@ -13,9 +13,12 @@
  * compiled with floating-point contraction disabled (-ffp-contract=off) so
  * that every + - * / sqrt is a single IEEE-rounded operation.
  *
- * Where the paper defers to Papers I-II or is silent, the readings used here
- * are the ones listed in the design notes (geometry G1-G13, formal solution
- * R6/R7 with the parabola guard, ALI R10, Ng R11).
+ * Where the paper defers to Papers I-II or is silent, this file states the
+ * reading it takes beside the code that takes it: the geometry rules at
+ * voxel_centre, quad_roots, the crossing functions and trace; the
+ * formal-solution weights and their series at orc_coeffs; the parabola guard
+ * at use_parabola; the launch set at orc_angle_geometry; the ALI update at
+ * orc_ali_update; Ng at orc_ng.
  *
  * Voxel index: v = (i*n2 + j)*n3 + k, with (i,j,k) = (r,theta,phi) on the
  * spherical grid and (R,phi,z) on the cylindrical grid.

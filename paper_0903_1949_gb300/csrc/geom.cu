@@ -6,7 +6,24 @@
 // This translation unit is compiled with -fmad=false: every +, -, *, / and
 // sqrt below is one IEEE double rounding, in the order written, so crossing
 // parameters are reproducible bit for bit by any implementation of the same
-// geometry rules (G1-G12 in the design notes).
+// geometry rules:
+//  * voxel centre = mid-points of the edges, x = (r_m sin th_m) cos ph_m,
+//    y = (r_m sin th_m) sin ph_m, z = r_m cos th_m (cylinder: R_m cos ph_m,
+//    R_m sin ph_m, z_m), with cos/sin of edges and mid-points from host libm;
+//  * line invariants a = n.n, b = x0.n, p2 = x0.x0 (cylinder: x, y only);
+//  * roots of A t^2 + 2 B t + C: disc = B B - A C > 0, q = -(B + sign(B) sqrt),
+//    roots q/A and C/q; inner shell = smaller root, outer = larger;
+//  * cones: |cos th_j| < 1e-12 is the plane z = 0, else the quadratic with
+//    the nappe test sign(z(t)) = sign(cos th_j); a double root is no crossing;
+//  * half-planes: t = -(c y - s x)/(c n_y - s n_x), valid if c x(t) + s y(t) > 0;
+//  * z-planes only in the direction of n_z;
+//  * step to the smallest candidate > t; tied surfaces move all their axes in
+//    one step; leaving the domain takes precedence;
+//  * a transparent hole is crossed to the larger root of the inner surface;
+//  * a characteristic = the backward walk reversed + the forward walk, the
+//    origin's length the sum of both first steps;
+//  * launch order: outer-boundary voxels, core voxels, then completions, each
+//    in increasing voxel index.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
