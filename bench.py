@@ -42,6 +42,7 @@ if ROOT not in sys.path:
 METRIC = "formal-solution voxel·angle updates/s; FP32-mixed vs FP64 at equal J error"
 UNIT = "voxel-angle updates/s"
 DEFAULT_HBM_FALLBACK = 6800.0
+ALGO_BYTES_PER_SEGMENT = 8
 
 
 def parse():
@@ -184,10 +185,32 @@ def workload_text(p):
     return "%s: %s %dx%dx%d voxels, %d solid angles" % (p["name"], kind, n[0], n[1], n[2], p["n_ang"])
 
 
-def cpu_oracle_sample(p, n_angles):
-    """Oracle FS of a bounded, evenly spaced sample of solid angles (geometry untimed)."""
+def oracle_parallel_fs(p, steps=1, warmup=1):
+    """Wall time of one FP64 oracle formal solution over ALL solid angles with the angle loop on
+    every host core (OpenMP, per-thread fixed-order partial sums); the first call, which also builds
+    and caches the crossing lists, is untimed.  Returns (seconds per formal solution, threads)."""
     from oracle import oracle as O
 
+    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"])
+    S = p["B"].copy()
+    used = 1
+    for _ in range(max(1, warmup)):
+        _, _, _, _, used = o.formal_solution_par(S, p["chi"], p["B"])
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.formal_solution_par(S, p["chi"], p["B"])
+    dt = (time.perf_counter() - t0) / steps
+    o.close()
+    return dt, used
+
+
+def cpu_oracle_sample(p, n_angles):
+    """The FP64 oracle on the host cores: one whole formal solution with the angle loop on all
+    cores, and the serial oracle on a bounded, evenly spaced sample of solid angles."""
+    from oracle import oracle as O
+
+    nvox = p["chi"].size
+    dt_par, threads = oracle_parallel_fs(p)
     o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"])
     ws = np.linspace(0, p["n_ang"] - 1, n_angles).astype(int)
     for w in ws:
@@ -198,10 +221,14 @@ def cpu_oracle_sample(p, n_angles):
         o.fs_angle(w, S, p["chi"], p["B"])
     dt = time.perf_counter() - t0
     o.close()
-    nvox = p["chi"].size
-    return {"value": len(ws) * nvox / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "serial FP64 oracle formal solution of %d of the %d solid angles (evenly spaced), "
-                      "%.1f s, geometry excluded" % (len(ws), p["n_ang"], dt)}
+    return {"value": p["n_ang"] * nvox / dt_par, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "nproc": os.cpu_count(),
+            "sample": "FP64 oracle formal solution of all %d solid angles, angle loop over %d host threads "
+                      "(OpenMP, per-thread fixed-order partial sums), %.2f s, geometry built in an untimed first "
+                      "call" % (p["n_ang"], threads, dt_par),
+            "serial": {"value": len(ws) * nvox / dt, "unit": UNIT, "cores": 1,
+                       "sample": "serial FP64 oracle formal solution of %d of the %d solid angles (evenly spaced), "
+                                 "%.1f s, geometry excluded" % (len(ws), p["n_ang"], dt)}}
 
 
 def run_reference(args):
@@ -214,29 +241,17 @@ def run_reference(args):
     from oracle import oracle as O
 
     O.build()
-    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"])
-    nper = 4
-    ws = np.linspace(0, p["n_ang"] - 1, nper).astype(int)
-    for w in ws:
-        o.angle(w)
-    S = p["B"].copy()
-    for _ in range(args.warmup):
-        for w in ws:
-            o.fs_angle(w, S, p["chi"], p["B"])
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for w in ws:
-            o.fs_angle(w, S, p["chi"], p["B"])
-    dt = (time.perf_counter() - t0) / args.steps
+    dt, threads = oracle_parallel_fs(p, steps=args.steps, warmup=args.warmup)
     nvox = p["chi"].size
-    val = nper * nvox / dt
+    val = p["n_ang"] * nvox / dt
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_text(p), "step": "serial CPU oracle formal solution of %d solid angles"
-                       % nper},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d of %d solid angles per step" % (nper, p["n_ang"])},
+            "config": {"workload": workload_text(p), "step": "CPU oracle formal solution of all %d solid angles, "
+                       "angle loop over %d host threads" % (p["n_ang"], threads)},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle", "nproc": os.cpu_count(),
+                             "sample": "all %d solid angles per step (one whole formal solution), crossing lists "
+                                       "built in the untimed warm-up" % p["n_ang"]},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -323,7 +338,9 @@ def main():
     info = g.info()
     seg_per_launch = info["n_segments"] / info["n_blocks"]  # one march launch per angle block and step
     march_avg_ms = ms / info["n_blocks"]  # the step's duration shared by its march launches
-    achieved = seg_per_launch * bytes_per_seg / (march_avg_ms / 1e3) / 1e9
+    # algorithmic bytes of the method: an int32 voxel id and an FP32 path length per crossing segment
+    achieved = seg_per_launch * ALGO_BYTES_PER_SEGMENT / (march_avg_ms / 1e3) / 1e9
+    achieved_design = seg_per_launch * bytes_per_seg / (march_avg_ms / 1e3) / 1e9
     peak, peak_src = hbm_peak()
     traffic, traffic_src = ncu_traffic(seg_per_launch)
     g.set_timing(1)  # every launch: march and gather shares of a step (informational window)
@@ -349,6 +366,17 @@ def main():
     ms64p = timed(g.ali_step, 2)
     g.tune(rt.RT_TUNE_STREAMED_WEIGHTS, 1)
     value64p = job_throughput(units, world, ms64p)
+
+    # ---- FP64 FMA rate of this device: the denominator of the FP64 path's roofline ----
+    ck64 = Clocks(local)
+    ck64.start()
+    ck64.mark()
+    rates = [rt.rt_measure_fp64_rate(local) for _ in range(5)]
+    ck64.mark()
+    fp64_peak = {"flops_per_s": max(r[0] for r in rates), "ms_per_launch": min(r[1] for r in rates),
+                 "samples": [r[0] for r in rates], "clocks": ck64.stop(),
+                 "method": "rt_measure_fp64_rate: 16 CTAs x 256 threads per SM, 8 independent FMA chains of 4096 "
+                           "FMAs per thread, 5 launches per sample timed with CUDA events, best of 5 samples"}
 
     # ---- end to end through the C ABI with pinned host buffers ----
     g.set_precision(rt.RT_MIXED)
@@ -377,6 +405,8 @@ def main():
     equal = None
     if not args.no_equal_error and rank == 0:
         equal = equal_error(g, p, rt, torch)
+
+    fresh = fresh_chi_costs(g, p, torch) if rank == 0 else None
 
     conv = None
     if not args.no_convergence and rank == 0:
@@ -411,7 +441,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "1 GPU",
                        "geometry_ms": info["geometry_ms"], "geometry_trace_ms": info["geometry_trace_ms"],
                        "geometry_lists_ms": info["geometry_lists_ms"], "device_gb": info["device_bytes"] / 1e9},
-            "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "steps": k64,
+            "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "steps": k64, "fp64_peak": fp64_peak,
                      "mixed_over_fp64": value / value64,
                      "path": "FP64 march with FP64 weights streamed per chi (48 B per segment), FP64 gather",
                      "plain": {"value": value64p, "ms_per_step": ms64p, "steps": 2,
@@ -419,9 +449,15 @@ def main():
                                "path": "FP64 march evaluating its weights per segment (FP64-ALU bound)"}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "traffic_over_algorithmic": (traffic / (ALGO_BYTES_PER_SEGMENT * seg_per_launch)
+                                                      if traffic else None),
                          "kernel": "k_march_sw<2> (FP32 streamed-weight ray march, J only)",
-                         "algorithmic_bytes": "%g B per crossing segment (u32 voxel word + FP32 E, alpha, beta, "
-                                              "gamma + FP32 w l/L + i32 list position)" % bytes_per_seg,
+                         "algorithmic_bytes": "%d B per crossing segment (int32 voxel id + FP32 path length, the "
+                                              "method's minimum stream)" % ALGO_BYTES_PER_SEGMENT,
+                         "design_bytes": {"per_segment": bytes_per_seg, "achieved": achieved_design,
+                                          "frac": achieved_design / peak,
+                                          "what": "bytes this design streams per segment: u32 voxel word + FP32 E, "
+                                                  "alpha, beta, gamma + FP32 w l/L + i32 list position"},
                          "segments_per_launch": seg_per_launch, "avg_launch_ms": march_avg_ms,
                          "avg_launch_ms_events": march_event_ms,
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src if peak_src == "measured"
@@ -441,6 +477,8 @@ def main():
             "clocks": ck}
     if equal is not None:
         line["equal_error"] = equal
+    if fresh is not None:
+        line["fresh_chi"] = fresh
     if batch is not None:
         line["batch"] = batch
     if conv is not None:
@@ -621,15 +659,107 @@ def convergence_measure(g, p, rt, torch, tol=1e-6, max_fs=400):
     return out
 
 
-def equal_error(g, p, rt, torch, target=1e-5, n_iter=24):
+def equal_error_converged(p, rt, torch, target=1e-5, max_fs=2000,
+                          tols=(1e-5, 3e-6, 1e-6, 3e-7, 1e-7, 3e-8, 1e-8)):
+    """FP32-mixed vs FP64, each run to the same J accuracy.
+
+    Both solvers use the nearest-neighbour Lambda* (built once per chi in FP64, the
+    paper's operator, Sect. 3.2.1) and Ng: rt_solve in RT_FP64 (FP64 formal solutions
+    with FP64 weights streamed per chi) and in RT_MIXED (FP64 residual formal
+    solutions, FP32 correction sweeps).  The reference J_ref is the FP64 solve
+    converged to max rel dS < 1e-12.  For each solver, solves from S = B with the
+    tolerances `tols` in turn until the J of the final S (one FP64 formal solution,
+    untimed) is within `target` of J_ref; the time of that solve is the solver's time
+    to `target`.  The NN operator and the per-chi weight streams are built before
+    the timed solves (reported as set-up)."""
+    kw = dict(inner_bc=p["inner_bc"], use_lstar=rt.RT_LSTAR_NN, ng=True)
+    g64 = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], precision=rt.RT_FP64, **kw)
+    gmx = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], precision=rt.RT_MIXED, refine_every=16, **kw)
+    out = {"target_max_rel_J_err": target, "lstar": "nearest-neighbour (FP64, built once per chi)", "ng": True}
+    try:
+        setup = {}
+        for name, g in (("fp64", g64), ("mixed", gmx)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.set_opacity(p["chi"], p["eps"], p["B"])
+            g.Lstar_nn()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            g.ali_step()  # first formal solutions of this chi: Lambda*, weight streams
+            g.ali_step()
+            torch.cuda.synchronize()
+            setup[name] = {"set_opacity_and_nn_build_s": t1 - t0, "first_two_steps_s": time.perf_counter() - t1}
+        out["setup"] = setup
+        g64.set_S(p["B"])
+        t0 = time.perf_counter()
+        it_ref, ok_ref = g64.solve(1e-12, max_fs)
+        out["reference"] = {"tol_max_rel_dS": 1e-12, "formal_solutions": it_ref, "converged": bool(ok_ref),
+                            "s": time.perf_counter() - t0}
+        g64.formal_solution(rt.RT_FP64)
+        J_ref = g64.J()
+
+        def j_err(S):
+            g64.set_S(S)
+            g64.formal_solution(rt.RT_FP64)
+            return float(np.max(np.abs(g64.J() - J_ref) / np.abs(J_ref)))
+
+        res = {}
+        for name, g in (("fp64", g64), ("mixed", gmx)):
+            runs = []
+            for tol in tols:
+                g.set_S(p["B"])
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                it, ok = g.solve(tol, max_fs)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                e = j_err(g.S())
+                runs.append({"tol_max_rel_dS": tol, "formal_solutions": it, "s": dt, "max_rel_J_err": e})
+                if e <= target:
+                    break
+            best = runs[-1]
+            res[name] = {"s": best["s"], "formal_solutions": best["formal_solutions"],
+                         "max_rel_J_err": best["max_rel_J_err"], "meets_target": best["max_rel_J_err"] <= target,
+                         "ms_per_formal_solution": 1e3 * best["s"] / max(1, best["formal_solutions"]),
+                         "runs": runs}
+        out.update(res)
+        out["speedup_mixed_over_fp64"] = res["fp64"]["s"] / res["mixed"]["s"]
+    finally:
+        g64.close()
+        gmx.close()
+    return out
+
+
+def fresh_chi_costs(g, p, torch):
+    """What a new opacity field costs the mixed path before its steady ALI steps:
+    rt_set_opacity (FP64 parabola choices), the first step (full FP32 formal
+    solution with Lambda*), the second (FP64 weights streamed to FP32 + the first
+    J-only march), against a steady step."""
+    torch.cuda.synchronize()
+    t = [time.perf_counter()]
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    torch.cuda.synchronize()
+    t.append(time.perf_counter())
+    for _ in range(4):
+        g.ali_step()
+        torch.cuda.synchronize()
+        t.append(time.perf_counter())
+    d = np.diff(t) * 1e3
+    units = p["chi"].size * p["n_ang"]
+    return {"set_opacity_ms": d[0], "first_step_ms": d[1], "second_step_ms": d[2], "steady_step_ms": d[4],
+            "cold_fs_voxel_angles_per_s": units / ((d[0] + d[1]) / 1e3),
+            "note": "host-timed with a device synchronize around each call; first step = full FP32 formal solution "
+                    "(J, Lambda*, flux, weights evaluated per segment), second step builds the FP32 weight stream"}
+
+
+def equal_error(g, p, rt, torch, target=1e-5):
     """FP32-mixed vs FP64 at equal J error, measured two ways on the same grid.
 
     (1) One formal solution from the same S: max relative J difference of the
         FP32 march against the FP64 march, and their time ratio.
-    (2) The ALI+Ng solver: n_iter iterations of each path from S = B.  When
-        their J agree within `target`, both carry the same J error with respect
-        to any reference (to within `target`), and the wall-time ratio is the
-        speedup at equal J error.
+    (2) Each solver run to convergence (equal_error_converged): the wall time
+        each needs from S = B until its J is within `target` of the converged
+        FP64 J, and their ratio.
     """
     nvox = p["chi"].size
     n1, n2, n3 = p["n"]
@@ -661,28 +791,7 @@ def equal_error(g, p, rt, torch, target=1e-5, n_iter=24):
                               "fp64_ms": times["fp64"] * 1e3, "fp32_ms": times["fp32"] * 1e3,
                               "speedup": times["fp64"] / times["fp32"], "meets_target": d <= target,
                               "note": "full formal solution (J, Lambda*, flux) from the same S"}
-    res = {}
-    for prec, name in ((rt.RT_FP64, "fp64"), (rt.RT_MIXED, "mixed")):
-        g.set_precision(prec)
-        g.set_opacity(p["chi"], p["eps"], p["B"])
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(n_iter):
-            g.ali_step()
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        S = g.S()
-        hist = g.history()[-1]
-        g.formal_solution(rt.RT_FP64)
-        res[name] = (dt, S, g.J(), hist, g.flux())
-    dS = float(np.max(np.abs(res["mixed"][1] - res["fp64"][1]) / np.abs(res["fp64"][1])))
-    dJ = float(np.max(np.abs(res["mixed"][2] - res["fp64"][2]) / np.abs(res["fp64"][2])))
-    out["ali_solver"] = {"iterations": n_iter, "fp64_s": res["fp64"][0], "mixed_s": res["mixed"][0],
-                         "speedup": res["fp64"][0] / res["mixed"][0], "max_rel_S_diff": dS, "max_rel_J_diff": dJ,
-                         "emergent_Fr_diff": fr_diff(res["mixed"][4], res["fp64"][4]),
-                         "meets_target": dJ <= target, "last_max_rel_dS_fp64": float(res["fp64"][3]),
-                         "note": "diagonal-Lambda* ALI + Ng from S = B; J and the emergent radial flux (outermost "
-                                 "shell, relative to its maximum) compared by an FP64 formal solution of each final S"}
+    out["converged"] = equal_error_converged(p, rt, torch, target)
     g.set_precision(rt.RT_MIXED)
     g.set_opacity(p["chi"], p["eps"], p["B"])
     return out

@@ -128,9 +128,13 @@ int rt_grid_destroy(rt_grid *g);
 int rt_get_info(const rt_grid *g, rt_info *info);
 
 /* Set extinction chi (> 0, finite), thermalisation eps (in (0, 1]) and Planck
- * function B (>= 0, finite) per voxel (Sect. 3.1 items 5-6).  S is set to B.
- * Host input is validated (RT_EINVAL, nothing changed); device input is
- * taken as given. */
+ * function B (>= 0, finite) per voxel (Sect. 3.1 items 5-6).  Every call
+ * resets S := B, the start of the ALI iteration, and clears the Ng history; a
+ * warm restart from an earlier S calls rt_set_S after it.  Input out of range
+ * (NaN and infinities included) gives RT_EINVAL with the first offending
+ * voxel in rt_last_error() and nothing changed: host arrays are checked on the
+ * host, device arrays by a kernel on the grid's stream, which this call then
+ * waits for. */
 int rt_set_opacity(rt_grid *g, const double *chi, const double *eps, const double *B, int where);
 
 /* Replace the source function S (warm restart). */
@@ -317,18 +321,31 @@ int rt_fs_angles(rt_grid *g, const int32_t *omegas, int n, int precision, double
  * under a device-memory budget that is already fully handed out, or a thread
  * that must not take the CUDA allocator's locks.  The paper has no counterpart;
  * this is a library service.  The call allocates nothing: its per-segment
- * scratch is a static device array of 16 MiB inside the library (held by every
- * GPU that loads it until the process exits), so the solid angle must have at
- * most 1 Mi crossing segments in RT_FP64 or 2 Mi in RT_MIXED (else RT_EINVAL
- * with the counts in rt_last_error()).  The grid must exist (rt_grid_create
- * allocates); Ibar and Lbar are caller-owned DEVICE buffers of n_vox doubles
- * that receive what rt_fs_angles returns for this angle, from the current S.
- * Work is queued on the grid's stream and not waited for.  The first call on a
- * device looks up the scratch's device address; make that first call before any
- * stream capture.  All calls share the one scratch array, which keeps the last
- * call's contents (nothing in it needs clearing: every entry read is written
- * first); calls whose GPU work overlaps (other streams, other threads) race. */
+ * scratch is a static device array of 16 MiB inside the library, so the solid
+ * angle must have at most 1 Mi crossing segments in RT_FP64 or 2 Mi in
+ * RT_MIXED (else RT_EINVAL with the counts in rt_last_error()).  The grid must
+ * exist: rt_grid_create (which allocates anyway) looks up the array's device
+ * address on its device, which is when the array is placed there (the
+ * library's code loads lazily) and held until the process exits, and loads the
+ * kernels this call launches; the call itself only reads that cached address.
+ * Ibar and Lbar are caller-owned DEVICE buffers of n_vox doubles that receive
+ * what rt_fs_angles returns for this angle, from the current S (the same
+ * kernels on this angle's segments alone, so the two agree to rounding, not bit
+ * for bit: rt_fs_angles marches the angle's whole block, which groups the
+ * characteristics into warp bundles differently).  Work is queued on the
+ * grid's stream and not waited for.  All calls share the one scratch array,
+ * which keeps the last call's contents (nothing in it needs clearing: every
+ * entry read is written first); calls whose GPU work overlaps (other streams,
+ * other threads) race.  Not async-signal-safe: never call it from a signal
+ * handler. */
 int rt_fs_angle_noalloc(rt_grid *g, int omega, int precision, double *Ibar, double *Lbar);
+
+/* FP64 fused multiply-add throughput of a device in flop/s (2 per FMA), the
+ * denominator of the FP64 path's roofline (measurement service; the paper
+ * has no counterpart): a grid that fills every SM runs independent FMA
+ * chains, timed with CUDA events; *ms_per_launch is one launch's mean time.
+ * Takes the device briefly (about a tenth of a second) on a stream of its own. */
+int rt_measure_fp64_rate(int device, double *flops_per_s, double *ms_per_launch);
 
 /* ---- batches: many opacity fields solved together ----------------------
  * A batch holds n_members problems (wavelengths of a line profile or
@@ -355,8 +372,18 @@ int rt_batch_set_member(rt_batch *b, int m, const double *chi, const double *eps
 /* One iteration of every member; max_rel_dS (may be NULL) gets n_members values. */
 int rt_batch_ali_step(rt_batch *b, double *max_rel_dS);
 
-/* Iterate until every member's max rel dS < tol; iters (may be NULL) gets, per
- * member, the iteration at which it first met tol (0 if never). */
+/* Solve every member to its fixed point in mixed precision with FP64
+ * refinement (as rt_solve does with RT_MIXED for one grid): an FP64 formal
+ * solution of each member still iterating gives its exact residual
+ * r = (1-eps) J + eps B - S; up to 16 batched FP32 J-only sweeps (one CUDA
+ * graph, no incoming radiation) then solve for the correction D of S with the
+ * diagonal Lambda* (D <- D + [(1-eps) J(D) + r - D] / (1 - (1-eps) Lambda*)),
+ * stopping early once a sweep changes D by < tol/100 relative, and S += D.  A
+ * member is done when the ALI update its FP64 residual asks for is below tol
+ * (max |dS| / |S + dS|); its S is then left alone.  The fixed point is the
+ * FP64 one.  max_iter bounds the formal solutions (FP64 and FP32 alike); iters
+ * (may be NULL) gets, per member, the formal-solution count at which it was
+ * found done (0 if never).  RT_ENOTCONVERGED when some member is not done. */
 int rt_batch_solve(rt_batch *b, double tol, int max_iter, int32_t *iters);
 
 /* Member m's S (what = 0), J (1) or Lambda* (2). */

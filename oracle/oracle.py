@@ -33,7 +33,10 @@ def build(force=False):
     tmp = _SO + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
            "-o", tmp, _SRC, "-lm"]
-    subprocess.check_call(cmd)
+    try:  # the angle-parallel formal solution wants OpenMP; without it that call runs on one thread
+        subprocess.check_call(cmd[:-1] + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL)
+    except (subprocess.CalledProcessError, OSError):
+        subprocess.check_call(cmd)
     os.replace(tmp, _SO)
     return _SO
 
@@ -62,12 +65,14 @@ def _lib():
                                    ctypes.c_int, _c_dbl_p, _c_dbl_p, _c_dbl_p]
         L.orc_formal_solution.argtypes = [ctypes.c_void_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, ctypes.c_int,
                                           _c_dbl_p, _c_dbl_p, _c_dbl_p]
+        L.orc_formal_solution_par.argtypes = [ctypes.c_void_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, ctypes.c_int,
+                                              _c_dbl_p, _c_dbl_p, _c_dbl_p, ctypes.c_int, _c_int_p]
         L.orc_ali_update.restype = ctypes.c_double
         L.orc_ali_update.argtypes = [ctypes.c_int, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p,
                                      ctypes.c_int]
         L.orc_ng.argtypes = [ctypes.c_int, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p]
         L.orc_solve.argtypes = [ctypes.c_void_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, ctypes.c_double,
-                                ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_dbl_p]
+                                ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_dbl_p, ctypes.c_int]
         L.orc_nn_lstar.argtypes = [ctypes.c_void_p, _c_dbl_p, _c_dbl_p]
         L.orc_nn_ali_update.restype = ctypes.c_double
         L.orc_nn_ali_update.argtypes = [ctypes.c_void_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p,
@@ -219,10 +224,27 @@ class OracleGrid:
                                           F.ctypes.data_as(_c_dbl_p))
         return J, L, F, miss
 
-    def solve(self, chi, eps, B, tol=1e-8, max_iter=500, use_lstar=True, ng=True, S0=None):
+    def formal_solution_par(self, S, chi, B, homog=False, threads=None):
+        """formal_solution with the angle loop over host threads (default: all cores);
+        returns (J, Lambda*, F, n missing, threads used)."""
+        S, pS = _d(S)
+        c, pc = _d(chi)
+        Bb, pB = _d(B)
+        J = np.empty(self.nvox)
+        L = np.empty(self.nvox)
+        F = np.empty((self.nvox, 3))
+        used = ctypes.c_int(1)
+        n = int(threads) if threads else (os.cpu_count() or 1)
+        miss = _lib().orc_formal_solution_par(self._h, pS, pc, pB, 1 if homog else 0,
+                                              J.ctypes.data_as(_c_dbl_p), L.ctypes.data_as(_c_dbl_p),
+                                              F.ctypes.data_as(_c_dbl_p), n, ctypes.byref(used))
+        return J, L, F, miss, used.value
+
+    def solve(self, chi, eps, B, tol=1e-8, max_iter=500, use_lstar=True, ng=True, S0=None, threads=1):
         """ALI (+Ng) to max rel dS < tol from S0 (default B); returns (S, iterations, history).
 
-        use_lstar: False/0 Lambda iteration, True/1 diagonal Lambda*, 2 nearest-neighbour Lambda*."""
+        use_lstar: False/0 Lambda iteration, True/1 diagonal Lambda*, 2 nearest-neighbour Lambda*.
+        threads > 1: each formal solution with the angle loop over that many host threads."""
         c, pc = _d(chi)
         e, pe = _d(eps)
         Bb, pB = _d(B)
@@ -230,6 +252,6 @@ class OracleGrid:
         hist = np.zeros(max_iter)
         mode = int(use_lstar) if not isinstance(use_lstar, bool) else (1 if use_lstar else 0)
         it = _lib().orc_solve(self._h, pS, pc, pe, pB, float(tol), int(max_iter), mode,
-                              1 if ng else 0, hist.ctypes.data_as(_c_dbl_p))
+                              1 if ng else 0, hist.ctypes.data_as(_c_dbl_p), int(threads))
         n = abs(it)
         return S, it, hist[:n]

@@ -27,6 +27,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_SPH 0
 #define ORC_CYL 1
@@ -724,6 +727,82 @@ int orc_formal_solution(orc_grid *g, const double *S, const double *chi, const d
     return missing;
 }
 
+/* The same formal solution with the angle loop spread over nthreads host
+ * threads (OpenMP when the oracle is compiled with it; one thread
+ * otherwise).  Thread t takes the solid angles w = t, t + nthreads, ... in
+ * increasing order and adds their terms into its own partial sums, exactly
+ * as the serial loop does; the partial sums are then added in thread order.
+ * The result is reproducible for a given thread count and equals the serial
+ * one up to the association of the angle sum.  Returns the number of
+ * (voxel, angle) pairs no characteristic hit, or < 0; *used receives the
+ * thread count that ran. */
+int orc_formal_solution_par(orc_grid *g, const double *S, const double *chi, const double *B, int homog,
+                            double *J, double *Lstar, double *F, int nthreads, int *used)
+{
+    int nvox = g->nvox;
+    if (nthreads < 1) nthreads = 1;
+#ifndef _OPENMP
+    nthreads = 1;
+#endif
+    size_t stride = 5 * (size_t)nvox; /* per thread: J, Lambda*, three flux components */
+    double *part = (double *)calloc((size_t)nthreads * stride, sizeof(double));
+    int *miss = (int *)calloc((size_t)nthreads, sizeof(int));
+    if (!part || !miss) { free(part); free(miss); return -2; }
+    int ran = 1;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#pragma omp single
+        ran = omp_get_num_threads();
+#endif
+        double *Ib = (double *)malloc(sizeof(double) * nvox);
+        double *Lb = (double *)malloc(sizeof(double) * nvox);
+        double *P = part + (size_t)t * stride;
+        for (int w = t; w < g->n_ang && Ib && Lb; w += nthreads) {
+            int rc = orc_fs_angle(g, w, S, chi, B, homog, Ib, Lb, NULL);
+            if (rc < 0) { miss[t] = rc; break; }
+            miss[t] += rc;
+            double wt = g->wt[w];
+            const double *d = &g->dir[3 * w];
+            for (int v = 0; v < nvox; ++v) {
+                P[v] += wt * Ib[v];
+                P[nvox + v] += wt * Lb[v];
+                P[2 * (size_t)nvox + v] += FOUR_PI * wt * d[0] * Ib[v];
+                P[3 * (size_t)nvox + v] += FOUR_PI * wt * d[1] * Ib[v];
+                P[4 * (size_t)nvox + v] += FOUR_PI * wt * d[2] * Ib[v];
+            }
+        }
+        if (!Ib || !Lb) miss[t] = -2;
+        free(Ib); free(Lb);
+    }
+    int missing = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        if (miss[t] < 0) { missing = miss[t]; break; }
+        missing += miss[t];
+    }
+    for (int v = 0; v < nvox; ++v) {
+        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int t = 0; t < nthreads; ++t)
+            for (int c = 0; c < 5; ++c) acc[c] += part[(size_t)t * stride + (size_t)c * nvox + v];
+        J[v] = acc[0];
+        Lstar[v] = acc[1];
+        if (F) {
+            int i, j, k;
+            vox_ijk(g, v, &i, &j, &k);
+            double e[3][3];
+            local_basis(g, i, j, k, e);
+            for (int c = 0; c < 3; ++c) F[3 * v + c] = e[c][0] * acc[2] + e[c][1] * acc[3] + e[c][2] * acc[4];
+        }
+    }
+    free(part); free(miss);
+    if (used) *used = ran;
+    return missing;
+}
+
 /* ---------------------------------------------------------- ALI and Ng -- */
 
 /* Operator-splitting update with the diagonal Lambda* (R10):
@@ -940,10 +1019,12 @@ double orc_nn_ali_update(const orc_grid *g, double *S, const double *J, const do
  * iteration, 1 diagonal Lambda*, 2 nearest-neighbour Lambda* (built once,
  * OS step solved by Jacobi sweeps to 1e-14).  ng = 1 applies Ng whenever four
  * ALI iterates have accumulated since the last extrapolation.  hist
- * (optional, max_iter entries) receives max rel dS of every step.  Returns
- * the number of steps taken (negative: not converged). */
+ * (optional, max_iter entries) receives max rel dS of every step.  With
+ * nthreads > 1 each formal solution runs its angle loop over that many host
+ * threads (orc_formal_solution_par).  Returns the number of steps taken
+ * (negative: not converged). */
 int orc_solve(orc_grid *g, double *S, const double *chi, const double *eps, const double *B, double tol,
-              int max_iter, int use_lstar, int ng, double *hist)
+              int max_iter, int use_lstar, int ng, double *hist, int nthreads)
 {
     int nvox = g->nvox;
     double *J = (double *)malloc(sizeof(double) * nvox);
@@ -959,7 +1040,8 @@ int orc_solve(orc_grid *g, double *S, const double *chi, const double *eps, cons
     }
     int nh = 0, it, done = 0;
     for (it = 1; it <= max_iter; ++it) {
-        orc_formal_solution(g, S, chi, B, 0, J, L, NULL);
+        if (nthreads > 1) orc_formal_solution_par(g, S, chi, B, 0, J, L, NULL, nthreads, NULL);
+        else orc_formal_solution(g, S, chi, B, 0, J, L, NULL);
         double rel;
         if (use_lstar == 2) rel = orc_nn_ali_update(g, S, J, L27, eps, B, 1e-14, 100000, NULL);
         else rel = orc_ali_update(nvox, S, J, L, eps, B, use_lstar);

@@ -191,6 +191,40 @@ cudaError_t pack_chiS32(int nvox, const double *chi, const double *S, const doub
     return cudaGetLastError();
 }
 
+// Input check of rt_set_opacity for device arrays: the smallest 4 v + c over
+// voxels v whose chi (c = 0), eps (c = 1) or B (c = 2) is out of range.
+__global__ void k_check_opacity(int n, const double *chi, const double *eps, const double *B,
+                                unsigned long long *first_bad)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const double c = chi[v], e = eps[v], b = B[v];
+        int code = -1;
+        if (!(c > 0.0) || !isfinite(c)) code = 0;
+        else if (!(e > 0.0 && e <= 1.0)) code = 1;
+        else if (!(b >= 0.0) || !isfinite(b)) code = 2;
+        if (code >= 0) atomicMin(first_bad, 4ull * (unsigned long long)v + (unsigned long long)code);
+    }
+}
+
+cudaError_t check_opacity(int nvox, const double *chi, const double *eps, const double *B,
+                          unsigned long long *first_bad, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(first_bad, 0xff, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    int blocks = nb(nvox);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_check_opacity<<<blocks, 256, 0, st>>>(nvox, chi, eps, B, first_bad);
+    return cudaGetLastError();
+}
+
+cudaError_t pack_preload()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_pack64);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_pack32);
+    return e;
+}
+
 cudaError_t ali_update(int nvox, double *S, const double *J, const double *Lst, const double *eps, const double *B,
                        int use_lstar, double *hist_slot, unsigned long long *maxrel, cudaStream_t st)
 {

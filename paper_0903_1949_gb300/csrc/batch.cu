@@ -79,6 +79,63 @@ __global__ void k_bali(int64_t n, const int64_t *voff, int nm, double *S, const 
     }
 }
 
+// FP64 residual of the refined batch solve: r = (1-eps) J64 + eps B - S for the
+// members still iterating (active[m]), 0 for the others; per member the max of
+// |dS| / |S + dS| over its voxels for the ALI update dS = r / (1 - (1-eps) L).
+__global__ void k_bresid(int64_t n, const int64_t *voff, int nm, const int *active, const double *S, const double *J,
+                         const double *L, const double *eps, const double *B, double *R, unsigned long long *maxrel)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nm;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (voff[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        if (!active[lo]) {
+            R[i] = 0.0;
+            continue;
+        }
+        const double e = eps[i], s = S[i];
+        const double r = (1.0 - e) * J[i] + e * B[i] - s;
+        R[i] = r;
+        const double d = r / (1.0 - (1.0 - e) * L[i]);
+        atomicMax(maxrel + lo, (unsigned long long)__double_as_longlong(fabs(d) / fabs(s + d)));
+    }
+}
+
+// One FP32-march correction sweep of the refined solve for every member:
+// D <- D + [(1-eps) J(D) + R - D] / (1 - (1-eps) L), J(D) the formal solution of
+// D with no incoming radiation; per member the max |change| / |S + D|.
+__global__ void k_bcorr(int64_t n, const int64_t *voff, int nm, double *D, const double *J, const double *R,
+                        const double *L, const double *eps, const double *S, unsigned long long *maxrel)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nm;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (voff[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        const double e = eps[i], d = D[i];
+        const double dn = d + ((1.0 - e) * J[i] + R[i] - d) / (1.0 - (1.0 - e) * L[i]);
+        D[i] = dn;
+        atomicMax(maxrel + lo, (unsigned long long)__double_as_longlong(fabs(dn - d) / fabs(S[i] + dn)));
+    }
+}
+
+__global__ void k_badd(int64_t n, double *S, const double *D)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        S[i] += D[i];
+}
+
+__global__ void k_bpack64(int64_t n, const double *chi, const double *S, double2 *cs)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        cs[i] = make_double2(chi[i], S[i]);
+}
+
 // Line mode.  S_k = (chi_c B + chi_l phi_k S_l) / chi_k for every frequency k
 // (members k*nvox .. (k+1)*nvox - 1 of the concatenated arrays).
 __global__ void k_line_src(int nvox, int nf, const double *chi, const double *chi_c, const double *chi_l,
@@ -208,6 +265,12 @@ struct rt_batch {
     int chunk = 1024;
     int grid_march = 152 * 5, grid_gather = 152 * 5;
     cudaGraphExec_t graph = nullptr;
+    // refined solve (rt_batch_solve): FP64 residual R, FP32 correction D, its graph
+    double *R = nullptr, *D = nullptr;
+    double2 *cs64 = nullptr;
+    int *d_active = nullptr;
+    cudaGraphExec_t graph_corr = nullptr;
+    int refine_every = 16;
     std::vector<double> history;  // max over members of max rel dS per iteration
     // two-level line mode (rt_line_*): the members are the frequencies of one grid
     int line = 0;
@@ -246,6 +309,8 @@ void bfree_all(rt_batch *b)
 {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
+    if (b->graph_corr) cudaGraphExecDestroy(b->graph_corr);
+    b->graph_corr = nullptr;
     for (void *p : b->allocs) cudaFree(p);
     b->allocs.clear();
     if (b->own_stream && b->st) cudaStreamDestroy(b->st);
@@ -309,6 +374,53 @@ int enqueue_iteration(rt_batch *b)
         k_bali<<<152 * 8, 256, 0, b->st>>>(b->ntot, b->d_voff, b->nm, b->S, b->J, b->L, b->eps, b->B, b->maxrel);
     }
     BCK(cudaGetLastError());
+    return RT_OK;
+}
+
+// One correction sweep of the refined solve for all members (captured).
+int enqueue_correction(rt_batch *b)
+{
+    k_bpack<<<152 * 8, 256, 0, b->st>>>(b->ntot, b->chi, b->D, b->B, b->cs, b->B32);
+    BCK(cudaGetLastError());
+    for (const Wave &w : b->waves) {
+        BCK(cudaMemsetAsync(b->counters, 0, 2 * sizeof(unsigned long long), b->st));
+        BCK(march_batch(b->d_mi + w.mi0, b->d_bpfx + w.pf0, w.n, w.bundles, b->chunk, 1, b->counters, b->grid_march,
+                        b->st));
+        BCK(gather_J_batch(b->d_gi + w.mi0, b->d_wpfx + w.pf0, w.n, w.work, b->counters + 1, b->grid_gather, b->st));
+    }
+    BCK(cudaMemsetAsync(b->maxrel, 0, sizeof(unsigned long long) * b->nm, b->st));
+    k_bcorr<<<152 * 8, 256, 0, b->st>>>(b->ntot, b->d_voff, b->nm, b->D, b->J, b->R, b->L, b->eps, b->S, b->maxrel);
+    BCK(cudaGetLastError());
+    return RT_OK;
+}
+
+int capture_corr(rt_batch *b)
+{
+    if (b->graph_corr) {
+        cudaGraphExecDestroy(b->graph_corr);
+        b->graph_corr = nullptr;
+    }
+    cudaGraph_t gr = nullptr;
+    BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_correction(b);
+    cudaError_t e = cudaStreamEndCapture(b->st, &gr);
+    if (rc != RT_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return rc;
+    }
+    if (e != cudaSuccess) return bfail(RT_ECUDA, std::string("stream capture failed: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->graph_corr, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return bfail(RT_ECUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(e));
+    return RT_OK;
+}
+
+int read_member_rel(rt_batch *b, std::vector<double> &rel)
+{
+    BCK(cudaMemcpyAsync(b->h_maxrel.data(), b->maxrel, sizeof(unsigned long long) * b->nm, cudaMemcpyDeviceToHost,
+                        b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    for (int m = 0; m < b->nm; ++m) std::memcpy(&rel[m], &b->h_maxrel[m], sizeof(double));
     return RT_OK;
 }
 
@@ -476,6 +588,10 @@ int rt_batch_create(rt_batch **out, rt_grid *const *grids, int n_grids, int n_me
     TRY(balloc(b, &b->d_voff, n_members + 1));
     TRY(balloc(b, &b->maxrel, n_members));
     TRY(balloc(b, &b->counters, 2));
+    TRY(balloc(b, &b->R, b->ntot));
+    TRY(balloc(b, &b->D, b->ntot));
+    TRY(balloc(b, &b->cs64, max_vox));
+    TRY(balloc(b, &b->d_active, n_members));
     if (cudaMemcpyAsync(b->d_voff, b->voff.data(), sizeof(int64_t) * (n_members + 1), cudaMemcpyHostToDevice, b->st) !=
         cudaSuccess)
         return fail_and_free(bfail(RT_ECUDA, "copy failed"));
@@ -628,23 +744,69 @@ int rt_batch_solve(rt_batch *b, double tol, int max_iter, int32_t *iters)
     if (b->line) return bfail(RT_EINVAL, "a line problem iterates with rt_line_solve");
     if (!(tol > 0.0) || max_iter < 1) return bfail(RT_EINVAL, "need tol > 0 and max_iter >= 1");
     BCK(cudaSetDevice(b->device));
-    std::vector<double> rel(b->nm);
+    for (int m = 0; m < b->nm; ++m)
+        if (!b->ready[m]) return bfail(RT_EINVAL, "member " + std::to_string(m) + " has no opacity yet");
+    for (rt_grid *g : b->grids) BCK(cudaStreamSynchronize(g->st));
+    // Mixed precision with FP64 refinement, per member as rt_solve does for one grid:
+    // an FP64 formal solution gives the exact residual r = (1-eps) J64 + eps B - S,
+    // then up to refine_every batched FP32 J-only sweeps solve for the correction D
+    // with the diagonal Lambda*, and S += D.  A member is done when the ALI update
+    // its FP64 residual asks for is below tol; its residual is then held at zero.
+    std::vector<double> rel(b->nm, 0.0);
     std::vector<int32_t> done(b->nm, 0);
+    std::vector<int> active(b->nm, 1);
     b->history.clear();
-    for (int it = 1; it <= max_iter; ++it) {
-        BRCK(step(b, rel.data()));
+    if (!b->graph_corr) BRCK(capture_corr(b));
+    const double inner_tol = 0.01 * tol;
+    int total = 0;
+    while (total < max_iter) {
+        for (int m = 0; m < b->nm; ++m) {
+            if (!active[m]) continue;
+            rt_grid *g = b->grids[b->mgrid[m]];
+            const int64_t o = b->voff[m], n = g->nvox;
+            k_bpack64<<<152 * 4, 256, 0, b->st>>>(n, b->chi + o, b->S + o, b->cs64);
+            BCK(cudaGetLastError());
+            BRCK(rt_grid_member_fs64J(g, b->cs64, b->B + o, b->pbits[m], b->J + o, b->st));
+        }
+        total++;
+        BCK(cudaMemcpyAsync(b->d_active, active.data(), sizeof(int) * b->nm, cudaMemcpyHostToDevice, b->st));
+        BCK(cudaMemsetAsync(b->maxrel, 0, sizeof(unsigned long long) * b->nm, b->st));
+        k_bresid<<<152 * 8, 256, 0, b->st>>>(b->ntot, b->d_voff, b->nm, b->d_active, b->S, b->J, b->L, b->eps, b->B,
+                                             b->R, b->maxrel);
+        BCK(cudaGetLastError());
+        BRCK(read_member_rel(b, rel));
+        double mx = 0.0;
         bool all = true;
         for (int m = 0; m < b->nm; ++m) {
-            if (!done[m] && rel[m] < tol) done[m] = it;
-            all = all && done[m];
+            if (!active[m]) continue;
+            mx = std::max(mx, rel[m]);
+            if (rel[m] < tol) {
+                done[m] = total;
+                active[m] = 0;
+            }
+            all = all && !active[m];
         }
+        b->history.push_back(mx);
         if (all) {
             if (iters) std::copy(done.begin(), done.end(), iters);
             return RT_OK;
         }
+        BCK(cudaMemsetAsync(b->D, 0, sizeof(double) * b->ntot, b->st));
+        for (int k = 0; k < b->refine_every && total < max_iter; ++k) {
+            BCK(cudaGraphLaunch(b->graph_corr, b->st));
+            BRCK(read_member_rel(b, rel));
+            total++;
+            double rd = 0.0;
+            for (int m = 0; m < b->nm; ++m)
+                if (active[m]) rd = std::max(rd, rel[m]);
+            if (rd < inner_tol) break;
+        }
+        k_badd<<<152 * 8, 256, 0, b->st>>>(b->ntot, b->S, b->D);
+        BCK(cudaGetLastError());
     }
+    BCK(cudaStreamSynchronize(b->st));
     if (iters) std::copy(done.begin(), done.end(), iters);
-    return bfail(RT_ENOTCONVERGED, "not every member converged in " + std::to_string(max_iter) + " iterations");
+    return bfail(RT_ENOTCONVERGED, "not every member converged in " + std::to_string(max_iter) + " formal solutions");
 }
 
 int rt_batch_get(const rt_batch *b, int m, int what, double *out, int where)
@@ -711,6 +873,10 @@ int rt_batch_autotune(rt_batch *b, int32_t *chunk_out, int32_t *grid_out, double
     b->grid_march = b->grid_gather = bg;
     BRCK(build_prefixes(b));
     BRCK(capture(b));
+    if (b->graph_corr) {  // recaptured with the chosen bundle size at the next rt_batch_solve
+        cudaGraphExecDestroy(b->graph_corr);
+        b->graph_corr = nullptr;
+    }
     BCK(cudaStreamSynchronize(b->st));
     auto it = std::find(b->allocs.begin(), b->allocs.end(), (void *)saveS);
     if (it != b->allocs.end()) b->allocs.erase(it);

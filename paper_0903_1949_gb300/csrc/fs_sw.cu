@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "coef.cuh"
 #include "rt_internal.h"
 
@@ -837,12 +839,16 @@ template <int K, int NS, bool BULK>
 cudaError_t launch_ring(const SwMarch &m, int64_t grid, cudaStream_t st)
 {
     constexpr size_t bytes = tma_smem_bytes<K, NS>();
-    static bool attr = false;  // per process: the attribute is a property of the kernel
-    if (!attr) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_march_tma<K, NS, BULK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    // the attribute belongs to the kernel on one device: set once per device
+    static std::atomic<uint64_t> done{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev < 64 ? (uint64_t)1 << dev : 0;
+    if (!bit || !(done.load(std::memory_order_acquire) & bit)) {
+        e = cudaFuncSetAttribute(k_march_tma<K, NS, BULK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
-        attr = true;
+        done.fetch_or(bit, std::memory_order_acq_rel);
     }
     k_march_tma<K, NS, BULK><<<(unsigned)grid, 256, bytes, st>>>(m);
     return cudaGetLastError();

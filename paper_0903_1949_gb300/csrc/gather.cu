@@ -137,8 +137,8 @@ __global__ void k_invL(int nvox, const int32_t *off, const int32_t *perm, const 
 }
 
 template <typename P>
-__global__ void k_gather_angle(int nvox, const int32_t *off, const int32_t *perm, const P *buf, int64_t s_lo,
-                               int64_t s_hi, const double *invL_w, double *Ibar, double *Lbar)
+__global__ void k_gather_angle(int nvox, const int32_t *off, const int32_t *perm, const P *buf, int64_t base,
+                               int64_t s_lo, int64_t s_hi, const double *invL_w, double *Ibar, double *Lbar)
 {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nvox) return;
@@ -146,7 +146,7 @@ __global__ void k_gather_angle(int nvox, const int32_t *off, const int32_t *perm
     for (int e = off[v]; e < off[v + 1]; ++e) {
         int s = perm[e];
         if (s < s_lo || s >= s_hi) continue;
-        P val = buf[s];
+        P val = buf[s - base];
         aI += (double)val.x;
         aL += (double)val.y;
     }
@@ -873,17 +873,25 @@ cudaError_t gather_multi_rows(int nvox, const int64_t *ufirst, int32_t *flag, in
     return cudaGetLastError();
 }
 
-cudaError_t gather_angle_range(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const void *buf, int fp32,
-                               int64_t s_lo, int64_t s_hi, const double *invL_w, double *Ibar, double *Lbar,
-                               cudaStream_t st)
+cudaError_t gather_angle_range(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const void *buf,
+                               int64_t buf_base, int fp32, int64_t s_lo, int64_t s_hi, const double *invL_w,
+                               double *Ibar, double *Lbar, cudaStream_t st)
 {
     if (fp32)
-        k_gather_angle<float2><<<(nvox + 255) / 256, 256, 0, st>>>(nvox, csr_off, perm_blk, (const float2 *)buf, s_lo,
-                                                                   s_hi, invL_w, Ibar, Lbar);
+        k_gather_angle<float2><<<(nvox + 255) / 256, 256, 0, st>>>(nvox, csr_off, perm_blk, (const float2 *)buf,
+                                                                   buf_base, s_lo, s_hi, invL_w, Ibar, Lbar);
     else
-        k_gather_angle<double2><<<(nvox + 255) / 256, 256, 0, st>>>(nvox, csr_off, perm_blk, (const double2 *)buf, s_lo,
-                                                                    s_hi, invL_w, Ibar, Lbar);
+        k_gather_angle<double2><<<(nvox + 255) / 256, 256, 0, st>>>(nvox, csr_off, perm_blk, (const double2 *)buf,
+                                                                    buf_base, s_lo, s_hi, invL_w, Ibar, Lbar);
     return cudaGetLastError();
+}
+
+cudaError_t gather_angle_preload()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_gather_angle<float2>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_gather_angle<double2>);
+    return e;
 }
 
 cudaError_t flux_local(const GeomDev &G, const double *Fc, double *F, cudaStream_t st)

@@ -138,6 +138,11 @@ struct rt_grid {
 int rt_grid_member_fs(rt_grid *g, const float2 *cs, const float *B32, const uint32_t *pbits, double *J, double *L,
                       double *Fc, cudaStream_t st);
 
+// FP64 J of another opacity field on this grid's geometry (a batch member):
+// (chi, S) packed in cs64, B, parabola choices in pbits.  Runs on st.
+int rt_grid_member_fs64J(rt_grid *g, const double2 *cs64, const double *B64, const uint32_t *pbits, double *J,
+                         cudaStream_t st);
+
 // The exact nearest-neighbour Lambda* (27 entries per voxel, slot q = 9 (di+1) +
 // 3 (dj+1) + (dk+1), phi periodic) of another opacity field chi, with its
 // parabola choices pbits (bit per segment, as para_bits), on this grid's

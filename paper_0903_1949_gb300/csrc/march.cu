@@ -255,6 +255,20 @@ __global__ void __launch_bounds__(256) k_march_bits(const uint32_t *__restrict__
                                                outv, chunk, pbits);
 }
 
+// FP64 J-only march (l I per segment) with the parabola choices of a bitmask:
+// the FP64 residual of a batch member (its chi differs from the grid's).
+__global__ void __launch_bounds__(256) k_march_bits64J(const uint32_t *__restrict__ vox, const double *__restrict__ len,
+                                                       const int64_t *__restrict__ ray_off, int64_t r_lo, int64_t r_hi,
+                                                       int64_t seg_lo, int64_t nseg, const double2 *__restrict__ cs,
+                                                       const double *__restrict__ Bv, double I_outer, int homog,
+                                                       double *__restrict__ out, int chunk,
+                                                       const uint32_t *__restrict__ pbits)
+{
+    const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    march_bundle<double, double2, 1, false, true>(vox, len, ray_off, r_lo, r_hi, seg_lo, nseg, wg, cs, Bv, I_outer,
+                                                  homog, out, chunk, pbits);
+}
+
 // Persistent batched march (FP32, J only): the warps of a grid sized to the
 // GPU take bundles of all work items (member x angle block, uneven grids
 // mixed) from a device counter until none is left.
@@ -403,6 +417,19 @@ cudaError_t march_block_bits(const uint32_t *vox, const float *len, const int64_
     return cudaGetLastError();
 }
 
+cudaError_t march_block_bits64J(const uint32_t *vox, const double *len, const int64_t *ray_off, int64_t r_lo,
+                                int64_t r_hi, int64_t seg_lo, int64_t nseg, const double2 *chiS, const double *B,
+                                double I_outer, int homog, double *out, int chunk, const uint32_t *pbits,
+                                cudaStream_t st)
+{
+    if (nseg <= 0) return cudaSuccess;
+    int64_t warps = (nseg + chunk - 1) / chunk;
+    int64_t blocks = (warps + 7) / 8;
+    k_march_bits64J<<<(unsigned)blocks, 256, 0, st>>>(vox, len, ray_off, r_lo, r_hi, seg_lo, nseg, chiS, B, I_outer,
+                                                      homog, out, chunk, pbits);
+    return cudaGetLastError();
+}
+
 cudaError_t para_bits(const uint32_t *vox, const double *len64, const double *chi, int64_t nseg, int parabolic,
                       uint32_t *bits, cudaStream_t st)
 {
@@ -412,6 +439,14 @@ cudaError_t para_bits(const uint32_t *vox, const double *len64, const double *ch
     if (blocks > 152 * 32) blocks = 152 * 32;
     k_para_bits<<<(unsigned)blocks, 256, 0, st>>>(vox, len64, chi, nseg, parabolic, bits);
     return cudaGetLastError();
+}
+
+cudaError_t march_block_preload()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_march4<float, float2, 2, true>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_march4<double, double2, 1, true>);
+    return e;
 }
 
 template cudaError_t march_block_J<double, double2>(const uint32_t *, const double *, const int64_t *, int64_t, int64_t,

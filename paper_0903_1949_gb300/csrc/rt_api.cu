@@ -1469,6 +1469,24 @@ int rt_grid_member_fs(rt_grid *g, const float2 *cs, const float *B32, const uint
     return RT_OK;
 }
 
+int rt_grid_member_fs64J(rt_grid *g, const double2 *cs64, const double *B64, const uint32_t *pbits, double *J,
+                         cudaStream_t st)
+{
+    const int n = g->nvox;
+    for (int b = 0; b < g->nblk; ++b) {
+        int w0 = g->blk_w0[b], nw = g->blk_nw[b];
+        int64_t r_lo = g->h_ang_ray_off[w0], r_hi = g->h_ang_ray_off[w0 + nw];
+        int64_t lo = g->h_ang_seg_off[w0], ns = g->h_ang_seg_off[w0 + nw] - lo;
+        const int32_t *off = g->d_csr_off + (size_t)b * (n + 1);
+        double *buf = (double *)g->d_segbuf;
+        CK(march_block_bits64J(g->d_vox, g->d_len64, g->d_ray_off, r_lo, r_hi, lo, ns, cs64, B64, g->I_outer, 0, buf,
+                               g->march_chunk, pbits, st));
+        CK(gather_J<double>(n, off, g->jt[b], g->d_perm + lo, buf, g->d_ang_seg_off, w0, nw, lo, g->d_wL32,
+                            g->d_invL, g->d_wt, g->d_partJ, J, b == 0, st));
+    }
+    return RT_OK;
+}
+
 extern "C" {
 
 const char *rt_last_error(void) { return g_err.c_str(); }
@@ -1505,7 +1523,8 @@ int rt_grid_create(rt_grid **out, const rt_grid_desc *d)
     for (int a = 0; a < 3; ++a) g->h_e[a].assign(d->edges[a], d->edges[a] + d->n[a] + 1);
     g->h_dirs.assign(d->dirs, d->dirs + 3 * (size_t)d->n_angles);
     g->h_wt.assign(d->weights, d->weights + d->n_angles);
-    int rc = upload_tables(g);
+    int rc = noalloc_prepare(g->device);
+    if (rc == RT_OK) rc = upload_tables(g);
     if (rc == RT_OK) rc = build_geometry(g);
     if (rc == RT_OK) rc = alloc_fields(g);
     if (rc == RT_OK) rc = sync(g);
@@ -1554,7 +1573,6 @@ int rt_set_opacity(rt_grid *g, const double *chi, const double *eps, const doubl
     if (!g || !chi || !eps || !B) return fail(RT_EINVAL, "NULL argument");
     if (where != RT_HOST && where != RT_DEVICE) return fail(RT_EINVAL, "where must be RT_HOST or RT_DEVICE");
     CK(cudaSetDevice(g->device));
-    drop_graph(g);
     const size_t n = g->nvox;
     if (where == RT_HOST) {
         for (size_t v = 0; v < n; ++v) {
@@ -1562,7 +1580,22 @@ int rt_set_opacity(rt_grid *g, const double *chi, const double *eps, const doubl
             if (!(eps[v] > 0.0 && eps[v] <= 1.0)) return fail(RT_EINVAL, "eps[%zu] must be in (0, 1]", v);
             if (!(B[v] >= 0.0) || !std::isfinite(B[v])) return fail(RT_EINVAL, "B[%zu] must be >= 0 and finite", v);
         }
+    } else {  // device input: checked on the device before anything is copied (one wait)
+        CK(check_opacity(g->nvox, chi, eps, B, g->d_maxrel, g->st));
+        g->launches++;
+        CK(cudaMemcpyAsync(g->h_pin, g->d_maxrel, sizeof(unsigned long long), cudaMemcpyDeviceToHost, g->st));
+        RCK(sync(g));
+        unsigned long long bad = 0;
+        std::memcpy(&bad, g->h_pin, sizeof(bad));
+        if (bad != ~0ull) {
+            const unsigned long long v = bad >> 2;
+            const int c = (int)(bad & 3ull);
+            if (c == 0) return fail(RT_EINVAL, "chi[%llu] must be > 0 and finite", v);
+            if (c == 1) return fail(RT_EINVAL, "eps[%llu] must be in (0, 1]", v);
+            return fail(RT_EINVAL, "B[%llu] must be >= 0 and finite", v);
+        }
     }
+    drop_graph(g);
     cudaMemcpyKind kind = where == RT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     CK(cudaMemcpyAsync(g->d_chi, chi, sizeof(double) * n, kind, g->st));
     CK(cudaMemcpyAsync(g->d_eps, eps, sizeof(double) * n, kind, g->st));
@@ -1914,7 +1947,7 @@ int rt_fs_angles(rt_grid *g, const int32_t *omegas, int n, int precision, double
             CK(march_block<float, float2>(g->d_vox, g->d_len32, g->d_ray_off, r_lo, r_hi, lo, ns, g->d_cs32, g->d_B32,
                                           (float)g->I_outer, 0, para, (float2 *)g->d_segbuf, g->march_chunk, g->st));
         marched = b;
-        CK(gather_angle_range(nv, off, g->d_perm + lo, g->d_segbuf, precision == RT_MIXED,
+        CK(gather_angle_range(nv, off, g->d_perm + lo, g->d_segbuf, 0, precision == RT_MIXED,
                               g->h_ang_seg_off[w] - lo, g->h_ang_seg_off[w + 1] - lo, g->d_invL + (size_t)w * nv, tI,
                               tL, g->st));
         cudaMemcpyKind kind = where == RT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;

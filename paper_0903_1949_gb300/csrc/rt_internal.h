@@ -163,10 +163,22 @@ struct GatherItem {
 cudaError_t gather_J_batch(const GatherItem *items, const int64_t *wpfx, int n_items, int64_t total,
                            unsigned long long *counter, int grid_blocks, cudaStream_t st);
 
-// Ibar, Lbar of one solid angle whose segments are [s_lo, s_hi) of the block.
-cudaError_t gather_angle_range(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const void *buf, int fp32,
-                               int64_t s_lo, int64_t s_hi, const double *invL_w, double *Ibar, double *Lbar,
-                               cudaStream_t st);
+// Ibar, Lbar of one solid angle whose segments are [s_lo, s_hi) of the block;
+// the value of block segment s is buf[s - buf_base].
+cudaError_t gather_angle_range(int nvox, const int32_t *csr_off, const int32_t *perm_blk, const void *buf,
+                               int64_t buf_base, int fp32, int64_t s_lo, int64_t s_hi, const double *invL_w,
+                               double *Ibar, double *Lbar, cudaStream_t st);
+// Loads the kernels of gather_angle_range and march_block on the current device
+// (modules load lazily otherwise, on their first launch).
+cudaError_t gather_angle_preload();
+cudaError_t march_block_preload();
+cudaError_t pack_preload();
+// *first_bad = min over bad voxels v of 4 v + c (c: 0 chi, 1 eps, 2 B), all ones if none (ali.cu).
+cudaError_t check_opacity(int nvox, const double *chi, const double *eps, const double *B,
+                          unsigned long long *first_bad, cudaStream_t st);
+// Resolves the device address of the allocation-free path's static scratch on
+// device dev (current) and loads the kernels that path launches (noalloc.cu).
+int noalloc_prepare(int dev);
 cudaError_t flux_local(const GeomDev &G, const double *Fc, double *F, cudaStream_t st);
 
 // ---- ray march (march.cu) ----
@@ -277,6 +289,11 @@ cudaError_t march_batch(const MarchItem *items, const int64_t *bpfx, int n_items
 cudaError_t march_block_bits(const uint32_t *vox, const float *len, const int64_t *ray_off, int64_t r_lo, int64_t r_hi,
                              int64_t seg_lo, int64_t nseg, const float2 *chiS, const float *B, float I_outer,
                              float2 *out, int chunk, const uint32_t *pbits, cudaStream_t st);
+// FP64 march writing l I per segment with the parabola choices of a bitmask.
+cudaError_t march_block_bits64J(const uint32_t *vox, const double *len, const int64_t *ray_off, int64_t r_lo,
+                                int64_t r_hi, int64_t seg_lo, int64_t nseg, const double2 *chiS, const double *B,
+                                double I_outer, int homog, double *out, int chunk, const uint32_t *pbits,
+                                cudaStream_t st);
 cudaError_t para_bits(const uint32_t *vox, const double *len64, const double *chi, int64_t nseg, int parabolic,
                       uint32_t *bits, cudaStream_t st);
 // Parabola-guard decision per segment, taken once in FP64 from chi and the FP64

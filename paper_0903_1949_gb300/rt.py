@@ -117,6 +117,7 @@ def load():
         "rt_line_solve": [_P, ctypes.c_double, _I, ctypes.POINTER(ctypes.c_int32)],
         "rt_line_get": [_P, _I, _P, _I],
         "rt_fs_sweep": [ctypes.POINTER(rt_grid_desc), _I, _P, _P, _P, _I, _P, _P, _I],
+        "rt_measure_fp64_rate": [_I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -365,6 +366,13 @@ def rt_fs_angle_noalloc(h, omega, precision, Ibar_dev, Lbar_dev):
 
 def rt_tune(h, knob, value):
     return _check(load().rt_tune(h, int(knob), int(value)))
+
+
+def rt_measure_fp64_rate(device=0):
+    """(FP64 flop/s of the device, ms per launch of the FMA-chain kernel)."""
+    f, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().rt_measure_fp64_rate(int(device), ctypes.byref(f), ctypes.byref(ms)))
+    return f.value, ms.value
 
 
 def rt_set_timing(h, enable=True):
