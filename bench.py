@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-angles", type=int, default=48, help="solid angles in the CPU oracle sample")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-wavelength batch measurement")
+    ap.add_argument("--no-disc", action="store_true", help="skip the cylindrical-disc (65^3, 64x64 angles) steps")
     ap.add_argument("--no-convergence", action="store_true", help="skip the time-to-convergence comparison")
     ap.add_argument("--no-line", action="store_true", help="skip the two-level-atom line measurement")
     ap.add_argument("--flux-max", type=int, default=64,
@@ -179,6 +180,22 @@ def ncu_traffic(segments_per_launch):
     return d["dram_bytes_per_segment"] * segments_per_launch, d.get("capture")
 
 
+FP64_SRC = [os.path.join(ROOT, "paper_0903_1949_gb300", "csrc", f) for f in ("fs_sw.cu", "march.cu", "coef.cuh")]
+
+
+def fp64_flops_per_segment():
+    """FP64 flops per crossing segment of the FP64 marches from the committed ncu counts, if taken of this source."""
+    path = os.path.join(ROOT, "profiles", "fp64_flops.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None, None
+    h = hashlib.sha256(b"".join(open(f, "rb").read() for f in FP64_SRC)).hexdigest()
+    if d.get("source_sha256") != h:
+        return None, "stale"
+    return d, d.get("capture")
+
+
 def workload_text(p):
     n = p["n"]
     kind = "spherical" if p["coord"] == 0 else "cylindrical"
@@ -202,6 +219,25 @@ def oracle_parallel_fs(p, steps=1, warmup=1):
     dt = (time.perf_counter() - t0) / steps
     o.close()
     return dt, used
+
+
+def fp64_roofline(flops, src, n_seg, ms_streamed, ms_plain, peak):
+    """FP64 path against the measured FP64 FMA rate: the J-only march over streamed FP64 weights
+    (the FP64 step) and the march that evaluates its weights (the plain FP64 step)."""
+    if not flops:
+        return {"bound": "fp64-alu", "achieved": None, "peak": peak["flops_per_s"] / 1e12, "unit": "TFLOP/s",
+                "frac": None, "flops_source": src or "missing"}
+    out = {"bound": "fp64-alu", "unit": "TFLOP/s", "peak": peak["flops_per_s"] / 1e12,
+           "peak_source": "rt_measure_fp64_rate on this GPU in this run", "flops_source": src}
+    for key, ms in (("streamed", ms_streamed), ("plain", ms_plain)):
+        f = flops[key + "_flops_per_segment"] * n_seg
+        out[key] = {"flops_per_segment": flops[key + "_flops_per_segment"], "achieved": f / (ms / 1e3) / 1e12,
+                    "frac": f / (ms / 1e3) / peak["flops_per_s"],
+                    "timing": "FP64 flops of the step's march (ncu thread-instruction counts per segment x segments) "
+                              "over the event-timed step"}
+    out["achieved"] = out["streamed"]["achieved"]
+    out["frac"] = out["streamed"]["frac"]
+    return out
 
 
 def cpu_oracle_sample(p, n_angles):
@@ -366,6 +402,7 @@ def main():
     ms64p = timed(g.ali_step, 2)
     g.tune(rt.RT_TUNE_STREAMED_WEIGHTS, 1)
     value64p = job_throughput(units, world, ms64p)
+    flops64, flops64_src = fp64_flops_per_segment()
 
     # ---- FP64 FMA rate of this device: the denominator of the FP64 path's roofline ----
     ck64 = Clocks(local)
@@ -421,11 +458,15 @@ def main():
         flux_res = flux_resolution(args.workload, args.flux_max, rt, I)
 
     batch = None
-    if not args.no_batch and rank == 0:
+    disc = None
+    if rank == 0 and (not args.no_batch or not args.no_disc):
         g.close()
         g = None
         torch.cuda.empty_cache()
+    if not args.no_batch and rank == 0:
         batch = batch_measure(rt, I, torch, max(3, args.steps // 3))
+    if not args.no_disc and rank == 0:
+        disc = disc_measure(rt, I, torch, max(5, args.steps // 2))
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -443,6 +484,7 @@ def main():
                        "geometry_lists_ms": info["geometry_lists_ms"], "device_gb": info["device_bytes"] / 1e9},
             "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "steps": k64, "fp64_peak": fp64_peak,
                      "mixed_over_fp64": value / value64,
+                     "roofline": fp64_roofline(flops64, flops64_src, info["n_segments"], ms64, ms64p, fp64_peak),
                      "path": "FP64 march with FP64 weights streamed per chi (48 B per segment), FP64 gather",
                      "plain": {"value": value64p, "ms_per_step": ms64p, "steps": 2,
                                "mixed_over_fp64_plain": value / value64p,
@@ -451,13 +493,14 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "traffic_over_algorithmic": (traffic / (ALGO_BYTES_PER_SEGMENT * seg_per_launch)
                                                       if traffic else None),
-                         "kernel": "k_march_sw<2> (FP32 streamed-weight ray march, J only)",
+                         "kernel": "k_march_sw (FP32 streamed-weight ray march, J only)",
                          "algorithmic_bytes": "%d B per crossing segment (int32 voxel id + FP32 path length, the "
                                               "method's minimum stream)" % ALGO_BYTES_PER_SEGMENT,
                          "design_bytes": {"per_segment": bytes_per_seg, "achieved": achieved_design,
                                           "frac": achieved_design / peak,
-                                          "what": "bytes this design streams per segment: u32 voxel word + FP32 E, "
-                                                  "alpha, beta, gamma + FP32 w l/L + i32 list position"},
+                                          "what": "bytes this design streams per segment: u32 voxel word + four FP32 "
+                                                  "weights (E, alpha, beta, gamma, with the gather weight w l/L folded "
+                                                  "in when 24 B) + i32 list position"},
                          "segments_per_launch": seg_per_launch, "avg_launch_ms": march_avg_ms,
                          "avg_launch_ms_events": march_event_ms,
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src if peak_src == "measured"
@@ -481,6 +524,8 @@ def main():
         line["fresh_chi"] = fresh
     if batch is not None:
         line["batch"] = batch
+    if disc is not None:
+        line["disc_cyl65"] = disc
     if conv is not None:
         line["convergence"] = conv
     if line_res is not None:
@@ -534,6 +579,69 @@ def batch_measure(rt, I, torch, steps):
     b.close()
     for q in grids:
         q.close()
+    return out
+
+
+def disc_measure(rt, I, torch, steps, name="cyl65"):
+    """The cylindrical disc (65 x 65 x 65 voxels, R 0.1..10, |z| <= 2, transparent hole;
+    64 x 64 solid angles; chi = chi0 (R/R0)^-1.5 exp(-z^2 / 2 (0.1 R)^2), midplane tau 1e3,
+    eps 1e-6, B ~ R^-0.75): mixed-precision and FP64 ALI steps as on the spherical
+    workload, and one FP32 formal solution against one FP64 one from the same S."""
+    p = I.make_problem(name)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=rt.RT_MIXED,
+                stream=stream.cuda_stream)
+    t_geom = time.perf_counter() - t0
+    units = p["chi"].size * p["n_ang"]
+    out = {"workload": workload_text(p), "geometry_s": t_geom}
+    try:
+        g.set_opacity(p["chi"], p["eps"], p["B"])
+
+        def timed(k):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(k):
+                g.ali_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / k
+
+        for _ in range(4):
+            g.ali_step()
+        ms = timed(steps)
+        info = g.info()
+        out["mixed"] = {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+                        "segments_per_step": info["n_segments"],
+                        "segments_per_voxel_angle": info["n_segments"] / units, "device_gb": info["device_bytes"] / 1e9}
+        S = p["B"] * np.random.default_rng(3).uniform(0.8, 1.2, p["B"].size)  # as on the spherical workload
+        fs = {}
+        for prec, label in ((rt.RT_FP64, "fp64"), (rt.RT_MIXED, "fp32")):
+            g.set_S(S)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            g.formal_solution(prec)
+            torch.cuda.synchronize()
+            fs[label] = (time.perf_counter() - t1, g.J())
+        out["formal_solution"] = {"max_rel_J_diff": float(np.max(np.abs(fs["fp32"][1] - fs["fp64"][1])
+                                                                 / np.abs(fs["fp64"][1]))),
+                                  "fp64_ms": fs["fp64"][0] * 1e3, "fp32_ms": fs["fp32"][0] * 1e3,
+                                  "note": "full formal solution (J, Lambda*, flux) from the same S = B x U(0.8, 1.2), "
+                                          "host-timed"}
+        g.set_precision(rt.RT_FP64)
+        g.set_S(p["B"])
+        for _ in range(3):
+            g.ali_step()
+        ms64 = timed(2)
+        info = g.info()
+        out["fp64"] = {"value": units / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "steps": 2,
+                       "device_gb": info["device_bytes"] / 1e9,
+                       "note": "FP64 weights streamed per chi when they fit in device memory, else evaluated per "
+                               "segment"}
+        out["mixed_over_fp64"] = ms64 / ms
+    finally:
+        g.close()
     return out
 
 

@@ -150,12 +150,13 @@ int rt_set_precision(rt_grid *g, int precision);
 #define RT_TUNE_MARCH_CHUNK 1
 /* RT_TUNE_STREAMED_WEIGHTS (default 1): the J-only march of the ALI iteration
  * streams per-segment weights (E, alpha, beta, gamma) evaluated once per chi
- * in FP64 and the gather weight w l / L: as FP32 for RT_MIXED (20 extra bytes
- * per segment of device memory), as FP64 for RT_FP64 (40 bytes), each
+ * in FP64 and the gather weight w l / L: as FP32 for RT_MIXED (16 extra bytes
+ * per segment of device memory with the gather weight folded in, see
+ * RT_TUNE_FOLD_WEIGHT; 20 without), as FP64 for RT_FP64 (40 bytes), each
  * allocated at its first use; 0, or when that memory is not available: the
  * march evaluates the weights itself from chi and l.
- * RT_TUNE_MARCH_COARSEN: segments per lane of the streamed-weight march, 1, 2
- * (default) or 4.  RT_TUNE_OVERLAP (default 1): the J gather of angle block b
+ * RT_TUNE_MARCH_COARSEN: segments per lane of the streamed-weight march, 1
+ * (default), 2 or 4.  RT_TUNE_OVERLAP (default 1): the J gather of angle block b
  * runs on a second stream of the library while block b + 1 is marched (the
  * grid's stream waits for it before the call returns its work); 0: both on
  * the grid's stream.  RT_TUNE_SCATTER (default 1): the streamed-weight march
@@ -220,6 +221,13 @@ int rt_set_precision(rt_grid *g, int precision);
  * decisions stay the exact serial ones, so the launch set and the crossing
  * lists are the same as with 0.  Other knobs need a grid. */
 #define RT_TUNE_GEOM_PREDICT 16
+/* RT_TUNE_FOLD_WEIGHT (default 1): the FP32 streamed-weight march carries the
+ * gather weight c = w_Omega l / L of each segment inside its four weights
+ * (it marches c_k I_k: E c_k / c_{k-1}, c alpha, c beta, c gamma, all formed in
+ * FP64 once per chi), so the per-segment c stream is not read: 24 instead of
+ * 28 bytes per segment.  Register-prefetch march only (RT_TUNE_MARCH_STAGES 0);
+ * agrees with 0 to FP32 rounding. */
+#define RT_TUNE_FOLD_WEIGHT 17
 int rt_tune(rt_grid *g, int knob, int value);
 
 /* Formal solution from the current S with the grid's precision: J, the

@@ -128,7 +128,9 @@ __device__ __forceinline__ Wd4 ldw(const Wd4 *p)
 
 // SLA: the S lookups of tile t + 1 are issued while tile t is marched (its
 // words are loaded two tiles ahead), so no tile waits for its own lookups.
-template <typename M, int K, bool SLA>
+// FOLD: the weights carry the gather weight (k_coef_stream_fold); the c stream
+// is not read and the recurrence value is the output itself.
+template <typename M, int K, bool SLA, bool FOLD = false>
 __device__ __forceinline__ void march_sw(const M &m, int64_t wg)
 {
     using T = typename M::T;
@@ -155,7 +157,7 @@ __device__ __forceinline__ void march_sw(const M &m, int64_t wg)
         const bool ok = s < s_end;
         w[j] = ok ? __ldcs(vx + s) : 0u;
         c[j] = ok ? ldw(cf + s) : W{1, 0, 0, 0};
-        g[j] = ok ? __ldcs(gw + s) : T(0);
+        g[j] = FOLD ? T(1) : (ok ? __ldcs(gw + s) : T(0));
         p[j] = (ps && ok) ? __ldcs(ps + s) : 0;
     }
     uint32_t wA[K];  // SLA: words of the next tile
@@ -189,7 +191,7 @@ __device__ __forceinline__ void march_sw(const M &m, int64_t wg)
             const bool ok = s < s_end;
             wN[j] = SLA ? wA[j] : (ok ? __ldcs(vx + s) : 0u);
             cN[j] = ok ? ldw(cf + s) : W{1, 0, 0, 0};
-            gN[j] = ok ? __ldcs(gw + s) : T(0);
+            gN[j] = FOLD ? T(1) : (ok ? __ldcs(gw + s) : T(0));
             pN[j] = (ps && ok) ? __ldcs(ps + s) : 0;
         }
         T S[K], SN[K];
@@ -697,10 +699,10 @@ __global__ void k_inv_perm(const int32_t *perm, int64_t n, int32_t *pos)
         pos[perm[e]] = (int32_t)e;
 }
 
-template <typename M, int K, bool SLA>
+template <typename M, int K, bool SLA, bool FOLD = false>
 __global__ void __launch_bounds__(256) k_march_sw(M m)
 {
-    march_sw<M, K, SLA>(m, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    march_sw<M, K, SLA, FOLD>(m, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
 }
 
 // FP64 weights of every segment for the current chi, rounded to FP32.
@@ -719,6 +721,41 @@ __global__ void k_coef_stream(const uint32_t *__restrict__ vox, const double *__
             al = 0.0;
         }
         cw[s] = make_float4((float)E, (float)al, (float)be, (float)ga);
+    }
+}
+
+// The FP64 weights with the gather weight folded in: the march then carries
+// c_s I_s, whose recurrence has the weights (E c_s / c_{s-1}, c_s alpha,
+// c_s beta, c_s gamma); at a characteristic start A = 0 and the E slot holds
+// c_s E (the incoming intensity's factor).  c_s = w_Omega l_s / L_{Omega v_s}
+// in FP64 as k_seg_weight forms it.
+__global__ void k_coef_stream_fold(const uint32_t *__restrict__ vox, const double *__restrict__ len64,
+                                   const double *__restrict__ chi, const int64_t *__restrict__ ang_seg_off, int n_ang,
+                                   const double *__restrict__ wt, const double *__restrict__ invL, int nvox,
+                                   int64_t nseg, float4 *__restrict__ cw)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nseg; s += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_ang;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (ang_seg_off[mid] <= s) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t w = vox[s];
+        const bool para = (w & RTK_PARA) != 0u;
+        const double x = chi[w & RTK_VOXMASK] * len64[s];
+        const double p = para ? chi[vox[s + 1] & RTK_VOXMASK] * len64[s + 1] : 0.0;
+        double E, al, be, ga;
+        Coef64::eval(x, p, para, E, al, be, ga);
+        if (w & (RTK_RAYSTART | RTK_RESTART)) {
+            be += al;
+            al = 0.0;
+        }
+        const double *iL = invL + (int64_t)lo * nvox;
+        const double c = wt[lo] * len64[s] * iL[w & RTK_VOXMASK];
+        double A = c * E;
+        if (!(w & RTK_RAYSTART)) A /= wt[lo] * len64[s - 1] * iL[vox[s - 1] & RTK_VOXMASK];
+        cw[s] = make_float4((float)A, (float)(c * al), (float)(c * be), (float)(c * ga));
     }
 }
 
@@ -867,6 +904,11 @@ cudaError_t march_sw_launch(const SwMarch &m, int coarsen, cudaStream_t st)
     const int64_t grid = (m.nbundles + 7) / 8;
     if (grid <= 0) return cudaSuccess;
     if (m.stages >= 2) return m.bulk ? launch_ring_k<true>(m, coarsen, grid, st) : launch_ring_k<false>(m, coarsen, grid, st);
+    if (m.fold) {  // register prefetch with lookahead only
+        if (coarsen == 1) k_march_sw<SwMarch, 1, true, true><<<(unsigned)grid, 256, 0, st>>>(m);
+        else k_march_sw<SwMarch, 2, true, true><<<(unsigned)grid, 256, 0, st>>>(m);
+        return cudaGetLastError();
+    }
     if (m.lookahead) {
         if (coarsen == 4) k_march_sw<SwMarch, 4, true><<<(unsigned)grid, 256, 0, st>>>(m);
         else if (coarsen == 1) k_march_sw<SwMarch, 1, true><<<(unsigned)grid, 256, 0, st>>>(m);
@@ -935,6 +977,15 @@ cudaError_t coef_stream(const uint32_t *vox, const double *len64, const double *
 {
     if (nseg <= 0) return cudaSuccess;
     k_coef_stream<<<grid_cap(nseg), 256, 0, st>>>(vox, len64, chi, nseg, cw);
+    return cudaGetLastError();
+}
+
+cudaError_t coef_stream_fold(const uint32_t *vox, const double *len64, const double *chi, const int64_t *ang_seg_off,
+                             int n_ang, const double *wt, const double *invL, int nvox, int64_t nseg, float4 *cw,
+                             cudaStream_t st)
+{
+    if (nseg <= 0) return cudaSuccess;
+    k_coef_stream_fold<<<grid_cap(nseg), 256, 0, st>>>(vox, len64, chi, ang_seg_off, n_ang, wt, invL, nvox, nseg, cw);
     return cudaGetLastError();
 }
 

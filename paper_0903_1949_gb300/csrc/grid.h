@@ -86,12 +86,14 @@ struct rt_grid {
     bool cw64_ok = false;
     int pos_state = 0;        // list positions: 0 not tried, 1 allocated, -1 not available
     bool cw_ok = false;       // d_cw4 matches the current chi
-    int sw_coarsen = 2;       // segments per lane (RT_TUNE_MARCH_COARSEN)
+    int sw_coarsen = 1;       // segments per lane (RT_TUNE_MARCH_COARSEN)
     int sw_overlap = 1;       // gather of block b on st2 while block b + 1 is marched (RT_TUNE_OVERLAP)
     int sw_scatter = 1;       // march stores in ownership-list order (RT_TUNE_SCATTER)
     int sw_stages = 0;        // shared-memory ring depth of the streamed-weight march (RT_TUNE_MARCH_STAGES)
     int sw_bulk = 0;          // ring filled by bulk copies instead of cp.async (RT_TUNE_MARCH_BULK)
     int sw_lookahead = 1;
+    int sw_fold = 1;          // gather weight folded into the streamed weights (RT_TUNE_FOLD_WEIGHT)
+    int cw_fold = -1;         // the fold state the current d_cw4 was built with
     // blocked voxel order of the FP32 streamed-weight march's S lookups (RT_TUNE_S_BLOCKED)
     int sblk = 1, sblk_state = 0;
     int32_t *d_vblk = nullptr;

@@ -832,33 +832,42 @@ bool sw_common(rt_grid *g)
 bool use_sw(rt_grid *g)
 {
     if (!g->sw_enabled || g->sw_state < 0) return false;
+    const int fold = g->sw_fold && g->sw_stages == 0;
     if (g->sw_state == 0) {
-        void *a = nullptr, *b = nullptr;
-        if (cudaMalloc(&a, sizeof(float4) * (size_t)g->n_seg) != cudaSuccess ||
-            cudaMalloc(&b, sizeof(float) * (size_t)(g->n_seg + 4)) != cudaSuccess) {
+        void *a = nullptr;
+        if (cudaMalloc(&a, sizeof(float4) * (size_t)g->n_seg) != cudaSuccess) {
             cudaGetLastError();
-            if (a) cudaFree(a);
             g->sw_state = -1;
             return false;
         }
         g->allocs.push_back(a);
-        g->allocs.push_back(b);
-        g->bytes += (int64_t)(20 * g->n_seg);
+        g->bytes += (int64_t)(16 * g->n_seg);
         g->d_cw4 = (float4 *)a;
-        g->d_cg = (float *)b;
-        if (seg_weight(g->d_vox, g->d_len64, g->d_ang_seg_off, g->n_ang, g->d_wt, g->d_invL, g->nvox, g->n_seg, g->d_cg,
-                       g->st) != cudaSuccess) {
-            g->sw_state = -1;
-            return false;
-        }
-        g->launches++;
         g->sw_state = 1;
         g->cw_ok = false;
     }
-    if (!g->cw_ok) {
-        if (coef_stream(g->d_vox, g->d_len64, g->d_chi, g->n_seg, g->d_cw4, g->st) != cudaSuccess) return false;
+    if (!fold && !g->d_cg) {  // the separate gather-weight stream of the unfolded march
+        void *b = nullptr;
+        if (cudaMalloc(&b, sizeof(float) * (size_t)(g->n_seg + 4)) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        g->allocs.push_back(b);
+        g->bytes += (int64_t)(4 * g->n_seg);
+        g->d_cg = (float *)b;
+        if (seg_weight(g->d_vox, g->d_len64, g->d_ang_seg_off, g->n_ang, g->d_wt, g->d_invL, g->nvox, g->n_seg, g->d_cg,
+                       g->st) != cudaSuccess)
+            return false;
+        g->launches++;
+    }
+    if (!g->cw_ok || g->cw_fold != fold) {
+        cudaError_t e = fold ? coef_stream_fold(g->d_vox, g->d_len64, g->d_chi, g->d_ang_seg_off, g->n_ang, g->d_wt,
+                                                g->d_invL, g->nvox, g->n_seg, g->d_cw4, g->st)
+                             : coef_stream(g->d_vox, g->d_len64, g->d_chi, g->n_seg, g->d_cw4, g->st);
+        if (e != cudaSuccess) return false;
         g->launches++;
         g->cw_ok = true;
+        g->cw_fold = fold;
     }
     return sw_common(g);
 }
@@ -957,6 +966,7 @@ SwMarch sw_march(rt_grid *g, int b, int homog, float *out)
     m.stages = g->sw_stages;
     m.bulk = g->sw_bulk;
     m.lookahead = g->sw_lookahead;
+    m.fold = g->sw_fold && g->sw_stages == 0;
     m.err = g->d_err;
     m.seg_lo = g->h_ang_seg_off[w0];
     m.nbundles = g->h_bnd_off[b + 1] - g->h_bnd_off[b];
@@ -1036,7 +1046,8 @@ int run_fs_J_sw(rt_grid *g, int prec, int homog, const double *S_src, double *J)
     float *b32[3] = {(float *)g->d_segbuf, (float *)g->d_segbuf + g->max_blk_seg,
                      (float *)g->d_segbuf + 2 * g->max_blk_seg};
     double *b64[2] = {(double *)g->d_segbuf, (double *)g->d_segbuf + g->max_blk_seg};
-    const int64_t bps = f64 ? (scatter ? 48 : 44) : (scatter ? 28 : 24);  // streamed bytes per segment
+    const bool fold = !f64 && g->sw_fold && g->sw_stages == 0;  // no separate gather-weight stream
+    const int64_t bps = (f64 ? (scatter ? 48 : 44) : (scatter ? 28 : 24)) - (fold ? 4 : 0);  // streamed bytes per segment
     auto segs = [&](int b) -> int64_t {
         return g->h_ang_seg_off[g->blk_w0[b] + g->blk_nw[b]] - g->h_ang_seg_off[g->blk_w0[b]];
     };
@@ -1130,7 +1141,8 @@ int run_fs_J_sw_streams(rt_grid *g, int prec, int homog, const double *S_src, do
     float *b32[3] = {(float *)g->d_segbuf, (float *)g->d_segbuf + g->max_blk_seg,
                      (float *)g->d_segbuf + 2 * g->max_blk_seg};
     double *b64[2] = {(double *)g->d_segbuf, (double *)g->d_segbuf + g->max_blk_seg};
-    const int64_t bps = f64 ? (scatter ? 48 : 44) : (scatter ? 28 : 24);  // streamed bytes per segment
+    const bool fold = !f64 && g->sw_fold && g->sw_stages == 0;  // no separate gather-weight stream
+    const int64_t bps = (f64 ? (scatter ? 48 : 44) : (scatter ? 28 : 24)) - (fold ? 4 : 0);  // streamed bytes per segment
     auto segs = [&](int b) -> int64_t {
         return g->h_ang_seg_off[g->blk_w0[b] + g->blk_nw[b]] - g->h_ang_seg_off[g->blk_w0[b]];
     };
@@ -1699,6 +1711,11 @@ int rt_tune(rt_grid *g, int knob, int value)
     if (knob == RT_TUNE_MARCH_STREAMS) {
         if (value < 1 || value > 3) return fail(RT_EINVAL, "march streams: 1, 2 or 3");
         g->sw_mstreams = value;
+        return RT_OK;
+    }
+    if (knob == RT_TUNE_FOLD_WEIGHT) {
+        if (value != 0 && value != 1) return fail(RT_EINVAL, "fold weight: 0 or 1");
+        g->sw_fold = value;
         return RT_OK;
     }
     if (knob == RT_TUNE_MARCH_LOOKAHEAD) {

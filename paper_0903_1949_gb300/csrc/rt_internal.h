@@ -195,6 +195,12 @@ cudaError_t march_block_I(const uint32_t *vox, const double *len, const int64_t 
 // FP64 weights of every segment for the chi given, as FP32 (E, alpha, beta + [run start] alpha, gamma).
 cudaError_t coef_stream(const uint32_t *vox, const double *len64, const double *chi, int64_t nseg, float4 *cw,
                         cudaStream_t st);
+// The same weights with the gather weight c_s = w_Omega l_s / L_{Omega v_s}
+// folded in: (E c_s / c_{s-1} (c_s E at a characteristic start), c alpha,
+// c beta, c gamma), so the march yields c_s I_s directly.
+cudaError_t coef_stream_fold(const uint32_t *vox, const double *len64, const double *chi, const int64_t *ang_seg_off,
+                             int n_ang, const double *wt, const double *invL, int nvox, int64_t nseg, float4 *cw,
+                             cudaStream_t st);
 // w_Omega l_s / L_{Omega v_s} of every segment (geometry only).
 cudaError_t seg_weight(const uint32_t *vox, const double *len64, const int64_t *ang_seg_off, int n_ang,
                        const double *wt, const double *invL, int nvox, int64_t nseg, float *cg, cudaStream_t st);
@@ -211,6 +217,7 @@ struct SwMarch {
     int stages;            // 0: register prefetch of one tile; 2..4: shared-memory ring of that many tiles per warp
     int bulk;              // ring filled by bulk copies (1) or by per-lane 16-byte cp.async (0)
     int lookahead;         // register prefetch: S lookups of the next tile issued during this one (1)
+    int fold;              // cw carries c = w l / L (c E_k / c_{k-1}, c alpha, c beta, c gamma); cg unused
     int *err;              // raised when a bounded wait of the staged march gives up
     int64_t seg_lo, nbundles;
     const float *S;        // S per voxel, FP32

@@ -28,6 +28,7 @@ RT_TUNE_NN_KRYLOV = 12
 RT_TUNE_MARCH_STREAMS = 13
 RT_TUNE_GRAPH = 15
 RT_TUNE_GEOM_PREDICT = 16
+RT_TUNE_FOLD_WEIGHT = 17
 
 _STATUS = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONVERGED", 5: "RT_ETIMEOUT",
            6: "RT_EDEVICE"}

@@ -46,9 +46,15 @@ def _iterate(p, interp, knobs, precision=rt.RT_MIXED, angle_block=0):
 
 
 T = rt
+# the unfolded march (the staged rings support only that one); the folded default is checked in FOLDED
 BASE = {T.RT_TUNE_STREAMED_WEIGHTS: 1, T.RT_TUNE_MARCH_COARSEN: 2, T.RT_TUNE_MARCH_CHUNK: 512, T.RT_TUNE_SCATTER: 1,
         T.RT_TUNE_OVERLAP: 1, T.RT_TUNE_MARCH_STAGES: 0, T.RT_TUNE_MARCH_BULK: 0, T.RT_TUNE_MARCH_LOOKAHEAD: 1,
-        T.RT_TUNE_S_BLOCKED: 1, T.RT_TUNE_MARCH_STREAMS: 3, T.RT_TUNE_GRAPH: 1}
+        T.RT_TUNE_S_BLOCKED: 1, T.RT_TUNE_MARCH_STREAMS: 3, T.RT_TUNE_GRAPH: 1, T.RT_TUNE_FOLD_WEIGHT: 0}
+# the library's defaults (gather weight folded into the streamed weights, one segment per lane) and,
+# bit-identical to them, the same arithmetic with the data moved differently
+FOLDED = {**BASE, T.RT_TUNE_FOLD_WEIGHT: 1, T.RT_TUNE_MARCH_COARSEN: 1}
+FOLDED_SAME = [{T.RT_TUNE_SCATTER: 0}, {T.RT_TUNE_OVERLAP: 0}, {T.RT_TUNE_S_BLOCKED: 0}, {T.RT_TUNE_GRAPH: 0},
+               {T.RT_TUNE_MARCH_STREAMS: 1}, {T.RT_TUNE_MARCH_LOOKAHEAD: 0}]
 # same arithmetic in the same order, data moved differently: bit-identical
 SAME = [
     {T.RT_TUNE_S_BLOCKED: 0},
@@ -71,6 +77,9 @@ CLOSE = [
     {T.RT_TUNE_MARCH_CHUNK: 64},
     {T.RT_TUNE_MARCH_CHUNK: 4096, T.RT_TUNE_MARCH_COARSEN: 1, T.RT_TUNE_MARCH_STAGES: 3},
     {T.RT_TUNE_STREAMED_WEIGHTS: 0},
+    {T.RT_TUNE_FOLD_WEIGHT: 1},
+    {T.RT_TUNE_FOLD_WEIGHT: 1, T.RT_TUNE_MARCH_COARSEN: 1},
+    {T.RT_TUNE_FOLD_WEIGHT: 1, T.RT_TUNE_MARCH_STREAMS: 1, T.RT_TUNE_GRAPH: 0},
 ]
 
 
@@ -84,6 +93,11 @@ def test_march_configurations(name):
     for var in CLOSE:
         S = _iterate(p, interp, {**BASE, **var})
         assert np.max(np.abs(S - S0) / np.abs(S0)) < 2e-6, (name, var)
+    S1 = _iterate(p, interp, FOLDED)
+    assert np.array_equal(S1, _iterate(p, interp, {}))  # FOLDED is what the library does by default
+    for var in FOLDED_SAME:
+        S = _iterate(p, interp, {**FOLDED, **var})
+        assert np.array_equal(S, S1), (name, var, float(np.max(np.abs(S - S1) / np.abs(S1))))
     o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"], interp=interp)
     S_o, _, _ = o.solve(p["chi"], p["eps"], p["B"], tol=0.0, max_iter=STEPS, ng=False)
     assert np.max(np.abs(S0 - S_o) / np.abs(S_o)) < 1e-5
@@ -128,7 +142,8 @@ def test_tune_rejects_bad_values():
     for knob, bad in ((T.RT_TUNE_MARCH_CHUNK, 32), (T.RT_TUNE_MARCH_COARSEN, 3), (T.RT_TUNE_MARCH_STAGES, 1),
                       (T.RT_TUNE_MARCH_STAGES, 5), (T.RT_TUNE_MARCH_BULK, 2), (T.RT_TUNE_SCATTER, -1),
                       (T.RT_TUNE_OVERLAP, 7), (T.RT_TUNE_STREAMED_WEIGHTS, 3), (T.RT_TUNE_MARCH_LOOKAHEAD, 2),
-                      (T.RT_TUNE_S_BLOCKED, 2), (T.RT_TUNE_MARCH_STREAMS, 0), (T.RT_TUNE_MARCH_STREAMS, 4), (T.RT_TUNE_GRAPH, 2), (99, 1)):
+                      (T.RT_TUNE_S_BLOCKED, 2), (T.RT_TUNE_MARCH_STREAMS, 0), (T.RT_TUNE_MARCH_STREAMS, 4), (T.RT_TUNE_GRAPH, 2), (T.RT_TUNE_FOLD_WEIGHT, 2),
+                      (99, 1)):
         with pytest.raises(rt.RtError) as ei:
             g.tune(knob, bad)
         assert ei.value.code == rt.RT_EINVAL
