@@ -487,7 +487,8 @@ typedef struct rt_timing {
     int64_t march_segments;   /* crossing segments processed by the timed march launches */
     int64_t kernel_launches;  /* every kernel this library launched on the grid since the reset */
     int64_t march_bytes;      /* DRAM bytes the timed march launches stream by design (per segment:
-                                 8 FP32, 12 FP64, 24 streamed-weight FP32, 28 with RT_TUNE_SCATTER) */
+                                 8 FP32, 12 FP64; streamed-weight FP32 24, or 20 without RT_TUNE_SCATTER,
+                                 4 more without RT_TUNE_FOLD_WEIGHT; streamed-weight FP64 48 / 44) */
 } rt_timing;
 
 int rt_set_timing(rt_grid *g, int enable);
