@@ -233,6 +233,8 @@ def fp64_roofline(flops, src, n_seg, ms_streamed, ms_plain, peak):
     out = {"bound": "fp64-alu", "unit": "TFLOP/s", "peak": peak["flops_per_s"] / 1e12,
            "peak_source": "rt_measure_fp64_rate on this GPU in this run", "flops_source": src}
     for key, ms in (("streamed", ms_streamed), ("plain", ms_plain)):
+        if key + "_flops_per_segment" not in flops:
+            continue
         f = flops[key + "_flops_per_segment"] * n_seg
         out[key] = {"flops_per_segment": flops[key + "_flops_per_segment"], "achieved": f / (ms / 1e3) / 1e12,
                     "frac": f / (ms / 1e3) / peak["flops_per_s"],
