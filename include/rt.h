@@ -223,10 +223,11 @@ int rt_set_precision(rt_grid *g, int precision);
 #define RT_TUNE_GEOM_PREDICT 16
 /* RT_TUNE_FOLD_WEIGHT (default 1): the FP32 streamed-weight march carries the
  * gather weight c = w_Omega l / L of each segment inside its four weights
- * (it marches c_k I_k: E c_k / c_{k-1}, c alpha, c beta, c gamma, all formed in
- * FP64 once per chi), so the per-segment c stream is not read: 24 instead of
- * 28 bytes per segment.  Register-prefetch march only (RT_TUNE_MARCH_STAGES 0);
- * agrees with 0 to FP32 rounding. */
+ * (it marches c_k I_k: E c_k / c_{k-1}, c alpha, c beta, c gamma, formed once per
+ * chi: optical depths and c in FP64, the weights in FP32 on the FP32 pipe), so
+ * the per-segment c stream is not read: 24 instead of 28 bytes per segment.
+ * Register-prefetch march only (RT_TUNE_MARCH_STAGES 0); agrees with 0 (whose
+ * weights are evaluated in FP64 and rounded) to FP32 rounding. */
 #define RT_TUNE_FOLD_WEIGHT 17
 int rt_tune(rt_grid *g, int knob, int value);
 

@@ -724,11 +724,14 @@ __global__ void k_coef_stream(const uint32_t *__restrict__ vox, const double *__
     }
 }
 
-// The FP64 weights with the gather weight folded in: the march then carries
+// The weights with the gather weight folded in: the march then carries
 // c_s I_s, whose recurrence has the weights (E c_s / c_{s-1}, c_s alpha,
 // c_s beta, c_s gamma); at a characteristic start A = 0 and the E slot holds
-// c_s E (the incoming intensity's factor).  c_s = w_Omega l_s / L_{Omega v_s}
-// in FP64 as k_seg_weight forms it.
+// c_s E (the incoming intensity's factor).  The optical depths and c_s =
+// w_Omega l_s / L_{Omega v_s} are formed in FP64 (as k_seg_weight forms c);
+// (E, alpha, beta, gamma) are evaluated in FP32 by the same Coef32 as the
+// marches that evaluate them per segment (on the FP32 pipe: GB300's FP64 pipe
+// is narrow), and the products with c and the ratio c_s / c_{s-1} in FP32.
 __global__ void k_coef_stream_fold(const uint32_t *__restrict__ vox, const double *__restrict__ len64,
                                    const double *__restrict__ chi, const int64_t *__restrict__ ang_seg_off, int n_ang,
                                    const double *__restrict__ wt, const double *__restrict__ invL, int nvox,
@@ -743,19 +746,19 @@ __global__ void k_coef_stream_fold(const uint32_t *__restrict__ vox, const doubl
         }
         const uint32_t w = vox[s];
         const bool para = (w & RTK_PARA) != 0u;
-        const double x = chi[w & RTK_VOXMASK] * len64[s];
-        const double p = para ? chi[vox[s + 1] & RTK_VOXMASK] * len64[s + 1] : 0.0;
-        double E, al, be, ga;
-        Coef64::eval(x, p, para, E, al, be, ga);
+        const float x = (float)(chi[w & RTK_VOXMASK] * len64[s]);
+        const float p = para ? (float)(chi[vox[s + 1] & RTK_VOXMASK] * len64[s + 1]) : 0.0f;
+        float E, al, be, ga;
+        Coef32::eval(x, p, para, E, al, be, ga);
         if (w & (RTK_RAYSTART | RTK_RESTART)) {
             be += al;
-            al = 0.0;
+            al = 0.0f;
         }
         const double *iL = invL + (int64_t)lo * nvox;
-        const double c = wt[lo] * len64[s] * iL[w & RTK_VOXMASK];
-        double A = c * E;
-        if (!(w & RTK_RAYSTART)) A /= wt[lo] * len64[s - 1] * iL[vox[s - 1] & RTK_VOXMASK];
-        cw[s] = make_float4((float)A, (float)(c * al), (float)(c * be), (float)(c * ga));
+        const float c = (float)(wt[lo] * len64[s] * iL[w & RTK_VOXMASK]);
+        float A = c * E;
+        if (!(w & RTK_RAYSTART)) A = __fdividef(A, (float)(wt[lo] * len64[s - 1] * iL[vox[s - 1] & RTK_VOXMASK]));
+        cw[s] = make_float4(A, c * al, c * be, c * ga);
     }
 }
 

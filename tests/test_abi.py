@@ -67,6 +67,16 @@ def test_invalid_descriptions_are_rejected(lib, bad):
     assert len(rt.rt_last_error()) > 0
 
 
+def test_too_many_voxels_rejected(lib):
+    """Voxel ids live in 28 bits of the segment word: 1024 x 512 x 1024 voxels (2^29) is refused
+    before any device work."""
+    e = I.sph_edges(1024, 512, 1024)
+    with pytest.raises(rt.RtError) as ei:
+        rt.rt_grid_create(**_desc(edges=e))
+    assert ei.value.code == rt.RT_EINVAL
+    assert "too many voxels" in str(ei.value)
+
+
 def test_zero_angles_rejected(lib):
     with pytest.raises(rt.RtError) as ei:
         rt.rt_grid_create(**_desc(dirs=np.zeros((0, 3)), weights=np.zeros(0)))
