@@ -287,9 +287,14 @@ int rt_get_history(const rt_grid *g, double *hist, int max, int *n);
  * 3.2.1, with J from the formal solution of Sect. 2) is differentiated
  * implicitly: the adjoint source function lam solves
  *   lam = gS + Lambda^T gJ + Lambda_F^T gF + Lambda^T ((1 - eps) lam)
- * by the same diagonal-Lambda* preconditioned iteration as the forward ALI
- * (run to max|d lam| <= tol max|lam|, at most max_iter sweeps), where
- * Lambda^T is the ray march run backwards along every characteristic; then
+ * by the same preconditioned iteration as the forward ALI (run to
+ * max|d lam| <= tol max|lam|, at most max_iter sweeps), where Lambda^T is the
+ * ray march run backwards along every characteristic: with the diagonal
+ * Lambda* (use_lstar = RT_LSTAR_DIAG) each sweep divides the residual by
+ * 1 - (1-eps) Lambda*; with RT_LSTAR_NN it solves (I - Lambda*_NN^T diag(1-eps)) x
+ * = residual, the transpose of the forward OS step, by the same BiCGSTAB and
+ * Jacobi sweeps (the NN operator is built for the grid's chi if it is not yet),
+ * which keeps the sweep count small at eps << 1; then
  *   dL/dchi = (dJ/dchi)^T (gJ + (1-eps) lam) + (dF/dchi)^T gF,
  *   dL/dB   = eps lam + (dJ/dB)^T (gJ + (1-eps) lam) + (dF/dB)^T gF,
  *   dL/deps = lam (B - J).

@@ -285,6 +285,59 @@ __global__ void k_adj_final(int n, const double *lam, const double *eps, const d
     }
 }
 
+// Transpose of the nearest-neighbour operator with the (1 - eps) factor of its
+// columns moved in: T[q][v] = L27[26 - q][u_q] (1 - eps[u_q]), u_q the voxel at
+// slot q of v (v sits at slot 26 - q of u_q: the offsets are opposite, phi
+// periodic), so that sum_q T[q][v] x[u_q] = ((Lambda*_NN)^T diag(1 - eps) x)_v,
+// the preconditioner of the adjoint iteration in the form the OS-step solver
+// takes (with eps = 0 there).
+__global__ void k_nn_transpose(int nvox, int sph, int n1, int n2, int n3, const double *L27, const double *eps,
+                               double *T)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    const int i0 = v / (n2 * n3), j0 = (v / n3) % n2, k0 = v % n3;
+    for (int q = 0; q < 27; ++q) {
+        int i = i0 + q / 9 - 1, j = j0 + (q / 3) % 3 - 1, k = k0 + q % 3 - 1;
+        if (sph) k = (k < 0) ? k + n3 : ((k >= n3) ? k - n3 : k);
+        else j = (j < 0) ? j + n2 : ((j >= n2) ? j - n2 : j);
+        double t = 0.0;
+        if (i >= 0 && i < n1 && j >= 0 && j < n2 && k >= 0 && k < n3) {
+            const int u = (i * n2 + j) * n3 + k;
+            t = L27[(int64_t)(26 - q) * nvox + u] * (1.0 - eps[u]);
+        }
+        T[(int64_t)q * nvox + v] = t;
+    }
+}
+
+// r = gbar + y - lam  (residual of the adjoint fixed point)
+__global__ void k_adj_res(int n, const double *gbar, const double *y, const double *lam, double *r)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) r[v] = gbar[v] + y[v] - lam[v];
+}
+
+// lam += x; maxd <- max |x|, maxl <- max |lam|
+__global__ void k_adj_add(int n, double *lam, const double *x, unsigned long long *maxd, unsigned long long *maxl)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    double d = 0.0, m = 0.0;
+    if (v < n) {
+        const double ln = lam[v] + x[v];
+        d = fabs(x[v]);
+        m = fabs(ln);
+        lam[v] = ln;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        d = fmax(d, __shfl_down_sync(0xffffffffu, d, o));
+        m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(maxd, (unsigned long long)__double_as_longlong(d));
+        atomicMax(maxl, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
 __global__ void k_axpy(int n, const double *x, double *y)  // y += x
 {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -405,7 +458,22 @@ extern "C" int rt_adjoint(rt_grid *g, const double *dL_dS, const double *dL_dJ, 
     ACK(cudaMemcpyAsync(gbar, gS, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->st));
     k_axpy<<<(n + 255) / 256, 256, 0, g->st>>>(n, y, gbar);
     ACK(cudaMemcpyAsync(lam, gbar, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->st));
-    // adjoint ALI: lam <- lam + (gbar + Lambda^T((1-eps) lam) - lam) / (1 - (1-eps) Lambda*)
+    // adjoint ALI: lam <- lam + M^-1 (gbar + Lambda^T((1-eps) lam) - lam), M = 1 - (1-eps) Lambda*
+    // (diagonal), or M = I - (Lambda*_NN)^T diag(1-eps) solved like the forward OS step
+    const bool nn = g->use_lstar == RT_LSTAR_NN;
+    double *T27 = nullptr, *zeros = nullptr, *r = nullptr;
+    if (nn) {
+        rc = rt_grid_build_nn(g);
+        if (rc != RT_OK) return rc;
+        T27 = tmp.get<double>(27 * (size_t)n);
+        zeros = tmp.get<double>(n);
+        r = tmp.get<double>(n);
+        if (!T27 || !zeros || !r) return afail(RT_ENOMEM, "adjoint NN work arrays could not be allocated");
+        ACK(cudaMemsetAsync(zeros, 0, sizeof(double) * n, g->st));
+        k_nn_transpose<<<(n + 127) / 128, 128, 0, g->st>>>(n, g->coord == RT_SPHERICAL, g->n1, g->n2, g->n3,
+                                                           g->d_L27, g->d_eps, T27);
+        ACK(cudaGetLastError());
+    }
     int it = 0;
     bool conv = false;
     for (it = 1; it <= max_iter; ++it) {
@@ -413,7 +481,33 @@ extern "C" int rt_adjoint(rt_grid *g, const double *dL_dS, const double *dL_dJ, 
         rc = adjoint_pass(g, false, 1, v1, nullptr, tS, nullptr, nullptr, y, nullptr, nullptr);
         if (rc != RT_OK) return rc;
         ACK(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned long long), g->st));
-        k_adj_ali<<<(n + 255) / 256, 256, 0, g->st>>>(n, lam, gbar, y, g->d_eps, g->d_L, mx, mx + 1);
+        if (nn) {
+            k_adj_res<<<(n + 255) / 256, 256, 0, g->st>>>(n, gbar, y, lam, r);
+            NnOs o{};
+            o.nvox = n;
+            o.sph = g->coord == RT_SPHERICAL;
+            o.n1 = g->n1;
+            o.n2 = g->n2;
+            o.n3 = g->n3;
+            o.L27 = T27;
+            o.eps = zeros;
+            o.y = r;
+            o.work = g->d_nnx;
+            o.mx = g->d_nnmx;
+            o.jtol = g->nn_jtol;
+            o.jmax = g->nn_jmax;
+            o.krylov = g->nn_krylov;
+            o.kmax = 1000;
+            double *x = nullptr;
+            int kits = 0, sweeps = 0, status = 0;
+            ACK(nn_os_solve(o, g->st, &x, &kits, &sweeps, &status));
+            if (status == 2) return afail(RT_EDEVICE, "adjoint NN OS step diverged");
+            if (status == 1) return afail(RT_ENOTCONVERGED, "adjoint NN OS step did not converge");
+            ACK(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned long long), g->st));
+            k_adj_add<<<(n + 255) / 256, 256, 0, g->st>>>(n, lam, x, mx, mx + 1);
+        } else {
+            k_adj_ali<<<(n + 255) / 256, 256, 0, g->st>>>(n, lam, gbar, y, g->d_eps, g->d_L, mx, mx + 1);
+        }
         unsigned long long h[2];
         ACK(cudaMemcpyAsync(h, mx, sizeof(h), cudaMemcpyDeviceToHost, g->st));
         ACK(cudaStreamSynchronize(g->st));

@@ -140,6 +140,10 @@ struct rt_grid {
 int rt_grid_member_fs(rt_grid *g, const float2 *cs, const float *B32, const uint32_t *pbits, double *J, double *L,
                       double *Fc, cudaStream_t st);
 
+// The grid's exact nearest-neighbour Lambda* (d_L27) for its current chi, built
+// on first use after rt_set_opacity; returns an RT_ status.
+int rt_grid_build_nn(rt_grid *g);
+
 // FP64 J of another opacity field on this grid's geometry (a batch member):
 // (chi, S) packed in cs64, B, parabola choices in pbits.  Runs on st.
 int rt_grid_member_fs64J(rt_grid *g, const double2 *cs64, const double *B64, const uint32_t *pbits, double *J,

@@ -1481,6 +1481,8 @@ int rt_grid_member_fs(rt_grid *g, const float2 *cs, const float *B32, const uint
     return RT_OK;
 }
 
+int rt_grid_build_nn(rt_grid *g) { return build_nn(g); }
+
 int rt_grid_member_fs64J(rt_grid *g, const double2 *cs64, const double *B64, const uint32_t *pbits, double *J,
                          cudaStream_t st)
 {

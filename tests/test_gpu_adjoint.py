@@ -51,14 +51,21 @@ def _grid(p, interp):
                    precision=rt.RT_FP64, ng=True)
 
 
-def _converge(g, max_iter=3000):
-    """ALI steps until max rel dS reaches the FP64 rounding floor."""
-    rel = 1.0
-    for _ in range(max_iter):
+def _converge(g, max_iter=3000, floor=1e-14):
+    """ALI steps until max rel dS reaches the FP64 rounding floor.  The ALI amplifies
+    the rounding of J by up to (1 - eps) / (1 - (1 - eps) Lambda) ~ 1 / eps in thick
+    media, so at small eps the floor is higher: there the steps go on until max rel dS
+    has not reached a new low for 20 steps (it then fluctuates at the floor)."""
+    rel, best, best_it = 1.0, np.inf, 0
+    for it in range(max_iter):
         rel = g.ali_step()
-        if rel < 1e-15:
+        if rel < 0.1 * floor:
             break
-    assert rel < 1e-14, rel
+        if rel < best:
+            best, best_it = rel, it
+        elif best < floor and it - best_it >= 20:
+            break
+    assert min(rel, best) < floor, rel
 
 
 def _loss_gpu(g, w, kinds, chi, eps, B):
@@ -86,12 +93,12 @@ def _adjoint(g, w, kinds, p):
     return dict(chi=dchi, eps=deps, B=dB)
 
 
-def _fd_check(loss, p, grads, fields, voxels):
+def _fd_check(loss, p, grads, fields, voxels, h_rel=None):
     for f in fields:
         gmax = np.max(np.abs(grads[f]))
         for v in voxels:
             args = {k: p[k].copy() for k in ("chi", "eps", "B")}
-            h = H_REL * args[f][v]
+            h = (h_rel or {}).get(f, H_REL) * args[f][v]
             args[f][v] += h
             Lp = loss(args["chi"], args["eps"], args["B"])
             args[f][v] -= 2.0 * h
@@ -161,4 +168,71 @@ def test_adjoint_reports_non_convergence_and_bad_arguments():
     with pytest.raises(rt.RtError) as ei:
         g.adjoint(w["S"], tol=0.0)
     assert ei.value.code == rt.RT_EINVAL
+    g.close()
+
+
+def _nn_case(eps_scale, chi_scale, seed):
+    rng = np.random.default_rng(seed)
+    p = tiny_problem(I.SPHERICAL, (7, 5, 9), 4, 4, I.CORE_B, eps=1.0, seed=seed)
+    n = p["nvox"]
+    p["chi"] = p["chi"] * chi_scale
+    p["eps"] = eps_scale * (0.5 + rng.uniform(size=n))
+    p["B"] = 1.0 + 0.5 * rng.uniform(size=n)
+    w = dict(S=rng.standard_normal(n), J=rng.standard_normal(n), F=rng.standard_normal((n, 3)))
+    return p, w
+
+
+def _nn_grid(p, lstar):
+    return rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=rt.RT_FP64,
+                   ng=True, use_lstar=lstar)
+
+
+def test_nn_preconditioned_adjoint_equals_diagonal_one_in_fewer_sweeps():
+    """Where the diagonal-Lambda* adjoint iteration converges, the NN-preconditioned one
+    reaches the same adjoint (the fixed point does not depend on the preconditioner)."""
+    p, w = _nn_case(0.05, 3.0, 31)
+    out = {}
+    for lstar in (rt.RT_LSTAR_DIAG, rt.RT_LSTAR_NN):
+        g = _nn_grid(p, lstar)
+        g.set_opacity(p["chi"], p["eps"], p["B"])
+        g.set_S(p["B"])
+        _converge(g)
+        dchi, deps, dB, it, ok = g.adjoint(w["S"], w["J"], w["F"].reshape(-1), tol=1e-14, max_iter=20000)
+        assert ok, lstar
+        out[lstar] = (dict(chi=dchi, eps=deps, B=dB), it)
+        g.close()
+    (gd, itd), (gn, itn) = out[rt.RT_LSTAR_DIAG], out[rt.RT_LSTAR_NN]
+    print("adjoint sweeps: diagonal %d, nearest-neighbour %d" % (itd, itn))
+    assert itn < itd
+    for f in ("chi", "eps", "B"):
+        assert np.max(np.abs(gn[f] - gd[f])) <= 1e-10 * np.max(np.abs(gd[f])), f
+
+
+def test_nn_preconditioned_adjoint_matches_finite_differences_at_small_eps():
+    """eps ~ 1e-4 in an optically thick tiny grid, where the diagonal-Lambda* iteration is
+    impractically slow: the NN-preconditioned adjoint against central differences of
+    NN-converged FP64 solves, on seeded voxels of chi, eps and B."""
+    p, w = _nn_case(1e-4, 30.0, 32)
+    g = _nn_grid(p, rt.RT_LSTAR_NN)
+    g.set_opacity(p["chi"], p["eps"], p["B"])
+    g.set_S(p["B"])
+    _converge(g, max_iter=1000, floor=1e-12)
+    # the adjoint iterate carries the same ~1/eps amplification of FP64 rounding as S: 1e-11
+    dchi, deps, dB, it, ok = g.adjoint(w["S"], w["J"], w["F"].reshape(-1), tol=1e-11, max_iter=2000)
+    assert ok and it < 500, it
+    print("NN adjoint sweeps at eps ~ 1e-4: %d" % it)
+    grads = dict(chi=dchi, eps=deps, B=dB)
+    voxels = np.random.default_rng(33).choice(p["nvox"], 6, replace=False)
+    def loss(c, e, b):
+        g.set_opacity(c, e, b)
+        g.set_S(b)
+        _converge(g, max_iter=1000, floor=1e-12)
+        g.formal_solution(rt.RT_FP64)
+        return w["S"] @ g.S() + w["J"] @ g.J() + np.sum(w["F"] * g.flux())
+
+    # the converged loss carries ~1e-13 of FP64 noise (see _converge), which a central difference
+    # divides by 2h: a step of 1e-6 eps ~ 1e-10 would make that a 1e-2 error, so eps is stepped by 1e-4
+    # of itself and chi by 1e-5 (truncation ~h^2 stays far below); L is linear in B (S is), so a
+    # step of 1e-2 B is exact there
+    _fd_check(loss, p, grads, ("chi", "eps", "B"), voxels, h_rel={"chi": 1e-5, "eps": 1e-4, "B": 1e-2})
     g.close()
