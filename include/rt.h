@@ -199,7 +199,11 @@ int rt_set_precision(rt_grid *g, int precision);
  * first runs BiCGSTAB on the Jacobi-preconditioned system until its
  * preconditioned residual (the change a Jacobi sweep would make) is below the
  * RT_TUNE_NN_JTOL bound, then Jacobi sweeps confirm that bound; 0 runs the
- * Jacobi sweeps alone.  Both stop on the same criterion. */
+ * Jacobi sweeps alone.  Both stop on the same criterion, tested after every
+ * iteration and sweep.  The whole OS step is one cooperative launch whose
+ * blocks meet at grid barriers; a barrier wait that gives up after a second
+ * makes the calling rt_ali_step / rt_solve / rt_adjoint return RT_ETIMEOUT
+ * with S not updated by that step. */
 #define RT_TUNE_NN_KRYLOV 12
 /* RT_TUNE_MARCH_STREAMS (default 3): with RT_TUNE_OVERLAP, the marches of
  * consecutive angle blocks alternate between 1, 2 or 3 streams (the FP64 march
@@ -229,6 +233,12 @@ int rt_set_precision(rt_grid *g, int precision);
  * Register-prefetch march only (RT_TUNE_MARCH_STAGES 0); agrees with 0 (whose
  * weights are evaluated in FP64 and rounded) to FP32 rounding. */
 #define RT_TUNE_FOLD_WEIGHT 17
+/* RT_TUNE_NN_TEST_STALL (test hook, default 0): 1 makes one block of the next
+ * nearest-neighbour OS step leave out its first barrier arrival, so every
+ * bounded wait of that launch runs out: the call returns RT_ETIMEOUT, S is
+ * not updated and the knob is 0 again.  It tests the bounded waits without a
+ * device fault. */
+#define RT_TUNE_NN_TEST_STALL 18
 int rt_tune(rt_grid *g, int knob, int value);
 
 /* Formal solution from the current S with the grid's precision: J, the
@@ -495,6 +505,10 @@ typedef struct rt_timing {
     int64_t march_bytes;      /* DRAM bytes the timed march launches stream by design (per segment:
                                  8 FP32, 12 FP64; streamed-weight FP32 24, or 20 without RT_TUNE_SCATTER,
                                  4 more without RT_TUNE_FOLD_WEIGHT; streamed-weight FP64 48 / 44) */
+    double os_ms;             /* summed event time of the nearest-neighbour OS-step solves (timing 1 only) */
+    int64_t os_solves;        /* OS-step solves since the reset (counted at any timing setting) */
+    int64_t os_krylov_its;    /* their BiCGSTAB iterations */
+    int64_t os_sweeps;        /* their Jacobi sweeps */
 } rt_timing;
 
 int rt_set_timing(rt_grid *g, int enable);

@@ -493,7 +493,6 @@ extern "C" int rt_adjoint(rt_grid *g, const double *dL_dS, const double *dL_dJ, 
             o.eps = zeros;
             o.y = r;
             o.work = g->d_nnx;
-            o.mx = g->d_nnmx;
             o.jtol = g->nn_jtol;
             o.jmax = g->nn_jmax;
             o.krylov = g->nn_krylov;
@@ -501,6 +500,8 @@ extern "C" int rt_adjoint(rt_grid *g, const double *dL_dS, const double *dL_dJ, 
             double *x = nullptr;
             int kits = 0, sweeps = 0, status = 0;
             ACK(nn_os_solve(o, g->st, &x, &kits, &sweeps, &status));
+            ++g->launches;
+            if (status == 3) return afail(RT_ETIMEOUT, "adjoint NN OS step: a grid-barrier wait gave up");
             if (status == 2) return afail(RT_EDEVICE, "adjoint NN OS step diverged");
             if (status == 1) return afail(RT_ENOTCONVERGED, "adjoint NN OS step did not converge");
             ACK(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned long long), g->st));

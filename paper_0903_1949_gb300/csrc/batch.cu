@@ -281,7 +281,6 @@ struct rt_batch {
     bool line_ready = false;
     int lstar = RT_LSTAR_DIAG;  // line operator: diagonal or nearest-neighbour
     double *Lbar27 = nullptr, *L27k = nullptr, *nnx = nullptr, *nny = nullptr;
-    unsigned long long *nnmx = nullptr;
     int nn_sweeps = 0;
     int ng = 0;  // Ng extrapolation of S_l
     double *H = nullptr, *ng_part = nullptr, *ng_coef = nullptr;
@@ -461,7 +460,6 @@ int line_nn_os(rt_batch *b)
     o.eps = b->eps_l;
     o.y = b->nny;
     o.work = b->nnx;
-    o.mx = b->nnmx;
     o.jtol = 1e-14;
     o.jmax = 100000;
     o.krylov = 1;
@@ -469,6 +467,7 @@ int line_nn_os(rt_batch *b)
     double *x = nullptr;
     int its = 0, sweeps = 0, status = 0;
     BCK(nn_os_solve(o, b->st, &x, &its, &sweeps, &status));
+    if (status == 3) return bfail(RT_ETIMEOUT, "line NN OS step: a grid-barrier wait gave up");
     if (status == 2) return bfail(RT_EDEVICE, "line NN OS step diverged");
     if (status == 1) return bfail(RT_ENOTCONVERGED, "line NN OS step: no convergence in 100000 sweeps");
     b->nn_sweeps = sweeps;
@@ -926,8 +925,7 @@ int rt_line_create(rt_batch **out, rt_grid *g, int n_freq, const double *phi, co
         (rc = balloc(b, &b->tmp, n)) != RT_OK ||
         (use_lstar == RT_LSTAR_NN &&
          ((rc = balloc(b, &b->Lbar27, 27 * (size_t)n)) != RT_OK || (rc = balloc(b, &b->L27k, 27 * (size_t)n)) != RT_OK ||
-          (rc = balloc(b, &b->nnx, (size_t)nn_os_work_elems(n))) != RT_OK || (rc = balloc(b, &b->nny, n)) != RT_OK ||
-          (rc = balloc(b, &b->nnmx, 2)) != RT_OK)) ||
+          (rc = balloc(b, &b->nnx, (size_t)nn_os_work_elems(n))) != RT_OK || (rc = balloc(b, &b->nny, n)) != RT_OK)) ||
         (ng && ((rc = balloc(b, &b->H, 4 * (size_t)n)) != RT_OK ||
                 (rc = balloc(b, &b->ng_part, ng_partial_elems(n))) != RT_OK ||
                 (rc = balloc(b, &b->ng_coef, 4)) != RT_OK))) {

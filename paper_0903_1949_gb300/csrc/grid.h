@@ -69,7 +69,7 @@ struct rt_grid {
     int64_t timing_count = 0;
     std::vector<cudaEvent_t> ev;      // event pool, two per timed launch
     size_t ev_used = 0;
-    std::vector<int> ev_kind;         // 0 march, 1 gather
+    std::vector<int> ev_kind;         // 0 march, 1 gather, 2 NN OS-step solve
     std::vector<int64_t> ev_segs;
     int64_t launches = 0;
     int march_chunk = 512;  // segments per warp bundle (RT_TUNE_MARCH_CHUNK)
@@ -130,6 +130,8 @@ struct rt_grid {
     double nn_jtol = 1e-14;
     int nn_jmax = 100000;
     int nn_krylov = 1, nn_krylov_its = 0;  // BiCGSTAB before the Jacobi sweeps of the OS step
+    int nn_stall = 0;                   // RT_TUNE_NN_TEST_STALL
+    int64_t os_solves = 0, os_its = 0, os_sweeps = 0;  // OS-step counters since the timing reset
     std::vector<int64_t> h_bnd_off;
     int bnd_chunk = 0;
 };

@@ -10,7 +10,7 @@
 // least recently touched makes room when the window is full) and emits, per segment,
 // c_s d_u with u's neighbour slot of v_s (c_s = w_Omega l_s / L_{Omega v_s});
 // one thread per voxel sums them over its ownership list in list order.  The
-// OS step (I - (1-eps) L*) x = y is solved by Jacobi sweeps.  All FP64.
+// OS step (I - (1-eps) L*) x = y is solved in nn_krylov.cu.  All FP64.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -190,56 +190,6 @@ __global__ void k_nn_rows(int nvox, const double *planes, double *rows)
     }
 }
 
-// max over the block, then one atomic per block (bits of non-negative doubles)
-__device__ __forceinline__ void block_max_to(double x, unsigned long long *dst)
-{
-    __shared__ double red[32];
-    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
-    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    __syncthreads();  // red may hold the previous call's values
-    if ((threadIdx.x & 31) == 0) red[w] = x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double m = red[0];
-        for (int q = 1; q < nw; ++q) m = fmax(m, red[q]);
-        atomicMax(dst, (unsigned long long)__double_as_longlong(m));
-    }
-}
-
-// One Jacobi sweep of (I - (1-eps) L*) x = y: xo = (y + (1-eps) sum_{q != 13} L*_q xi[u_q]) / (1 - (1-eps) L*_13).
-// TRACK: also mx[0] <- max |xo - xi|, mx[1] <- max |xo| (the sweep that a convergence check reads).
-template <bool TRACK>
-__global__ void __launch_bounds__(256) k_nn_jacobi(int nvox, int sph, int n1, int n2, int n3, const double *L27,
-                                                   const double *eps, const double *y, const double *xi, double *xo,
-                                                   unsigned long long *mx)
-{
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    double dd = 0.0, xa = 0.0;
-    if (v < nvox) {
-        const Ijk c = decode(v, n2, n3);
-        const double *L = L27 + v;  // slot q at L[q * nvox]
-        double off = 0.0;
-#pragma unroll
-        for (int q = 0; q < 27; ++q) {
-            if (q == 13) continue;
-            int i = c.i + q / 9 - 1, j = c.j + (q / 3) % 3 - 1, k = c.k + q % 3 - 1;
-            if (sph) k = (k < 0) ? k + n3 : ((k >= n3) ? k - n3 : k);  // phi periodic (offsets are +-1)
-            else j = (j < 0) ? j + n2 : ((j >= n2) ? j - n2 : j);
-            if (i < 0 || i >= n1 || j < 0 || j >= n2 || k < 0 || k >= n3) continue;
-            off += L[(int64_t)q * nvox] * xi[(i * n2 + j) * n3 + k];
-        }
-        const double e = 1.0 - eps[v];
-        const double xn = (y[v] + e * off) / (1.0 - e * L[13 * (int64_t)nvox]);
-        dd = fabs(xn - xi[v]);
-        xa = fabs(xn);
-        xo[v] = xn;
-    }
-    if (TRACK) {
-        block_max_to(dd, mx);
-        block_max_to(xa, mx + 1);
-    }
-}
-
 // y = (1-eps) J + eps B - S   (ALI step, and the residual of the refinement)
 __global__ void k_nn_rhs(int n, const double *S, const double *J, const double *eps, const double *B, double *y)
 {
@@ -301,14 +251,6 @@ cudaError_t nn_diag(int nvox, const double *L27, double *L, cudaStream_t st)
 cudaError_t nn_rows(int nvox, const double *planes, double *rows, cudaStream_t st)
 {
     k_nn_rows<<<152 * 8, 256, 0, st>>>(nvox, planes, rows);
-    return cudaGetLastError();
-}
-
-cudaError_t nn_jacobi(int nvox, int sph, int n1, int n2, int n3, const double *L27, const double *eps, const double *y,
-                      const double *xi, double *xo, unsigned long long *mx, cudaStream_t st)
-{
-    if (mx) k_nn_jacobi<true><<<nb(nvox, 256), 256, 0, st>>>(nvox, sph, n1, n2, n3, L27, eps, y, xi, xo, mx);
-    else k_nn_jacobi<false><<<nb(nvox, 256), 256, 0, st>>>(nvox, sph, n1, n2, n3, L27, eps, y, xi, xo, nullptr);
     return cudaGetLastError();
 }
 

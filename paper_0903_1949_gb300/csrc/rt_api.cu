@@ -1375,8 +1375,8 @@ int build_nn(rt_grid *g)
 
 // x = (I - (1-eps) L*_NN)^-1 y: BiCGSTAB on the Jacobi-preconditioned system
 // (unless RT_TUNE_NN_KRYLOV is 0), then Jacobi sweeps until one changes x by
-// <= nn_jtol max |x| (checked on the last sweep of each batch); returns the
-// result's buffer in *x_out.
+// <= nn_jtol max |x|, in one cooperative launch; returns the result's buffer
+// in *x_out.
 int nn_solve(rt_grid *g, const double *y, double **x_out)
 {
     NnOs o{};
@@ -1389,16 +1389,23 @@ int nn_solve(rt_grid *g, const double *y, double **x_out)
     o.eps = g->d_eps;
     o.y = y;
     o.work = g->d_nnx;
-    o.mx = g->d_nnmx;
     o.jtol = g->nn_jtol;
     o.jmax = g->nn_jmax;
     o.krylov = g->nn_krylov;
     o.kmax = 1000;
+    o.stall = g->nn_stall;
+    g->nn_stall = 0;
     int its = 0, sweeps = 0, status = 0;
+    const int t = tstart(g, 2);
     CK(nn_os_solve(o, g->st, x_out, &its, &sweeps, &status));
-    g->launches += 8 * its + sweeps;
+    tstop(g, t, 2, 0);
+    g->launches += 1;
     g->nn_sweeps = sweeps;
     g->nn_krylov_its = its;
+    g->os_solves += 1;
+    g->os_its += its;
+    g->os_sweeps += sweeps;
+    if (status == 3) return fail(RT_ETIMEOUT, "NN Lambda* OS step: a grid-barrier wait gave up; S not updated by this step");
     if (status == 2) return fail(RT_EDEVICE, "NN Lambda* OS step diverged");
     if (status == 1) return fail(RT_ENOTCONVERGED, "NN Lambda* OS step: no convergence in %d sweeps", sweeps);
     return RT_OK;
@@ -1725,6 +1732,11 @@ int rt_tune(rt_grid *g, int knob, int value)
         g->sw_lookahead = value;
         return RT_OK;
     }
+    if (knob == RT_TUNE_NN_TEST_STALL) {
+        if (value != 0 && value != 1) return fail(RT_EINVAL, "NN OS-step stall test: 0 or 1");
+        g->nn_stall = value;
+        return RT_OK;
+    }
     return fail(RT_EINVAL, "unknown tuning knob %d", knob);
 }
 
@@ -1989,6 +2001,7 @@ int rt_set_timing(rt_grid *g, int enable)
         g->ev_segs.clear();
         g->ev_bytes.clear();
         g->launches = 0;
+        g->os_solves = g->os_its = g->os_sweeps = 0;
         g->timing_count = 0;
         g->timing_every = enable;
     }
@@ -2010,12 +2023,17 @@ int rt_get_timing(rt_grid *g, rt_timing *t)
             t->march_launches++;
             t->march_segments += g->ev_segs[q];
             t->march_bytes += g->ev_bytes[q];
-        } else {
+        } else if (g->ev_kind[q] == 1) {
             t->gather_ms += ms;
             t->gather_launches++;
+        } else {
+            t->os_ms += ms;
         }
     }
     t->kernel_launches = g->launches;
+    t->os_solves = g->os_solves;
+    t->os_krylov_its = g->os_its;
+    t->os_sweeps = g->os_sweeps;
     return RT_OK;
 }
 

@@ -334,25 +334,24 @@ cudaError_t nn_diag(int nvox, const double *L27, double *L, cudaStream_t st);
 // Operator-splitting step (I - (1-eps) L*) x = y of the nearest-neighbour
 // Lambda* (slot planes): BiCGSTAB on the Jacobi-preconditioned system (krylov
 // != 0, at most kmax iterations) to a preconditioned residual <= jtol max |x|,
-// then Jacobi sweeps until one changes x by <= jtol max |x| (at most jmax).
-// work: nn_os_work_elems(nvox) doubles; mx: 2 words.  *status: 0 converged,
-// 1 not within jmax sweeps, 2 non-finite; *x_out: the solution's buffer (in work).
+// then Jacobi sweeps until one changes x by <= jtol max |x| (at most jmax), all
+// in one cooperative launch; synchronises st.  work: nn_os_work_elems(nvox)
+// doubles.  *status: 0 converged, 1 not within jmax sweeps, 2 non-finite, 3 a
+// grid-barrier wait gave up (x invalid); *x_out: the solution's buffer (in work).
+// stall != 0 (test hook): one block skips its first barrier arrival, so every
+// wait of the launch runs out and the status is 3.
 struct NnOs {
     int nvox, sph, n1, n2, n3;
     const double *L27, *eps, *y;
     double *work;
-    unsigned long long *mx;
     double jtol;
     int jmax, krylov, kmax;
+    int stall;
 };
 int64_t nn_os_work_elems(int nvox);
 cudaError_t nn_os_solve(const NnOs &o, cudaStream_t st, double **x_out, int *krylov_its, int *sweeps, int *status);
 // The operator's 27 slot planes (L27[q nvox + v]) as rows: rows[27 v + q].
 cudaError_t nn_rows(int nvox, const double *planes, double *rows, cudaStream_t st);
-// One Jacobi sweep of (I - (1-eps) L*) x = y; with mx (may be NULL): mx[0] <- max |xo - xi|,
-// mx[1] <- max |xo| (atomic max of the bits of non-negative doubles)
-cudaError_t nn_jacobi(int nvox, int sph, int n1, int n2, int n3, const double *L27, const double *eps, const double *y,
-                      const double *xi, double *xo, unsigned long long *mx, cudaStream_t st);
 cudaError_t nn_rhs(int n, const double *S, const double *J, const double *eps, const double *B, double *y,
                    cudaStream_t st);
 cudaError_t nn_rhs_corr(int n, const double *d, const double *Jd, const double *r, const double *eps, double *y,

@@ -29,6 +29,7 @@ RT_TUNE_MARCH_STREAMS = 13
 RT_TUNE_GRAPH = 15
 RT_TUNE_GEOM_PREDICT = 16
 RT_TUNE_FOLD_WEIGHT = 17
+RT_TUNE_NN_TEST_STALL = 18
 
 _STATUS = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONVERGED", 5: "RT_ETIMEOUT",
            6: "RT_EDEVICE"}
@@ -60,7 +61,8 @@ class rt_info(ctypes.Structure):
 class rt_timing(ctypes.Structure):
     _fields_ = [("march_ms", ctypes.c_double), ("gather_ms", ctypes.c_double), ("march_launches", ctypes.c_int64),
                 ("gather_launches", ctypes.c_int64), ("march_segments", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64), ("march_bytes", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("march_bytes", ctypes.c_int64), ("os_ms", ctypes.c_double),
+                ("os_solves", ctypes.c_int64), ("os_krylov_its", ctypes.c_int64), ("os_sweeps", ctypes.c_int64)]
 
 
 _lib = None

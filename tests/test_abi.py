@@ -110,3 +110,31 @@ def test_struct_layout_matches_header(lib):
     # rt_grid_desc / rt_info sizes as laid out by the C compiler for x86-64 and aarch64
     assert ctypes.sizeof(rt.rt_grid_desc) == 112
     assert ctypes.sizeof(rt.rt_info) == 80
+    assert ctypes.sizeof(rt.rt_timing) == 88
+
+
+def test_struct_offsets_match_the_c_compiler(tmp_path):
+    """Every field offset and struct size of the binding's ctypes structs equals
+    what gcc lays out from include/rt.h on this machine."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    structs = [rt.rt_grid_desc, rt.rt_info, rt.rt_timing]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "rt.h"', "int main(void) {"]
+    for st in structs:
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (st.__name__, st.__name__))
+        for name, _ in st._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (st.__name__, name, st.__name__, name))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for st in structs:
+        assert int(got[st.__name__]) == ctypes.sizeof(st), st.__name__
+        for name, _ in st._fields_:
+            assert int(got["%s.%s" % (st.__name__, name)]) == getattr(st, name).offset, (st.__name__, name)

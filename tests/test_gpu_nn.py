@@ -202,3 +202,43 @@ def test_inexact_os_step_keeps_the_fixed_point():
             g.tune(rt.RT_TUNE_NN_JTOL, 16)
         finally:
             g.close()
+
+
+def test_os_step_is_one_launch_and_its_bounded_wait_reports_a_timeout():
+    """The OS step runs as one cooperative launch (rt_get_timing counts its
+    solves, BiCGSTAB iterations and sweeps).  With the stall test hook one
+    block leaves out a barrier arrival: every wait of that launch gives up after
+    its bound, the step returns RT_ETIMEOUT without touching S, and the grid
+    then steps on exactly as one that never stalled."""
+    p, interp = CASES["sph17"]()
+    eps = np.full(p["nvox"], 1e-4)
+
+    def grid():
+        g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=rt.RT_FP64,
+                    use_lstar=rt.RT_LSTAR_NN, ng=False)
+        g.set_opacity(p["chi"], eps, p["B"])
+        return g
+
+    g = grid()
+    g.set_timing(1)
+    g.ali_step()
+    t = g.timing()
+    print("one OS step: %d BiCGSTAB iterations, %d Jacobi sweeps, %.3f ms"
+          % (t["os_krylov_its"], t["os_sweeps"], t["os_ms"]))
+    assert t["os_solves"] == 1 and t["os_krylov_its"] > 0 and t["os_sweeps"] >= 1 and t["os_ms"] > 0.0
+    g.set_timing(0)
+    S1 = g.S()
+    g.tune(rt.RT_TUNE_NN_TEST_STALL, 1)
+    with pytest.raises(rt.RtError) as ei:
+        g.ali_step()
+    assert ei.value.code == rt.RT_ETIMEOUT, str(ei.value)
+    assert np.array_equal(g.S(), S1)
+    g.ali_step()  # the hook cleared itself
+    S2 = g.S()
+    g.close()
+    h = grid()
+    h.ali_step()
+    assert np.array_equal(h.S(), S1)  # deterministic
+    h.ali_step()
+    assert np.array_equal(h.S(), S2)
+    h.close()
