@@ -180,7 +180,9 @@ int rt_set_precision(rt_grid *g, int precision);
 /* RT_TUNE_NN_JTOL: the OS step of the nearest-neighbour Lambda* stops its
  * Jacobi sweeps when a sweep changes dS by at most 10^-value max |dS|,
  * value 1..15 (default 14: the step solved to FP64 rounding).  A looser step
- * changes the iterates, not the fixed point. */
+ * changes the iterates, not the fixed point.  Inside the FP32 correction
+ * sweeps of an RT_MIXED rt_solve, whose right-hand sides carry FP32 rounding,
+ * the bound is max(10^-value, 1e-8); its FP64 residual steps use 10^-value. */
 #define RT_TUNE_NN_JTOL 8
 /* RT_TUNE_MARCH64_COARSEN: segments per lane of the FP64 streamed-weight
  * march, 1 or 2 (default). */

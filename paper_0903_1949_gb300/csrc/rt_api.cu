@@ -1375,9 +1375,11 @@ int build_nn(rt_grid *g)
 
 // x = (I - (1-eps) L*_NN)^-1 y: BiCGSTAB on the Jacobi-preconditioned system
 // (unless RT_TUNE_NN_KRYLOV is 0), then Jacobi sweeps until one changes x by
-// <= nn_jtol max |x|, in one cooperative launch; returns the result's buffer
-// in *x_out.
-int nn_solve(rt_grid *g, const double *y, double **x_out)
+// <= jtol max |x| (jtol <= 0: the grid's nn_jtol), in one cooperative launch;
+// returns the result's buffer in *x_out.
+constexpr double kCorrOsJtol = 1e-8;  // OS-step bound inside the FP32 correction sweeps of rt_solve
+
+int nn_solve(rt_grid *g, const double *y, double **x_out, double jtol = 0.0)
 {
     NnOs o{};
     o.nvox = g->nvox;
@@ -1389,7 +1391,7 @@ int nn_solve(rt_grid *g, const double *y, double **x_out)
     o.eps = g->d_eps;
     o.y = y;
     o.work = g->d_nnx;
-    o.jtol = g->nn_jtol;
+    o.jtol = jtol > 0.0 ? jtol : g->nn_jtol;
     o.jmax = g->nn_jmax;
     o.krylov = g->nn_krylov;
     o.kmax = 1000;
@@ -1835,8 +1837,10 @@ int rt_solve(rt_grid *g, double tol, int max_iter, int *iters)
             double *slot = g->ng ? ng_append_slot(g) : nullptr;
             if (g->use_lstar == RT_LSTAR_NN) {
                 CK(nn_rhs_corr(n, g->d_delta, g->d_Jd, g->d_r, g->d_eps, g->d_nny, g->st));
+                // the right-hand side carries the FP32 rounding of the correction's
+                // formal solution (~1e-7 of it): its OS step needs no more than 1e-8
                 double *x = nullptr;
-                RCK(nn_solve(g, g->d_nny, &x));
+                RCK(nn_solve(g, g->d_nny, &x, std::max(g->nn_jtol, kCorrOsJtol)));
                 CK(cudaMemsetAsync(g->d_maxrel, 0, sizeof(unsigned long long), g->st));
                 CK(nn_apply(n, g->d_delta, x, g->d_S, slot, g->d_maxrel, g->st));
             } else {
