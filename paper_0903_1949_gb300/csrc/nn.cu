@@ -135,36 +135,84 @@ __global__ void __launch_bounds__(128) k_nn_walk(NnWalk a)
         const double c = wq * a.len64[s] * invLq[v];
         const Ijk cv = decode(v, a.n2, a.n3);
         const int64_t o = (s - a.seg_lo) * NNW;
+        // the segment's 16 slots as one 16-byte store, its 16 values as eight
+        unsigned sw[4] = {0u, 0u, 0u, 0u};
+        double2 *vo = reinterpret_cast<double2 *>(a.val + o);
 #pragma unroll
-        for (int e = 0; e < NNW; ++e) {
-            const int q = W.vox[e] >= 0 ? slot_of(cv, W.ijk[e], a.sph, a.n2, a.n3) : -1;
-            a.slot[o + e] = (int8_t)q;
-            a.val[o + e] = q >= 0 ? c * W.d[e] : 0.0;
+        for (int e = 0; e < NNW; e += 2) {
+            const int q0 = W.vox[e] >= 0 ? slot_of(cv, W.ijk[e], a.sph, a.n2, a.n3) : -1;
+            const int q1 = W.vox[e + 1] >= 0 ? slot_of(cv, W.ijk[e + 1], a.sph, a.n2, a.n3) : -1;
+            sw[e >> 2] |= ((unsigned)(uint8_t)(int8_t)q0) << (8 * (e & 3));
+            sw[(e + 1) >> 2] |= ((unsigned)(uint8_t)(int8_t)q1) << (8 * ((e + 1) & 3));
+            vo[e >> 1] = make_double2(q0 >= 0 ? c * W.d[e] : 0.0, q1 >= 0 ? c * W.d[e + 1] : 0.0);
         }
+        *reinterpret_cast<uint4 *>(a.slot + o) = make_uint4(sw[0], sw[1], sw[2], sw[3]);
         vprev = v;
     }
 }
 
-// L27 rows of one block: thread per voxel, entries in list order, slots in window order.
-__global__ void __launch_bounds__(128) k_nn_gather(int nvox, const int32_t *off, const int32_t *perm,
-                                                   const int8_t *slot, const double *val, double *L27, int first)
+// L27 rows of one block by gather work units (at most a fixed number of
+// consecutive entries of one voxel's ownership list each, so that the outer
+// voxels crossed by thousands of characteristics do not hold up the launch):
+// one thread per unit sums its entries in list order, window slots in order.
+// A voxel with one unit is finished here; the units of a longer list leave
+// their 27 sums in part for k_nn_gather_rows.
+__global__ void __launch_bounds__(128) k_nn_gather_units(int nvox, int64_t nunits, const int32_t *urow,
+                                                         const int32_t *ubeg, const int32_t *off, const int32_t *perm,
+                                                         const int8_t *slot, const double *val, double *part,
+                                                         double *L27, int first)
 {
     __shared__ double acc[27][128];
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
 #pragma unroll
     for (int q = 0; q < 27; ++q) acc[q][threadIdx.x] = 0.0;
-    if (v >= nvox) return;
-    for (int e = off[v]; e < off[v + 1]; ++e) {
+    if (u >= nunits) return;
+    const int v = urow[u];
+    const bool next_same = u + 1 < nunits && urow[u + 1] == v;
+    const bool single = (u == 0 || urow[u - 1] != v) && !next_same;
+    const int e1 = next_same ? ubeg[u + 1] : off[v + 1];
+    for (int e = ubeg[u]; e < e1; ++e) {
         const int64_t o = (int64_t)perm[e] * NNW;
-        for (int k = 0; k < NNW; ++k) {
-            const int q = slot[o + k];
-            if (q >= 0) acc[q][threadIdx.x] += val[o + k];
+        // one 16-byte load of the 16 slots, eight of the values
+        const uint4 sq = *reinterpret_cast<const uint4 *>(slot + o);
+        const unsigned sw[4] = {sq.x, sq.y, sq.z, sq.w};
+        const double2 *vi = reinterpret_cast<const double2 *>(val + o);
+#pragma unroll
+        for (int h = 0; h < NNW / 2; ++h) {
+            const double2 d = vi[h];
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                const int k = 2 * h + w;
+                const int q = (int)(int8_t)(uint8_t)(sw[k >> 2] >> (8 * (k & 3)));
+                if (q >= 0) acc[q][threadIdx.x] += w ? d.y : d.x;
+            }
         }
     }
+    if (single) {
 #pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            double *e = L27 + (int64_t)q * nvox + v;  // slot planes: coalesced over v
+            *e = first ? acc[q][threadIdx.x] : *e + acc[q][threadIdx.x];
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 27; ++q) part[27 * u + q] = acc[q][threadIdx.x];
+    }
+}
+
+// One thread per voxel with several units: their sums added in unit order.
+__global__ void k_nn_gather_rows(int nvox, int nmulti, const int32_t *multi, const int64_t *ufirst,
+                                 const double *part, double *L27, int first)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nmulti) return;
+    const int v = multi[i];
+    const int64_t u0 = ufirst[v], u1 = ufirst[v + 1];
     for (int q = 0; q < 27; ++q) {
-        double *e = L27 + (int64_t)q * nvox + v;  // slot planes: coalesced over v
-        *e = first ? acc[q][threadIdx.x] : *e + acc[q][threadIdx.x];
+        double a = 0.0;
+        for (int64_t u = u0; u < u1; ++u) a += part[27 * u + q];
+        double *e = L27 + (int64_t)q * nvox + v;
+        *e = first ? a : *e + a;
     }
 }
 
@@ -236,9 +284,14 @@ cudaError_t nn_walk(const NnWalk &a, cudaStream_t st)
 }
 
 cudaError_t nn_gather(int nvox, const int32_t *off, const int32_t *perm, const int8_t *slot, const double *val,
-                      double *L27, int first, cudaStream_t st)
+                      const NnUnits &un, double *part, double *L27, int first, cudaStream_t st)
 {
-    k_nn_gather<<<nb(nvox, 128), 128, 0, st>>>(nvox, off, perm, slot, val, L27, first);
+    if (un.nunits > 0)
+        k_nn_gather_units<<<(unsigned)((un.nunits + 127) / 128), 128, 0, st>>>(nvox, un.nunits, un.urow, un.ubeg, off, perm,
+                                                                              slot, val, part, L27, first);
+    if (un.nmulti > 0)
+        k_nn_gather_rows<<<(unsigned)((un.nmulti + 127) / 128), 128, 0, st>>>(nvox, (int)un.nmulti, un.multi, un.ufirst,
+                                                                             part, L27, first);
     return cudaGetLastError();
 }
 

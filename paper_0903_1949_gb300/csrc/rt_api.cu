@@ -1316,23 +1316,28 @@ int nn_lstar_into(rt_grid *g, const double *chi, const uint32_t *pbits, double *
 {
     const int n = g->nvox;
     int8_t *slot = nullptr;
-    double *val = nullptr;
+    double *val = nullptr, *part = nullptr;
+    int64_t max_units = 1;
+    for (int b = 0; b < g->nblk; ++b) max_units = std::max(max_units, g->h_nunits[b]);
     if (cudaMalloc(&slot, (size_t)RTK_NNW * std::max<int64_t>(1, g->max_blk_seg)) != cudaSuccess ||
-        cudaMalloc(&val, sizeof(double) * RTK_NNW * std::max<int64_t>(1, g->max_blk_seg)) != cudaSuccess) {
+        cudaMalloc(&val, sizeof(double) * RTK_NNW * std::max<int64_t>(1, g->max_blk_seg)) != cudaSuccess ||
+        cudaMalloc(&part, sizeof(double) * 27 * (size_t)max_units) != cudaSuccess) {
         cudaGetLastError();
         if (slot) cudaFree(slot);
+        if (val) cudaFree(val);
         return fail(RT_ENOMEM, "NN Lambda* work arrays could not be allocated");
     }
     struct Free {
-        void *a, *b;
+        void *a, *b, *c;
         cudaStream_t st;
         ~Free()
         {
             cudaStreamSynchronize(st);  // no launch may still use them
             cudaFree(a);
             cudaFree(b);
+            cudaFree(c);
         }
-    } fr{slot, val, st};
+    } fr{slot, val, part, st};
     for (int b = 0; b < g->nblk; ++b) {
         const int w0 = g->blk_w0[b], nw = g->blk_nw[b];
         NnWalk a{};
@@ -1354,8 +1359,15 @@ int nn_lstar_into(rt_grid *g, const double *chi, const uint32_t *pbits, double *
         a.slot = slot;
         a.val = val;
         CK(nn_walk(a, st));
-        CK(nn_gather(n, g->d_csr_off + (size_t)b * (n + 1), g->d_perm + a.seg_lo, slot, val, L27, b == 0, st));
-        g->launches += 2;
+        NnUnits un{};
+        un.urow = g->d_urow + g->h_ubase[b];
+        un.ubeg = g->d_ubeg + g->h_ubase[b];
+        un.ufirst = g->d_ufirst + (size_t)b * (n + 1);
+        un.nunits = g->h_nunits[b];
+        un.multi = g->d_multi + g->h_mbase[b];
+        un.nmulti = g->h_mbase[b + 1] - g->h_mbase[b];
+        CK(nn_gather(n, g->d_csr_off + (size_t)b * (n + 1), g->d_perm + a.seg_lo, slot, val, un, part, L27, b == 0, st));
+        g->launches += 3;
     }
     CK(cudaStreamSynchronize(st));
     return RT_OK;

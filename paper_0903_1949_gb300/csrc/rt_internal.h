@@ -328,8 +328,20 @@ struct NnWalk {
     double *val;                 // RTK_NNW per segment: w l / L times dI_s/dS_u
 };
 cudaError_t nn_walk(const NnWalk &a, cudaStream_t st);
+// An angle block's gather work units (its ownership lists cut into pieces of
+// at most a fixed number of entries): unit voxel and first entry, per-voxel
+// unit offsets, and the voxels with more than one unit.
+struct NnUnits {
+    const int32_t *urow, *ubeg;
+    const int64_t *ufirst;
+    int64_t nunits;
+    const int32_t *multi;
+    int64_t nmulti;
+};
+// L27 (+)= the block's per-segment (slot, value) records gathered per voxel;
+// part: 27 doubles per unit.
 cudaError_t nn_gather(int nvox, const int32_t *off, const int32_t *perm, const int8_t *slot, const double *val,
-                      double *L27, int first, cudaStream_t st);
+                      const NnUnits &un, double *part, double *L27, int first, cudaStream_t st);
 cudaError_t nn_diag(int nvox, const double *L27, double *L, cudaStream_t st);
 // Operator-splitting step (I - (1-eps) L*) x = y of the nearest-neighbour
 // Lambda* (slot planes): BiCGSTAB on the Jacobi-preconditioned system (krylov
