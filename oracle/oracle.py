@@ -201,7 +201,9 @@ class OracleGrid:
         return out
 
     def nn_ali_update(self, S, J, L27, eps, B, jtol=1e-14, jmax=100000):
-        """One NN-Lambda* operator-splitting update; returns (S_new, max rel dS, Jacobi sweeps)."""
+        """One NN-Lambda* operator-splitting update; returns (S_new, max rel dS, Jacobi sweeps).
+        max rel dS is NaN (and S_new the input S) when the Jacobi sweeps leave a
+        non-finite iterate."""
         S, pS = _d(np.array(S, dtype=np.float64, copy=True))
         J, pJ = _d(J)
         L, pL = _d(L27)

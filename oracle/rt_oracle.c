@@ -973,7 +973,10 @@ int orc_nn_lstar(orc_grid *g, const double *chi, double *L27)
  * 27-voxel neighbourhoods; Jacobi sweeps
  *   dS_v <- [r_v + (1-eps_v) sum_{u != v} L*_vu dS_u] / (1 - (1-eps_v) L*_vv)
  * from dS = 0 until max |sweep change| <= jtol max |dS| (at most jmax sweeps;
- * *sweeps receives the count).  S <- S + dS; returns max |dS| / |S_new|. */
+ * *sweeps receives the count).  S <- S + dS; returns max |dS| / |S_new|, or NaN
+ * with S unchanged when a sweep leaves a non-finite iterate (the sweeps do not
+ * contract when (1-eps) times a row's off-diagonal weight outgrows its diagonal
+ * term; the system itself may still be regular). */
 double orc_nn_ali_update(const orc_grid *g, double *S, const double *J, const double *L27, const double *eps,
                          const double *B, double jtol, int jmax, int *sweeps)
 {
@@ -995,10 +998,19 @@ double orc_nn_ali_update(const orc_grid *g, double *S, const double *J, const do
             }
             y[v] = (r[v] + (1.0 - eps[v]) * off) / (1.0 - (1.0 - eps[v]) * L[13]);
         }
+        int finite = 1;
         for (int v = 0; v < nvox; ++v) {
+            if (!isfinite(y[v])) finite = 0;
             if (fabs(y[v] - x[v]) > dmax) dmax = fabs(y[v] - x[v]);
             if (fabs(y[v]) > xmax) xmax = fabs(y[v]);
             x[v] = y[v];
+        }
+        /* a sweep that leaves a non-finite iterate has not solved the OS system
+         * (the sweeps do not contract there): S stays as it was, the result is NaN */
+        if (!finite) {
+            if (sweeps) *sweeps = m;
+            free(r); free(x); free(y);
+            return NAN;
         }
         if (!(dmax > jtol * xmax)) break;
     }
@@ -1046,6 +1058,7 @@ int orc_solve(orc_grid *g, double *S, const double *chi, const double *eps, cons
         if (use_lstar == 2) rel = orc_nn_ali_update(g, S, J, L27, eps, B, 1e-14, 100000, NULL);
         else rel = orc_ali_update(nvox, S, J, L, eps, B, use_lstar);
         if (hist) hist[it - 1] = rel;
+        if (isnan(rel)) break; /* the OS step failed: not converged */
         if (rel < tol) { done = 1; break; }
         if (ng) {
             /* history slots: H[3] newest */

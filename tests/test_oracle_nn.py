@@ -104,6 +104,36 @@ def test_nn_update_solves_its_banded_system():
     assert abs(rel - np.max(np.abs(dS) / np.abs(S + dS))) < 1e-12
 
 
+def test_nn_update_reports_sweeps_that_do_not_contract():
+    """The OS step is defined by its linear system (Sect. 3.2.1); Jacobi sweeps only
+    reach it when they contract.  With the off-diagonal weights scaled up until the
+    sweep matrix has spectral radius > 1 (the system stays regular) the sweeps blow
+    up: the update must say so (NaN) and leave S alone, not stop on a test that an
+    infinite max |dS| passes."""
+    p, interp = CASES["sph_core"]()
+    o = grid(p, interp)
+    n = p["nvox"]
+    eps = np.full(n, 0.05)
+    L27 = o.nn_lstar(p["chi"])
+    L27[:, [q for q in range(27) if q != 13]] *= 40.0
+    S = p["B"] * np.random.default_rng(6).uniform(0.5, 1.5, n)
+    J, _, _, _ = o.formal_solution(S, p["chi"], p["B"])
+    M = np.zeros((n, n))
+    for v in range(n):
+        for q in range(27):
+            u = neighbour(p, v, q)
+            if u is not None and q != 13:
+                M[v, u] = L27[v, q]
+    d = 1.0 - (1.0 - eps) * L27[:, 13]
+    G = ((1.0 - eps) / d)[:, None] * M
+    assert np.max(np.abs(np.linalg.eigvals(G))) > 1.0
+    A = np.eye(n) - (1.0 - eps)[:, None] * (M + np.diag(L27[:, 13]))
+    assert np.linalg.cond(A) < 1e12
+    S_new, rel, sweeps = o.nn_ali_update(S, J, L27, eps, p["B"])
+    assert np.isnan(rel) and sweeps > 1
+    assert np.array_equal(S_new, S)
+
+
 def test_nn_without_ng_beats_diagonal_with_ng():
     """The paper's convergence statement for the 3D case (Sect. 3.2.1): the local
     (diagonal) Lambda* with Ng converges more slowly than the nearest-neighbour one
