@@ -236,3 +236,43 @@ def test_nn_preconditioned_adjoint_matches_finite_differences_at_small_eps():
     # below) and chi by 1e-5; L is linear in B (S is), so a step of 1e-2 B is exact there
     _fd_check(loss, p, grads, ("chi", "eps", "B"), voxels, h_rel={"chi": 1e-5, "eps": 1e-3, "B": 1e-2})
     g.close()
+
+
+def test_nn_adjoint_in_the_tau_1e4_eps_1e8_regime():
+    """The C5 regime (chi ~ r^-2 with radial tau 1e4, eps 1e-8) on a 33 x 17 x 33 grid
+    with 8 x 8 solid angles: the forward NN solve and the NN-preconditioned adjoint both
+    converge (their OS steps do not rely on contracting Jacobi sweeps).  S, J and F are
+    linear in B, so central differences in B (h = 1e-2 B) carry only the solves' noise and
+    resolve the B gradient; in chi and eps the ~1/eps conditioning of the fixed point
+    leaves differences of FP64-converged solves too noisy for a 1e-6 check."""
+    p = I.make_problem("sph65", n=(33, 17, 33), n_mu=8, n_phi=8, tau=1e4, eps=1e-8, noise=0.0)
+    n = p["chi"].size
+    rng = np.random.default_rng(5)
+    w = dict(S=rng.standard_normal(n), J=rng.standard_normal(n), F=rng.standard_normal((n, 3)))
+    g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=rt.RT_FP64,
+                use_lstar=rt.RT_LSTAR_NN)
+    try:
+        def loss(B):
+            g.set_opacity(p["chi"], p["eps"], B)
+            g.set_S(B)
+            it, ok = g.solve(1e-9, 2000)
+            assert ok, g.history()[-3:]
+            g.formal_solution(rt.RT_FP64)
+            return w["S"] @ g.S() + w["J"] @ g.J() + np.sum(w["F"] * g.flux())
+
+        loss(p["B"])
+        _, _, dB, it, ok = g.adjoint(w["S"], w["J"], w["F"].reshape(-1), tol=1e-9, max_iter=3000)
+        assert ok, it
+        print("NN adjoint sweeps at tau 1e4, eps 1e-8: %d" % it)
+        gmax = np.max(np.abs(dB))
+        for v in np.random.default_rng(33).choice(n, 6, replace=False):
+            B = p["B"].copy()
+            h = 1e-2 * B[v]
+            B[v] += h
+            Lp = loss(B)
+            B[v] -= 2.0 * h
+            Lm = loss(B)
+            fd = (Lp - Lm) / (2.0 * h)
+            assert abs(fd - dB[v]) <= 3e-5 * gmax, (v, fd, dB[v], gmax)
+    finally:
+        g.close()

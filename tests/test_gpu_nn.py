@@ -310,3 +310,37 @@ def test_os_step_is_one_launch_and_its_bounded_wait_reports_a_timeout():
     h.ali_step()
     assert np.array_equal(h.S(), S2)
     h.close()
+
+
+def test_nn_solve_converges_at_tau_1e4_eps_1e8():
+    """The regime of the C5 adjoint configuration (chi ~ r^-2 with radial tau 1e4,
+    eps 1e-8) on a 33 x 17 x 33 grid with 8 x 8 solid angles: Jacobi sweeps of the NN
+    OS step do not contract there, the defect-correction solve does, and rt_solve
+    converges in FP64 and in mixed precision.  Check, with the oracle's formal
+    solution of the converged S (Sect. 2): the fixed-point residual (1-eps) J + eps B - S
+    is within the bound that the last ALI step leaves (|(I - (1-eps) L*) dS| <= 2 |dS|);
+    the two precisions agree to the conditioning of the problem (~1/eps amplifies the
+    FP32 rounding of J, so to 1e-4 rather than to rounding)."""
+    p = I.make_problem("sph65", n=(33, 17, 33), n_mu=8, n_phi=8, tau=1e4, eps=1e-8, noise=0.0)
+    out = {}
+    for prec, tol in ((rt.RT_FP64, 1e-7), (rt.RT_MIXED, 1e-6)):
+        g = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=prec,
+                    use_lstar=rt.RT_LSTAR_NN)
+        try:
+            g.set_opacity(p["chi"], p["eps"], p["B"])
+            it, ok = g.solve(tol, 600)
+            print("precision %d: %d formal solutions, last max rel dS %.2e" % (prec, it, g.history()[-1]))
+            assert ok, g.history()[-5:]
+            out[prec] = (g.S(), tol)
+        finally:
+            g.close()
+    o = O.OracleGrid(p["coord"], p["edges"], p["dirs"], p["weights"], p["inner_bc"])
+    for prec, (S, tol) in out.items():
+        J, _, _, miss = o.formal_solution(S, p["chi"], p["B"])
+        assert miss == 0
+        R = float(np.max(np.abs((1.0 - p["eps"]) * J + p["eps"] * p["B"] - S) / np.abs(S)))
+        print("precision %d: fixed-point residual with the oracle's J %.2e" % (prec, R))
+        assert R < 3.0 * tol, (prec, R)
+    o.close()
+    S64, S32 = out[rt.RT_FP64][0], out[rt.RT_MIXED][0]
+    assert np.max(np.abs(S32 - S64) / np.abs(S64)) < 1e-4
