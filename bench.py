@@ -462,6 +462,14 @@ def main():
     line_res = None
     if not args.no_line and rank == 0:
         line_res = line_measure(g, args.workload, rt, I, torch)
+        # the other thermalisation parameters of the paper's line test (eps_l = 1 is one
+        # iteration, S_l = B, in the tests)
+        line_res["eps_scan"] = {}
+        for e in (1e-2, 1e-8):
+            r = line_measure(g, args.workload, rt, I, torch, eps_l=e, max_iter=120)
+            line_res["eps_scan"]["%g" % e] = {k: r[k] for k in ("iterations_to_1e-3", "iterations_to_1e-4",
+                                                               "iterations", "converged", "s_per_iteration",
+                                                               "setup_s", "last_max_rel_dS_l")}
 
     flux_res = None
     if args.flux_max > 0 and rank == 0:
