@@ -19,8 +19,9 @@
 // Each block owns a contiguous range of voxels.  Where it fits in shared
 // memory, the FP32 solve keeps the block's halo of the 27-point stencil
 // (its range widened by n2 n3 + 2 n3 voxels either side on the spherical grid,
-// n2 n3 + n3 + 1 on the cylindrical one) of r, p and v
-// there: a phase loads the halo once from L2 and forms p = r + beta (p -
+// n2 n3 + n3 + 1 on the cylindrical one) of r, p and v there, and the block's
+// FP32 rows of M too where those fit: a phase loads the halo once from L2
+// (16-byte asynchronous copies that bypass L1) and forms p = r + beta (p -
 // omega v) and s = r - alpha v over it, so a BiCGSTAB iteration needs three
 // grid barriers, not five, and the neighbour reads of the matrix-vector
 // products are shared-memory reads (neighbours past the halo, across the
