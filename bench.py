@@ -770,11 +770,11 @@ def convergence_measure(g, p, rt, torch, tol=1e-6, max_fs=400):
     workload with the nearest-neighbour Lambda* (built once per chi, FP64), its OS
     step solved exactly or to 1e-4, and the diagonal Lambda* for as many formal
     solutions (it does not converge in practical time at eps 1e-4)."""
-    out = {"tol_max_rel_dS": tol, "solver": "rt_solve, RT_MIXED, refine_every 16, Ng"}
+    out = {"tol_max_rel_dS": tol, "solver": "rt_solve, RT_MIXED, library defaults (FP64 refinement after at most 32 FP32 correction sweeps), Ng"}
     runs = {}
     for label, jexp in (("nn_lstar", 14), ("nn_lstar_os_1e-4", 4)):
         nn = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], inner_bc=p["inner_bc"], precision=rt.RT_MIXED,
-                     use_lstar=rt.RT_LSTAR_NN, refine_every=16)
+                     use_lstar=rt.RT_LSTAR_NN)
         nn.tune(rt.RT_TUNE_NN_JTOL, jexp)
         nn.set_opacity(p["chi"], p["eps"], p["B"])
         torch.cuda.synchronize()
@@ -823,7 +823,7 @@ def equal_error_converged(p, rt, torch, target=1e-5, max_fs=2000,
     the timed solves (reported as set-up)."""
     kw = dict(inner_bc=p["inner_bc"], use_lstar=rt.RT_LSTAR_NN, ng=True)
     g64 = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], precision=rt.RT_FP64, **kw)
-    gmx = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], precision=rt.RT_MIXED, refine_every=16, **kw)
+    gmx = rt.Grid(p["coord"], p["edges"], p["dirs"], p["weights"], precision=rt.RT_MIXED, **kw)
     out = {"target_max_rel_J_err": target, "lstar": "nearest-neighbour (FP64, built once per chi)", "ng": True}
     try:
         setup = {}

@@ -88,7 +88,9 @@ typedef struct rt_grid_desc {
                                Lambda*; RT_LSTAR_NONE (0): plain Lambda iteration */
     int ng;                 /* 1: order-2 Ng acceleration every 4 ALI iterates */
     int refine_every;       /* RT_MIXED: maximum FP32 correction sweeps per FP64
-                             * refinement (0 = default 16) */
+                             * refinement (0 = default 32; the fixed point is the
+                             * FP64 one whatever the value, which sets only how often
+                             * an FP64 formal solution is paid for) */
     int angle_block;        /* solid angles per formal-solution block (0 = auto) */
     int device;             /* CUDA device ordinal */
     void *stream;           /* cudaStream_t for all work (NULL = legacy default) */

@@ -12,7 +12,7 @@ struct rt_grid {
     int device = 0;
     cudaStream_t st = nullptr;
     int coord = 0, n1 = 0, n2 = 0, n3 = 0, nvox = 0, n_ang = 0, nphi = 0;
-    int inner_bc = 0, interp = 0, precision = 0, use_lstar = 1, ng = 1, refine_every = 16;
+    int inner_bc = 0, interp = 0, precision = 0, use_lstar = 1, ng = 1, refine_every = 32;
     double I_outer = 0.0;
     std::vector<double> h_e[3], h_dirs, h_wt;
     std::vector<void *> allocs;

@@ -1552,7 +1552,7 @@ int rt_grid_create(rt_grid **out, const rt_grid_desc *d)
     g->precision = d->precision;
     g->use_lstar = d->use_lstar;
     g->ng = d->ng ? 1 : 0;
-    g->refine_every = d->refine_every > 0 ? d->refine_every : 16;
+    g->refine_every = d->refine_every > 0 ? d->refine_every : 32;
     g->I_outer = d->I_outer;
     g->ablk = d->angle_block;
     for (int a = 0; a < 3; ++a) g->h_e[a].assign(d->edges[a], d->edges[a] + d->n[a] + 1);
