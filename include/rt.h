@@ -267,8 +267,8 @@ int rt_ali_step(rt_grid *g, double *max_rel_dS);
 /* Iterate to max rel dS < tol.  RT_FP64: plain ALI(+Ng) with the FP64 formal
  * solution.  RT_MIXED: FP64 formal solutions give the exact residual
  * r = (1-eps) J + eps B - S, FP32 correction sweeps (ALI + Ng on the
- * homogeneous problem) solve for the update, repeated until the residual
- * meets tol.  *iters (may be NULL) receives the number of formal solutions
+ * homogeneous problem; at most refine_every of them, default 32) solve for
+ * the update, repeated until the residual meets tol.  *iters (may be NULL) receives the number of formal solutions
  * of the precision that drives convergence (FP64 ones for RT_FP64 and the
  * total for RT_MIXED).  Returns RT_ENOTCONVERGED at max_iter. */
 int rt_solve(rt_grid *g, double tol, int max_iter, int *iters);
